@@ -1,0 +1,141 @@
+"""SCR-preconditioned FGMRES and the mesh-motion AMG-CG (test
+infrastructure only; the CPU reference of the whole solver path).
+
+* Algorithm 1 (App. B): y = P_SCR^{-1} r
+    1. solve A yhat_v = r_v  (GMRES + P_A, delta_A, n_A^max)
+    2. r_p <- r_p - C yhat_v  (the garbled "C rhat_v" read as the solution
+       of step 1, the only reading consistent with the LDU inverse)
+    3. solve S y_p = r_p  (GMRES + P_S, delta_S, n_S^max), S applied by
+       Algorithm 2
+    4. r_v <- r_v - B y_p
+    5. solve A y_v = r_v  (GMRES + P_A, delta_A, n_A^max)
+* Algorithm 2 (App. B): S x_p = D x_p - C A^{-1} (B x_p) with A^{-1} an
+  inner GMRES + P_I solve to delta_I.
+* Outer level (Sec. 5.2.1): FGMRES on calA x = b preconditioned by P_SCR,
+  tolerance delta, n^max.  P_A = P_I = AMG(A), P_S = AMG(Shat).
+* Mesh motion (Sec. 5.2.2): CG + AMG(L) on the harmonic extension.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import amg
+from .krylov import KrylovInfo, fgmres, gmres, pcg
+from .schur import schur_hat
+from .sparse import BlockOperator, rel_residual, to_csr
+
+
+@dataclasses.dataclass
+class SolverOptions:
+    """Solver settings of the paper's table of solver parameters with the
+    outer tolerance tightened to 1e-8."""
+    rtol: float = 1e-8
+    max_it: int = 200
+    restart: int = 30
+    rtol_A: float = 1e-3
+    rtol_S: float = 1e-3
+    rtol_I: float = 1e-3
+    max_A: int = 200
+    max_S: int = 200
+    max_I: int = 200
+    restart_inner: int = 30
+    amg_theta: float = 0.08
+    amg_coarse: int = 64
+    amg_max_levels: int = 10
+    nu: int = 1
+    mm_rtol: float = 1e-8
+    mm_max_it: int = 500
+
+
+@dataclasses.dataclass
+class Counters:
+    outer: int = 0
+    a_solves: int = 0
+    a_iters: int = 0
+    s_iters: int = 0
+    i_iters: int = 0
+
+
+class SCRSolver:
+    def __init__(self, system, opts: SolverOptions | None = None):
+        self.opts = opts or SolverOptions()
+        self.op = BlockOperator.from_system(system)
+        o = self.opts
+        self.Shat = schur_hat(self.op)
+        self.amg_A = amg.setup(self.op.A, 3, o.amg_theta, o.amg_max_levels, o.amg_coarse, o.nu, o.nu)
+        self.amg_S = amg.setup(self.Shat, 1, o.amg_theta, o.amg_max_levels, o.amg_coarse, o.nu, o.nu)
+        self.cnt = Counters()
+
+    # Algorithm 2 ------------------------------------------------------
+    def apply_S(self, xp: np.ndarray) -> np.ndarray:
+        o, op = self.opts, self.op
+        xbar = op.B @ xp
+        xt, info = gmres(lambda v: op.A @ v, xbar, lambda v: amg.vcycle(self.amg_A, v),
+                         tol=o.rtol_I, maxit=o.max_I, restart=o.restart_inner)
+        self.cnt.i_iters += info.iters
+        xbar = op.C @ xt
+        xhat = op.D @ xp
+        return xhat - xbar
+
+    # Algorithm 1 ------------------------------------------------------
+    def solve_A(self, rv: np.ndarray) -> np.ndarray:
+        o, op = self.opts, self.op
+        y, info = gmres(lambda v: op.A @ v, rv, lambda v: amg.vcycle(self.amg_A, v),
+                        tol=o.rtol_A, maxit=o.max_A, restart=o.restart_inner)
+        self.cnt.a_solves += 1
+        self.cnt.a_iters += info.iters
+        return y
+
+    def apply_pc(self, r: np.ndarray) -> np.ndarray:
+        o, op = self.opts, self.op
+        rv, rp = op.split(np.asarray(r, dtype=np.float64))
+        yv_hat = self.solve_A(rv)
+        rp2 = rp - op.C @ yv_hat
+        yp, info = gmres(self.apply_S, rp2, lambda v: amg.vcycle(self.amg_S, v),
+                         tol=o.rtol_S, maxit=o.max_S, restart=o.restart_inner)
+        self.cnt.s_iters += info.iters
+        rv2 = rv - op.B @ yp
+        yv = self.solve_A(rv2)
+        return np.concatenate([yv, yp])
+
+    # outer level --------------------------------------------------------
+    def solve(self, b: np.ndarray, max_outer: int | None = None):
+        o = self.opts
+        x, info = fgmres(self.op.matvec, b, self.apply_pc, tol=o.rtol,
+                         maxit=o.max_it if max_outer is None else max_outer, restart=o.restart)
+        self.cnt.outer += info.iters
+        return x, info
+
+    def rel_residual(self, x, b) -> float:
+        return rel_residual(self.op, x, b)
+
+
+class MeshSolver:
+    """CG + AMG(L) on (L kron I3) U = g, vectors interleaved (n, 3)."""
+
+    def __init__(self, system, opts: SolverOptions | None = None):
+        self.opts = opts or SolverOptions()
+        o = self.opts
+        self.L = to_csr(system.L)
+        self.H = amg.setup(self.L, 1, o.amg_theta, o.amg_max_levels, o.amg_coarse, o.nu, o.nu)
+
+    def solve(self, g: np.ndarray, tol: float | None = None):
+        o = self.opts
+        n = self.L.shape[0]
+        op = lambda v: (self.L @ v.reshape(n, 3)).reshape(-1)
+        pc = lambda v: amg.vcycle(self.H, v.reshape(n, 3)).reshape(-1)
+        return pcg(op, g, pc, tol=o.mm_rtol if tol is None else tol, maxit=o.mm_max_it)
+
+
+def solve_system(system, opts: SolverOptions | None = None):
+    """The whole CPU reference path: setup, SCR-FGMRES and the mesh CG."""
+    s = SCRSolver(system, opts)
+    x, info = s.solve(system.b)
+    out = dict(x=x, info=info, counters=s.cnt)
+    if system.L is not None:
+        m = MeshSolver(system, opts)
+        u, minfo = m.solve(system.mesh_b)
+        out.update(u=u, mesh_info=minfo)
+    return out

@@ -1,0 +1,31 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    config.addinivalue_line("markers", "slow: longer CPU test")
+
+
+@pytest.fixture(scope="session")
+def tiny_system():
+    import fsi_inputs as F
+    return F.tube_system("tube_tiny", keep_mesh=True)
+
+
+@pytest.fixture(scope="session")
+def mini_system():
+    import fsi_inputs as F
+    return F.tube_system("tube_mini", keep_mesh=True)
+
+
+@pytest.fixture(scope="session")
+def mini_direct(mini_system):
+    from oracle import direct
+    return direct.solve_block(mini_system)

@@ -1,0 +1,290 @@
+"""Pins of the CPU oracle against brute force, closed forms and invariants
+(no GPU).  A few tests plant a mistake in an oracle function (on the CPU)
+and check that the pins catch it."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import fsi_inputs as F
+from oracle import amg, direct, krylov, schur, scr
+from oracle.sparse import BlockOperator, bsr_matvec_by_definition, rel_residual, to_csr
+
+
+def _random_bsr(rng, nbr, nbc, br, bc, density=0.3):
+    rp = [0]
+    cols = []
+    for i in range(nbr):
+        c = np.nonzero(rng.random(nbc) < density)[0]
+        cols.extend(c.tolist())
+        rp.append(len(cols))
+    rp = np.array(rp, dtype=np.int32)
+    col = np.array(cols, dtype=np.int32)
+    val = rng.standard_normal(len(cols) * br * bc)
+    return F.BSR(br, bc, nbr, nbc, rp, col, val)
+
+
+# ------------------------------------------------------------- sparse
+@pytest.mark.parametrize("br,bc", [(3, 3), (3, 1), (1, 3), (1, 1)])
+def test_block_matvec_definition_vs_dense(br, bc):
+    rng = np.random.default_rng(br * 10 + bc)
+    M = _random_bsr(rng, 17, 13, br, bc)
+    dense = np.zeros((17 * br, 13 * bc))
+    blocks = M.val.reshape(-1, br, bc)
+    for i in range(17):
+        for t in range(M.row_ptr[i], M.row_ptr[i + 1]):
+            j = M.col[t]
+            dense[i * br:(i + 1) * br, j * bc:(j + 1) * bc] += blocks[t]
+    x = rng.standard_normal(13 * bc)
+    assert np.allclose(bsr_matvec_by_definition(M, x), dense @ x, rtol=1e-13, atol=1e-13)
+    assert np.allclose(to_csr(M).toarray(), dense)
+
+
+# ------------------------------------------------------------- direct
+def test_direct_solution_residual(mini_system, mini_direct):
+    op = BlockOperator.from_system(mini_system)
+    assert rel_residual(op, mini_direct, mini_system.b) < 1e-12
+
+
+def test_direct_matches_dense_on_tiny(tiny_system):
+    op = BlockOperator.from_system(tiny_system)
+    x = direct.solve_block(tiny_system)
+    xd = np.linalg.solve(op.full().toarray(), tiny_system.b)
+    assert np.linalg.norm(x - xd) <= 1e-10 * np.linalg.norm(xd)
+
+
+def test_mesh_direct(mini_system):
+    u = direct.solve_mesh(mini_system)
+    L = to_csr(mini_system.L)
+    g = mini_system.mesh_b.reshape(-1, 3)
+    assert np.linalg.norm(L @ u.reshape(-1, 3) - g) < 1e-12 * np.linalg.norm(g)
+
+
+# ------------------------------------------------------------- schur
+def test_ldu_factorisation(tiny_system):
+    op = BlockOperator.from_system(tiny_system)
+    Lf, Df, Uf = schur.ldu_factors_dense(op)
+    K = op.full().toarray()
+    assert np.allclose(Lf @ Df @ Uf, K, rtol=1e-10, atol=1e-12 * np.abs(K).max())
+
+
+def test_exact_scr_is_inverse(tiny_system):
+    op = BlockOperator.from_system(tiny_system)
+    rng = np.random.default_rng(0)
+    r = rng.standard_normal(op.n)
+    y = schur.scr_exact_apply(op, r)
+    yd = np.linalg.solve(op.full().toarray(), r)
+    assert np.linalg.norm(y - yd) <= 1e-9 * np.linalg.norm(yd)
+
+
+def test_exact_scr_catches_planted_mistake(tiny_system, monkeypatch):
+    """Algorithm 1 with step 2 dropped (r_p not updated) must miss A^{-1}."""
+    op = BlockOperator.from_system(tiny_system)
+    rng = np.random.default_rng(0)
+    r = rng.standard_normal(op.n)
+    yd = np.linalg.solve(op.full().toarray(), r)
+
+    def broken(op, r):
+        A = op.A.toarray()
+        S = schur.schur_exact_dense(op)
+        rv, rp = op.split(r)
+        yp = np.linalg.solve(S, rp)
+        yv = np.linalg.solve(A, rv - op.B @ yp)
+        return np.concatenate([yv, yp])
+
+    monkeypatch.setattr(schur, "scr_exact_apply", broken)
+    y = schur.scr_exact_apply(op, r)
+    # the pin above holds to 1e-9; the planted mistake misses by far more
+    assert np.linalg.norm(y - yd) > 1e-6 * np.linalg.norm(yd)
+
+
+def test_schur_hat_definition(tiny_system):
+    op = BlockOperator.from_system(tiny_system)
+    A, B, C, D = (M.toarray() for M in (op.A, op.B, op.C, op.D))
+    Sh = D - C @ np.diag(1.0 / np.diag(A)) @ B
+    assert np.allclose(schur.schur_hat(op).toarray(), Sh, rtol=1e-12, atol=1e-14 * np.abs(Sh).max())
+    # Shat equals the exact S when A is diagonal
+    Adiag = sp.diags(op.A.diagonal()).tocsr()
+    op2 = BlockOperator.__new__(BlockOperator)
+    op2.A, op2.B, op2.C, op2.D = Adiag, op.B, op.C, op.D
+    op2.nv, op2.np, op2.n = op.nv, op.np, op.n
+    assert np.allclose(schur.schur_hat(op2).toarray(), schur.schur_exact_dense(op2), rtol=1e-10,
+                       atol=1e-14 * np.abs(Sh).max())
+
+
+def test_simple_identity(tiny_system):
+    op = BlockOperator.from_system(tiny_system)
+    P1 = schur.simple_matrix_dense(op)
+    P2 = schur.simple_factored_dense(op)
+    assert np.allclose(P1, P2, rtol=1e-9, atol=1e-12 * np.abs(P1).max())
+
+
+# ------------------------------------------------------------- krylov
+def _nonsym(rng, n):
+    return np.eye(n) * 4 + rng.standard_normal((n, n)) / np.sqrt(n)
+
+
+def test_gmres_finite_termination():
+    rng = np.random.default_rng(1)
+    n = 25
+    A = _nonsym(rng, n)
+    b = rng.standard_normal(n)
+    x, info = krylov.fgmres(lambda v: A @ v, b, tol=1e-13, restart=n, maxit=n)
+    assert info.iters <= n
+    assert np.linalg.norm(x - np.linalg.solve(A, b)) < 1e-10 * np.linalg.norm(x)
+
+
+def test_gmres_restarted_converges():
+    rng = np.random.default_rng(2)
+    n = 60
+    A = _nonsym(rng, n)
+    b = rng.standard_normal(n)
+    x, info = krylov.fgmres(lambda v: A @ v, b, tol=1e-10, restart=7, maxit=400)
+    assert info.converged and info.restarts > 1
+    assert np.linalg.norm(b - A @ x) <= 1e-10 * np.linalg.norm(b)
+
+
+def test_fgmres_exact_preconditioner_one_iteration(tiny_system):
+    op = BlockOperator.from_system(tiny_system)
+    x, info = krylov.fgmres(op.matvec, tiny_system.b, lambda r: schur.scr_exact_apply(op, r),
+                            tol=1e-8)
+    assert info.iters == 1
+    assert rel_residual(op, x, tiny_system.b) < 1e-8
+
+
+def test_fgmres_residual_estimate_matches_true_residual():
+    # the Givens recurrence value |g_{k+1}| equals ||b - A x_k||
+    rng = np.random.default_rng(3)
+    n = 40
+    A = _nonsym(rng, n)
+    b = rng.standard_normal(n)
+    for k in (3, 6, 9):
+        x, info = krylov.fgmres(lambda v: A @ v, b, tol=1e-300, restart=k, maxit=k,
+                                true_residual_check=False)
+        est = info.rel_res
+        true = np.linalg.norm(b - A @ x) / np.linalg.norm(b)
+        assert abs(est - true) < 1e-10
+
+
+def test_pcg():
+    rng = np.random.default_rng(4)
+    n = 30
+    Q = rng.standard_normal((n, n))
+    A = Q @ Q.T + n * np.eye(n)
+    b = rng.standard_normal(n)
+    x, info = krylov.pcg(lambda v: A @ v, b, lambda r: r / np.diag(A), tol=1e-12, maxit=n + 5)
+    assert info.converged and info.iters <= n
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-9)
+
+
+def test_zero_rhs():
+    x, info = krylov.fgmres(lambda v: 2 * v, np.zeros(5))
+    assert info.converged and np.all(x == 0)
+    x, info = krylov.pcg(lambda v: 2 * v, np.zeros(5))
+    assert info.converged and np.all(x == 0)
+
+
+# ------------------------------------------------------------- amg
+def test_tentative_prolongator_orthonormal():
+    agg = np.array([0, 0, 1, -1, 1, 1, 2, 0])
+    for bs in (1, 3):
+        Pt = amg.tentative_prolongator(agg, bs).toarray()
+        assert np.allclose(Pt.T @ Pt, np.eye(3 * bs))
+        # constants on each aggregate are reproduced
+        assert np.allclose((Pt @ (Pt.T @ np.ones(8 * bs)))[np.repeat(agg >= 0, bs)], 1.0)
+
+
+def test_aggregation_covers_strong_nodes(mini_system):
+    A = to_csr(mini_system.A)
+    S = amg.strength_graph(A, 3, 0.08)
+    agg = amg.aggregate_greedy(S)
+    has_nb = np.diff(S.indptr) > 0
+    assert np.all(agg[has_nb] >= 0) and np.all(agg[~has_nb] == -1)
+    # every aggregate is connected in the strength graph
+    for a in range(agg.max() + 1):
+        nodes = np.nonzero(agg == a)[0]
+        sub = S[nodes][:, nodes]
+        ncomp = sp.csgraph.connected_components(sub, directed=False)[0]
+        assert ncomp == 1
+
+
+def test_vcycle_contracts_on_spd(mini_system):
+    L = to_csr(mini_system.L)
+    H = amg.setup(L, 1, 0.08, 10, 16, 2, 2)
+    assert H.n_levels >= 2
+    rng = np.random.default_rng(5)
+    Ld = L.toarray()
+    # error propagation E = I - M^{-1} L; its energy norm must be < 1
+    n = L.shape[0]
+    E = np.eye(n) - np.column_stack([amg.vcycle(H, Ld[:, j]) for j in range(n)])
+    w, V = np.linalg.eigh(Ld)
+    Lh = V @ np.diag(np.sqrt(w)) @ V.T
+    Lhi = V @ np.diag(1 / np.sqrt(w)) @ V.T
+    rho = np.linalg.norm(Lh @ E @ Lhi, 2)
+    assert rho < 0.9, rho
+    # the V-cycle is a symmetric operator (usable in CG)
+    M = np.column_stack([amg.vcycle(H, np.eye(n)[:, j]) for j in range(n)])
+    assert np.allclose(M, M.T, atol=1e-10 * np.abs(M).max())
+
+
+def test_galerkin_operator(mini_system):
+    L = to_csr(mini_system.L)
+    H = amg.setup(L, 1, 0.08, 10, 16, 1, 1)
+    l0, l1 = H.levels[0], H.levels[1]
+    Ac = (l0.P.T @ l0.A @ l0.P).toarray()
+    assert np.allclose(l1.A.toarray(), Ac, rtol=1e-12, atol=1e-14 * np.abs(Ac).max())
+    # smoothed prolongator definition
+    lam = np.max(np.abs(L).sum(axis=1).A1 / np.abs(L.diagonal()))
+    Pt = amg.tentative_prolongator(l0.agg, 1)
+    P = Pt - (4 / (3 * lam)) * sp.diags(1 / L.diagonal()) @ L @ Pt
+    assert np.allclose(l0.P.toarray(), P.toarray(), rtol=1e-12, atol=1e-15)
+
+
+def test_two_level_exact_on_constant_near_nullspace():
+    # 1-D Laplacian: the V-cycle reduces a smooth error far better than one
+    # Jacobi sweep (checks the coarse-grid correction is wired in)
+    n = 200
+    L = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]).tocsr()
+    H = amg.setup(L, 1, 0.08, 10, 8, 1, 1)
+    x = np.sin(np.pi * np.arange(1, n + 1) / (n + 1))
+    b = L @ x
+    e_v = np.linalg.norm(x - amg.vcycle(H, b)) / np.linalg.norm(x)
+    e_j = np.linalg.norm(x - b / np.abs(L).sum(axis=1).A1) / np.linalg.norm(x)
+    assert e_v < 0.5 * e_j
+
+
+# ------------------------------------------------------------- scr
+def test_algorithm2_matches_schur_definition(tiny_system):
+    opts = scr.SolverOptions(rtol_I=1e-13, max_I=400, restart_inner=60)
+    s = scr.SCRSolver(tiny_system, opts)
+    S = schur.schur_exact_dense(s.op)
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal(s.op.np)
+    assert np.allclose(s.apply_S(x), S @ x, rtol=1e-8, atol=1e-9 * np.abs(S @ x).max())
+
+
+def test_algorithm1_with_tight_inner_is_inverse(tiny_system):
+    opts = scr.SolverOptions(rtol_A=1e-13, rtol_S=1e-13, rtol_I=1e-14, max_A=400, max_S=400,
+                             max_I=400, restart_inner=80)
+    s = scr.SCRSolver(tiny_system, opts)
+    rng = np.random.default_rng(7)
+    r = rng.standard_normal(s.op.n)
+    y = s.apply_pc(r)
+    yd = np.linalg.solve(s.op.full().toarray(), r)
+    assert np.linalg.norm(y - yd) <= 1e-7 * np.linalg.norm(yd)
+
+
+def test_full_solve_matches_direct(mini_system, mini_direct):
+    s = scr.SCRSolver(mini_system)
+    x, info = s.solve(mini_system.b)
+    assert info.converged
+    assert s.rel_residual(x, mini_system.b) <= 1e-8
+    assert np.linalg.norm(x - mini_direct) <= 1e-6 * np.linalg.norm(mini_direct)
+    assert 1 <= info.iters <= 10
+
+
+def test_mesh_cg_matches_direct(mini_system):
+    m = scr.MeshSolver(mini_system, scr.SolverOptions(mm_rtol=1e-12))
+    u, info = m.solve(mini_system.mesh_b)
+    assert info.converged
+    ud = direct.solve_mesh(mini_system)
+    assert np.linalg.norm(u - ud) <= 1e-9 * np.linalg.norm(ud)
