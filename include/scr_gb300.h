@@ -1,0 +1,213 @@
+/*
+ * scr_gb300.h - C ABI of the GB300 (sm_103a) SCR-FGMRES + AMG block solver.
+ *
+ * The library solves, on one GPU, the two linear systems of every Newton
+ * step of the segregated predictor multi-corrector of Liu et al. (arXiv
+ * 2206.06996):
+ *
+ *   1. the velocity-pressure block system  calA x = b,
+ *        calA = [[A, B], [C, D]]   (Sec. 5.2.1; blocks defined in Sec. 3.5,
+ *        eqs. ABCD_block_matrices_fluid / _solid),
+ *      by FGMRES (Sec. 5.2.1, "outer level") preconditioned with the Schur
+ *      complement reduction P_SCR (App. B, Algorithm 1), whose Schur
+ *      complement S = D - C A^{-1} B is applied matrix-free (App. B,
+ *      Algorithm 2), with AMG preconditioners P_A = P_I = AMG(A) and
+ *      P_S = AMG(Shat), Shat = D - C diag(A)^{-1} B (Sec. 5.2.1);
+ *   2. the mesh-motion system (harmonic extension, Sec. 2.2 and 5.2.2) by
+ *      CG preconditioned with AMG.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Status: every function returns an int: SCR_OK (0) or an error code
+ *   below.  No C++ exception crosses the boundary.  scr_last_error() returns
+ *   a message for the last failure on the calling thread.
+ * - Matrices are block CSR (scr_bsr): nb_rows x nb_cols blocks of br x bc
+ *   scalars, 0-based int32 row_ptr[nb_rows+1] and col_idx[nnzb] with column
+ *   indices sorted within each row, values block after block, each block
+ *   row-major.  Blocks: A 3x3 over velocity nodes, B 3x1, C 1x3, D 1x1 over
+ *   pressure indices (nodes first, then the duplicated interface pressures
+ *   of Sec. 3.3).  Dirichlet degrees of freedom arrive as identity rows with
+ *   zeroed columns.
+ * - Vectors: velocity nodes interleaved (x, y, z) for all n_v nodes, then all
+ *   n_p pressures: length 3 n_v + n_p.  The mesh system uses n_m nodes with
+ *   three interleaved displacement components (length 3 n_m).
+ * - Sign: the paper solves calA dx = -R; the caller passes b = -R.
+ * - Ownership: the caller owns every pointer it passes; set-up functions
+ *   deep-copy their inputs (converting precision and layout) and keep
+ *   nothing the caller gave.  Output vectors are caller-allocated.
+ * - ptr_is_device: 0 = host pointers (copied in and out on the handle's
+ *   stream), 1 = device pointers of the current device.
+ * - Streams: all work is ordered on the stream given to scr_create; calls
+ *   return after the stream work they need has finished, except where noted.
+ */
+#ifndef SCR_GB300_H
+#define SCR_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SCR_OK 0
+#define SCR_INVALID_ARG 1
+#define SCR_CUDA_ERROR 2
+#define SCR_NOT_CONVERGED 3 /* x holds the best iterate; iters/residual valid */
+#define SCR_DEVICE_TIMEOUT 4
+#define SCR_SINGULAR 5
+
+/* arithmetic of the preconditioner (the outer FGMRES, the Gram-Schmidt
+   steps, the operator calA and the final residual are always FP64) */
+#define SCR_FP64 0
+#define SCR_MIXED 1 /* A, Shat and the AMG hierarchies in FP32 */
+
+/* hierarchies for scr_amg_apply / scr_export */
+#define SCR_HIER_A 0
+#define SCR_HIER_SHAT 1
+#define SCR_HIER_MESH 2
+
+/* what scr_export returns */
+#define SCR_EXPORT_OPERATOR 0    /* level operator A_l (level 0 of SCR_HIER_SHAT is Shat) */
+#define SCR_EXPORT_PROLONGATOR 1 /* smoothed prolongator P_l */
+#define SCR_EXPORT_AGGREGATES 2  /* aggregate id per block row of level l (-1: none), into col_idx */
+
+typedef struct scr_ctx* scr_handle;
+
+/* Solver settings (Sec. 6, table of solver settings; outer tolerance
+   tightened to 1e-8).  Defaults from scr_default_opts. */
+typedef struct {
+  double rtol;        /* outer FGMRES relative residual ||b - calA x|| / ||b||, 1e-8 */
+  int max_it;         /* outer iteration cap n^max, 200 */
+  int restart;        /* outer FGMRES restart length, 30 */
+  double rtol_A;      /* intermediate GMRES on A (Alg. 1 steps 1, 5), delta_A = 1e-3 */
+  double rtol_S;      /* intermediate GMRES on S (Alg. 1 step 3), delta_S = 1e-3 */
+  double rtol_I;      /* inner GMRES on A inside Alg. 2, delta_I = 1e-3 */
+  int max_A, max_S, max_I; /* 200 each */
+  int restart_inner;  /* restart of the intermediate/inner GMRES, 30 */
+  int precision;      /* SCR_FP64 or SCR_MIXED */
+  int precond;        /* 0 = SCR (Algorithm 1) */
+  double amg_theta;   /* strength threshold, 0.08 */
+  int amg_max_levels; /* 10 */
+  int amg_coarse_size;/* block rows at which coarsening stops, 64 */
+  int amg_nu;         /* l1-Jacobi sweeps before and after the coarse correction, 1 */
+  double mm_rtol;     /* mesh CG relative residual, 1e-8 */
+  int mm_max_it;      /* mesh CG iteration cap, 500 */
+  int verbose;        /* 0 quiet */
+} scr_opts;
+
+typedef struct {
+  int nb_rows, nb_cols, br, bc, nnzb;
+  const int* row_ptr;
+  const int* col_idx;
+  const double* val;
+} scr_bsr;
+
+/* destination of scr_export (host pointers; pass NULL arrays to query sizes) */
+typedef struct {
+  int nb_rows, nb_cols, br, bc, nnzb;
+  int* row_ptr;
+  int* col_idx;
+  double* val;
+} scr_bsr_out;
+
+/* counters and timings of the last set-up and solves on a handle */
+typedef struct {
+  int outer_iters;      /* FGMRES iterations of the last scr_solve */
+  int a_solves;         /* intermediate A solves (Alg. 1 steps 1 and 5) */
+  int a_iters;          /* GMRES iterations inside them */
+  int s_iters;          /* GMRES iterations on S (Alg. 1 step 3) */
+  int i_iters;          /* inner GMRES iterations (Alg. 2) */
+  int vcycles_A, vcycles_S, vcycles_M;
+  int mm_iters;         /* mesh CG iterations of the last mm_solve */
+  double rel_res;       /* final FP64 ||b - calA x|| / ||b|| of the last scr_solve */
+  double mm_rel_res;
+  double setup_ms, solve_ms, mm_setup_ms, mm_solve_ms; /* host wall clock */
+  long long kernel_launches;  /* launches issued by this handle since creation */
+  long long spmv_bytes;       /* modelled HBM bytes of the SpMV-type launches */
+  int levels_A, levels_S, levels_M;
+  int syncs;                  /* host waits on device scalars */
+} scr_stats;
+
+/* Fill o with the defaults listed above.  Never fails for non-NULL o. */
+int scr_default_opts(scr_opts* o);
+
+/* Create a solver context on the current CUDA device.  cuda_stream is a
+   cudaStream_t (NULL: the legacy default stream).  o may be NULL
+   (defaults).  The handle owns all device memory it allocates. */
+int scr_create(scr_handle* h, const scr_opts* o, void* cuda_stream);
+
+/* Free every resource of h (NULL is accepted). */
+int scr_destroy(scr_handle h);
+
+/* Set-up of the block system (Sec. 5.2.1): copies A, B, C, D, forms
+   Shat = D - C diag(A)^{-1} B on the GPU (sparse product), builds the AMG
+   hierarchies of A and Shat.  Shapes: A n_v x n_v (3x3), B n_v x n_p (3x1),
+   C n_p x n_v (1x3), D n_p x n_p (1x1).  SCR_INVALID_ARG on a shape or
+   block-size mismatch, a missing diagonal block of A or a zero diagonal
+   entry of A; SCR_CUDA_ERROR on device failure. */
+int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C,
+              const scr_bsr* D, int ptr_is_device);
+
+/* Solve calA x = b to the outer tolerance (FGMRES + P_SCR, x_0 = 0).
+   b, x: length 3 n_v + n_p.  Returns SCR_NOT_CONVERGED if the outer cap is
+   reached (x = last iterate).  The final relative residual is recomputed in
+   FP64 with calA (scr_residual). */
+int scr_solve(scr_handle h, const double* b, double* x, int ptr_is_device);
+
+/* Iteration counts of the last scr_solve: outer FGMRES and the sum of all
+   intermediate and inner GMRES iterations. */
+int scr_iters(scr_handle h, int* outer, int* inner_total);
+
+/* FP64 ||b - calA x||_2 / ||b||_2 of the last scr_solve. */
+int scr_residual(scr_handle h, double* rel_res);
+
+/* Counters and timings (see scr_stats). */
+int scr_get_stats(scr_handle h, scr_stats* s);
+
+/* Mesh-motion set-up (Sec. 5.2.2): L is n_m x n_m with 1x1 blocks,
+   symmetric positive definite after the Dirichlet rows were made identity;
+   builds the AMG hierarchy of L (applied to the three displacement
+   components). */
+int mm_setup(scr_handle h, const scr_bsr* L, int ptr_is_device);
+
+/* CG + AMG on (L kron I_3) u = g; g, u: length 3 n_m interleaved. */
+int mm_solve(scr_handle h, const double* g, double* u, int ptr_is_device);
+
+/* Iterations and FP64 relative residual of the last mm_solve. */
+int mm_iters(scr_handle h, int* iters, double* rel_res);
+
+/* Message of the last error on this thread ("" if none). */
+const char* scr_last_error(void);
+
+/* ---------------- single steps of the path (device pointers) ----------
+   These run exactly the kernels the solver uses, for parity checks. */
+
+/* y = calA x, the fused block product (Sec. 5.2.1). */
+int scr_apply_op(scr_handle h, const double* x, double* y);
+
+/* y = P_SCR^{-1} r, Algorithm 1 of App. B. */
+int scr_apply_pc(scr_handle h, const double* r, double* y);
+
+/* y_p = S x_p = D x_p - C A^{-1} B x_p, Algorithm 2 of App. B. */
+int scr_apply_schur(scr_handle h, const double* xp, double* yp);
+
+/* x = one V-cycle of hierarchy `which` applied to b (x_0 = 0).  For
+   SCR_HIER_MESH, b and x hold three interleaved components. */
+int scr_amg_apply(scr_handle h, int which, const double* b, double* x);
+
+/* Number of levels of hierarchy `which` (0 if not set up). */
+int scr_amg_levels(scr_handle h, int which, int* n_levels);
+
+/* Copy a level operator, prolongator or the aggregates of a hierarchy to
+   host arrays in the block CSR layout above.  Call once with NULL arrays to
+   receive the sizes, then again with arrays of those sizes. */
+int scr_export(scr_handle h, int which, int level, int kind, scr_bsr_out* out);
+
+/* y = M x for a block matrix given in device memory (any br, bc in {1,3}),
+   on stream cuda_stream, with the same block-row kernel the solver uses.
+   x has nb_cols*bc entries, y nb_rows*br. */
+int scr_bsr_spmv(const scr_bsr* M, const double* x, double* y, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCR_GB300_H */

@@ -1,0 +1,501 @@
+// Vector kernels of the Krylov solvers: deterministic two-stage reductions
+// (fixed grid, per-block partial sums reduced in a fixed order), the two
+// classical Gram-Schmidt passes of FGMRES/GMRES fused with their dot
+// products, Givens rotations of the Hessenberg least-squares problem on the
+// device, and the CG recurrences.
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace scr {
+
+static constexpr int kRedThreads = 256;
+
+Reducer make_reducer(DeviceArena& a) {
+  Reducer r;
+  r.nblk = std::min(2 * sm_count(), 1024);
+  r.partial = a.alloc<double>((size_t)r.nblk * kMaxBasis);
+  return r;
+}
+
+// ------------------------------------------------------------ simple ops
+template <typename T>
+__global__ void k_fill(T* x, T v, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+  for (; i < n; i += st) x[i] = v;
+}
+template <typename T>
+__global__ void k_copy(const T* __restrict__ x, T* __restrict__ y, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+  for (; i < n; i += st) y[i] = x[i];
+}
+__global__ void k_f2d(const float* __restrict__ x, double* __restrict__ y, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+  for (; i < n; i += st) y[i] = (double)x[i];
+}
+__global__ void k_d2f_b(const double* __restrict__ x, float* __restrict__ y, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+  for (; i < n; i += st) y[i] = (float)x[i];
+}
+__global__ void k_axpby(double a, const double* __restrict__ x, double b, double* __restrict__ y, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+  for (; i < n; i += st) y[i] = a * x[i] + b * y[i];
+}
+template <typename T>
+__global__ void k_scale_by(const T* __restrict__ x, const double* __restrict__ sc, T* __restrict__ y, long long n) {
+  const T a = (T)*sc;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+  for (; i < n; i += st) y[i] = a * x[i];
+}
+
+static int grid_for(long long n) {
+  return (int)std::max<long long>(1, std::min<long long>(ceil_div(n, 256), 8LL * sm_count()));
+}
+
+template <typename T>
+void fill(T* x, T v, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_fill<T><<<grid_for(n), 256, 0, s>>>(x, v, n);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+template void fill<double>(double*, double, long long, cudaStream_t);
+template void fill<float>(float*, float, long long, cudaStream_t);
+template void fill<int>(int*, int, long long, cudaStream_t);
+
+template <typename T>
+void copy(const T* x, T* y, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_copy<T><<<grid_for(n), 256, 0, s>>>(x, y, n);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+template void copy<double>(const double*, double*, long long, cudaStream_t);
+template void copy<float>(const float*, float*, long long, cudaStream_t);
+template void copy<int>(const int*, int*, long long, cudaStream_t);
+
+void cast_d2f(const double* x, float* y, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_d2f_b<<<grid_for(n), 256, 0, s>>>(x, y, n);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+void cast_f2d(const float* x, double* y, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_f2d<<<grid_for(n), 256, 0, s>>>(x, y, n);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+void axpby(double a, const double* x, double b, double* y, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_axpby<<<grid_for(n), 256, 0, s>>>(a, x, b, y, n);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+template <typename T>
+void scale_by(const T* x, const double* sc, T* y, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_scale_by<T><<<grid_for(n), 256, 0, s>>>(x, sc, y, n);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
+template void scale_by<double>(const double*, const double*, double*, long long, cudaStream_t);
+
+template <typename T>
+__global__ void k_axpby_t(T a, const T* __restrict__ x, T b, T* __restrict__ y, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+  for (; i < n; i += st) y[i] = a * x[i] + b * y[i];
+}
+template <typename T>
+void axpby_t(double a, const T* x, double b, T* y, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_axpby_t<T><<<grid_for(n), 256, 0, s>>>((T)a, x, (T)b, y, n);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+template void axpby_t<double>(double, const double*, double, double*, long long, cudaStream_t);
+template void axpby_t<float>(double, const float*, double, float*, long long, cudaStream_t);
+
+// x[o*nrhs+h] = b[o*nrhs+h] * d[o]
+template <typename T>
+__global__ void k_diag_scale(const T* __restrict__ b, const T* __restrict__ d, T* __restrict__ x, long long n,
+                             int nrhs) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+  for (; i < n * nrhs; i += st) x[i] = b[i] * d[i / nrhs];
+}
+template <typename T>
+void diag_scale(const T* b, const T* d, T* x, long long n, int nrhs, cudaStream_t s) {
+  if (n <= 0) return;
+  k_diag_scale<T><<<grid_for(n * nrhs), 256, 0, s>>>(b, d, x, n, nrhs);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+template void diag_scale<double>(const double*, const double*, double*, long long, int, cudaStream_t);
+template void diag_scale<float>(const float*, const float*, float*, long long, int, cudaStream_t);
+template void scale_by<float>(const float*, const double*, float*, long long, cudaStream_t);
+
+// ------------------------------------------------------------ reductions
+// Reduce KMAX per-thread sums over the block and write them to
+// partial[blockIdx.x * kMaxBasis + j].
+template <int KMAX>
+__device__ __forceinline__ void block_store_partials(double (&acc)[KMAX], int k, double* partial) {
+  __shared__ double sm[kRedThreads / 32][KMAX];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    if (j < k) {
+      double v = warp_sum(acc[j]);
+      if (lane == 0) sm[wid][j] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double v = 0.0;
+#pragma unroll
+    for (int w = 0; w < kRedThreads / 32; ++w) v += sm[w][threadIdx.x];
+    partial[(long long)blockIdx.x * kMaxBasis + threadIdx.x] = v;
+  }
+}
+
+// partial sums of V_j . w
+// per-thread sums in the vector precision T, block and grid sums in FP64
+template <int KMAX, typename T>
+__device__ __forceinline__ void store_partials_t(T (&acc)[KMAX], int k, double* partial) {
+  double d[KMAX];
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) d[j] = (double)acc[j];
+  block_store_partials<KMAX>(d, k, partial);
+}
+
+template <int KMAX, typename T>
+__global__ void __launch_bounds__(kRedThreads) k_multidot(const T* __restrict__ V, long long ld, int k,
+                                                         const T* __restrict__ w, long long n,
+                                                         double* __restrict__ partial) {
+  T acc[KMAX];
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) acc[j] = (T)0;
+  const long long st = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += st) {
+    const T wi = w[i];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j < k) acc[j] = fma(V[j * ld + i], wi, acc[j]);
+  }
+  store_partials_t<KMAX, T>(acc, k, partial);
+}
+
+// w -= V h; partial sums of V_j . w (new)
+template <int KMAX, typename T>
+__global__ void __launch_bounds__(kRedThreads) k_cgs_update_dot(const T* __restrict__ V, long long ld, int k,
+                                                               const double* __restrict__ h, T* __restrict__ w,
+                                                               long long n, double* __restrict__ partial) {
+  T hj[KMAX], acc[KMAX];
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    hj[j] = j < k ? (T)h[j] : (T)0;
+    acc[j] = (T)0;
+  }
+  const long long st = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += st) {
+    T wi = w[i];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j < k) wi = fma(-V[j * ld + i], hj[j], wi);
+    w[i] = wi;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j < k) acc[j] = fma(V[j * ld + i], wi, acc[j]);
+  }
+  store_partials_t<KMAX, T>(acc, k, partial);
+}
+
+// w -= V h; partial sum of w . w
+template <int KMAX, typename T>
+__global__ void __launch_bounds__(kRedThreads) k_cgs_update_norm(const T* __restrict__ V, long long ld, int k,
+                                                                const double* __restrict__ h, T* __restrict__ w,
+                                                                long long n, double* __restrict__ partial) {
+  T hj[KMAX];
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) hj[j] = j < k ? (T)h[j] : (T)0;
+  T acc[1] = {(T)0};
+  const long long st = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += st) {
+    T wi = w[i];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j < k) wi = fma(-V[j * ld + i], hj[j], wi);
+    w[i] = wi;
+    acc[0] = fma(wi, wi, acc[0]);
+  }
+  store_partials_t<1, T>(acc, 1, partial);
+}
+
+// out[j] = sum_b partial[b][j], fixed order
+__global__ void k_reduce_partials(const double* __restrict__ partial, int nblk, int k, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = wid; j < k; j += nw) {
+    double v = 0.0;
+    for (int b = lane; b < nblk; b += 32) v += partial[(long long)b * kMaxBasis + j];
+    v = warp_sum(v);
+    if (lane == 0) out[j] = v;
+  }
+}
+
+template <int KMAX, typename T>
+static void launch_multidot(const T* V, long long ld, int k, const T* w, long long n, const Reducer& r,
+                            cudaStream_t s) {
+  k_multidot<KMAX, T><<<r.nblk, kRedThreads, 0, s>>>(V, ld, k, w, n, r.partial);
+}
+template <int KMAX, typename T>
+static void launch_cgs_dot(const T* V, long long ld, int k, const double* h, T* w, long long n, const Reducer& r,
+                           cudaStream_t s) {
+  k_cgs_update_dot<KMAX, T><<<r.nblk, kRedThreads, 0, s>>>(V, ld, k, h, w, n, r.partial);
+}
+template <int KMAX, typename T>
+static void launch_cgs_norm(const T* V, long long ld, int k, const double* h, T* w, long long n, const Reducer& r,
+                            cudaStream_t s) {
+  k_cgs_update_norm<KMAX, T><<<r.nblk, kRedThreads, 0, s>>>(V, ld, k, h, w, n, r.partial);
+}
+
+#define SCR_KDISPATCH(FN, T, k, ...)                \
+  do {                                              \
+    if ((k) <= 1) FN<1, T>(__VA_ARGS__);            \
+    else if ((k) <= 4) FN<4, T>(__VA_ARGS__);       \
+    else if ((k) <= 8) FN<8, T>(__VA_ARGS__);       \
+    else if ((k) <= 16) FN<16, T>(__VA_ARGS__);     \
+    else if ((k) <= 32) FN<32, T>(__VA_ARGS__);     \
+    else FN<kMaxBasis, T>(__VA_ARGS__);             \
+  } while (0)
+
+static void reduce(const Reducer& r, int k, double* out, cudaStream_t s) {
+  k_reduce_partials<<<1, 256, 0, s>>>(r.partial, r.nblk, k, out);
+  SCR_LAUNCH();
+  counters().launches += 2;
+}
+
+template <typename T>
+void norm2(const T* x, long long n, double* out, const Reducer& r, cudaStream_t s) {
+  launch_multidot<1, T>(x, 0, 1, x, n, r, s);
+  SCR_LAUNCH();
+  reduce(r, 1, out, s);
+}
+
+template <typename T>
+void multidot(const T* V, long long ld, int k, const T* w, long long n, double* out, const Reducer& r,
+              cudaStream_t s) {
+  SCR_KDISPATCH(launch_multidot, T, k, V, ld, k, w, n, r, s);
+  SCR_LAUNCH();
+  reduce(r, k, out, s);
+}
+
+template <typename T>
+void cgs_update_dot(const T* V, long long ld, int k, const double* h, T* w, long long n, double* out,
+                    const Reducer& r, cudaStream_t s) {
+  SCR_KDISPATCH(launch_cgs_dot, T, k, V, ld, k, h, w, n, r, s);
+  SCR_LAUNCH();
+  reduce(r, k, out, s);
+}
+
+template <typename T>
+void cgs_update_norm(const T* V, long long ld, int k, const double* h, T* w, long long n, double* out,
+                     const Reducer& r, cudaStream_t s) {
+  SCR_KDISPATCH(launch_cgs_norm, T, k, V, ld, k, h, w, n, r, s);
+  SCR_LAUNCH();
+  reduce(r, 1, out, s);
+}
+
+#define SCR_INST_BLAS(T)                                                                                      \
+  template void norm2<T>(const T*, long long, double*, const Reducer&, cudaStream_t);                         \
+  template void multidot<T>(const T*, long long, int, const T*, long long, double*, const Reducer&,           \
+                            cudaStream_t);                                                                    \
+  template void cgs_update_dot<T>(const T*, long long, int, const double*, T*, long long, double*,            \
+                                  const Reducer&, cudaStream_t);                                              \
+  template void cgs_update_norm<T>(const T*, long long, int, const double*, T*, long long, double*,           \
+                                   const Reducer&, cudaStream_t);
+SCR_INST_BLAS(double)
+SCR_INST_BLAS(float)
+
+// ------------------------------------------------------------ Arnoldi scalars
+__global__ void k_arnoldi_finalize(ArnoldiState* st, int j, double* host_rel) {
+  constexpr int ldh = kMaxBasis + 1;
+  double* Hj = st->H + (long long)j * ldh;
+  for (int i = 0; i <= j; ++i) Hj[i] = st->h1[i] + st->h2[i];
+  const double hn = sqrt(fmax(st->nrm2, 0.0));
+  Hj[j + 1] = hn;
+  // previous rotations
+  for (int i = 0; i < j; ++i) {
+    const double t = st->cs[i] * Hj[i] + st->sn[i] * Hj[i + 1];
+    Hj[i + 1] = -st->sn[i] * Hj[i] + st->cs[i] * Hj[i + 1];
+    Hj[i] = t;
+  }
+  const double a = Hj[j], c = Hj[j + 1];
+  const double d = hypot(a, c);
+  double cs = 1.0, sn = 0.0;
+  if (d != 0.0) {
+    cs = a / d;
+    sn = c / d;
+  }
+  st->cs[j] = cs;
+  st->sn[j] = sn;
+  Hj[j] = d;
+  Hj[j + 1] = 0.0;
+  st->g[j + 1] = -sn * st->g[j];
+  st->g[j] = cs * st->g[j];
+  st->rel = fabs(st->g[j + 1]) / st->bnorm;
+  // happy breakdown: the new direction vanished relative to the column
+  st->breakdown = (hn <= 1e-300 || d == 0.0) ? 1 : 0;
+  st->inv_hnext = hn > 1e-300 ? 1.0 / hn : 0.0;
+  host_rel[0] = st->rel;
+  host_rel[1] = (double)st->breakdown;
+}
+
+void arnoldi_finalize(ArnoldiState* st, int j, double* host_rel, cudaStream_t s) {
+  k_arnoldi_finalize<<<1, 1, 0, s>>>(st, j, host_rel);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
+__global__ void k_arnoldi_start(ArnoldiState* st, int first, double* host_rel) {
+  const double beta = sqrt(fmax(st->nrm2, 0.0));
+  st->beta = beta;
+  if (first) st->bnorm = beta;
+  for (int i = 0; i <= kMaxBasis; ++i) st->g[i] = 0.0;
+  st->g[0] = beta;
+  st->inv_hnext = beta > 0.0 ? 1.0 / beta : 0.0;
+  st->rel = st->bnorm > 0.0 ? beta / st->bnorm : 0.0;
+  st->breakdown = 0;
+  host_rel[0] = st->rel;
+  host_rel[1] = st->bnorm;
+}
+
+void arnoldi_start(ArnoldiState* st, int first, double* host_rel, cudaStream_t s) {
+  k_arnoldi_start<<<1, 1, 0, s>>>(st, first, host_rel);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
+__global__ void k_backsolve(ArnoldiState* st, int k) {
+  constexpr int ldh = kMaxBasis + 1;
+  for (int i = k - 1; i >= 0; --i) {
+    double v = st->g[i];
+    for (int l = i + 1; l < k; ++l) v -= st->H[(long long)l * ldh + i] * st->y[l];
+    const double d = st->H[(long long)i * ldh + i];
+    st->y[i] = d != 0.0 ? v / d : 0.0;
+  }
+}
+
+template <int KMAX, typename T>
+__global__ void k_update_x(const ArnoldiState* __restrict__ st, int k, const T* __restrict__ Z, long long ld,
+                           T* __restrict__ x, long long n) {
+  T y[KMAX];
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) y[j] = j < k ? (T)st->y[j] : (T)0;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x, stp = (long long)gridDim.x * blockDim.x;
+  for (; i < n; i += stp) {
+    T v = x[i];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j)
+      if (j < k) v = fma(y[j], Z[j * ld + i], v);
+    x[i] = v;
+  }
+}
+template <int KMAX, typename T>
+static void launch_update_x(const ArnoldiState* st, int k, const T* Z, long long ld, T* x, long long n,
+                            cudaStream_t s) {
+  k_update_x<KMAX, T><<<grid_for(n), 256, 0, s>>>(st, k, Z, ld, x, n);
+}
+
+template <typename T>
+void gmres_update(ArnoldiState* st, int k, const T* Z, long long ld, T* x, long long n, cudaStream_t s) {
+  if (k <= 0) return;
+  k_backsolve<<<1, 1, 0, s>>>(st, k);
+  SCR_LAUNCH();
+  SCR_KDISPATCH(launch_update_x, T, k, st, k, Z, ld, x, n, s);
+  SCR_LAUNCH();
+  counters().launches += 2;
+}
+template void gmres_update<double>(ArnoldiState*, int, const double*, long long, double*, long long, cudaStream_t);
+template void gmres_update<float>(ArnoldiState*, int, const float*, long long, float*, long long, cudaStream_t);
+
+// ------------------------------------------------------------ CG
+__global__ void k_cg_scalar(CgState* st, int mode, double* host_rel) {
+  switch (mode) {
+    case 0:  // start: bnorm2 in rr
+      st->bnorm2 = st->rr;
+      st->rel = st->rr > 0 ? 1.0 : 0.0;
+      if (host_rel) host_rel[0] = st->rel, host_rel[1] = st->bnorm2;
+      break;
+    case 1:  // alpha = rz / pq
+      st->alpha = st->pq != 0.0 ? st->rz / st->pq : 0.0;
+      break;
+    case 2:  // residual estimate
+      st->rel = st->bnorm2 > 0 ? sqrt(st->rr / st->bnorm2) : 0.0;
+      if (host_rel) host_rel[0] = st->rel;
+      break;
+    case 3:  // first rz
+      st->rz = st->rz_new;
+      break;
+    case 4:  // beta = rz_new / rz
+      st->beta = st->rz != 0.0 ? st->rz_new / st->rz : 0.0;
+      st->rz = st->rz_new;
+      break;
+  }
+}
+
+__global__ void k_cg_xr(const CgState* __restrict__ st, const double* __restrict__ p, const double* __restrict__ q,
+                        double* __restrict__ x, double* __restrict__ r, long long n, double* __restrict__ partial) {
+  const double a = st->alpha;
+  double acc[1] = {0.0};
+  const long long stp = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stp) {
+    x[i] = fma(a, p[i], x[i]);
+    const double ri = fma(-a, q[i], r[i]);
+    r[i] = ri;
+    acc[0] = fma(ri, ri, acc[0]);
+  }
+  block_store_partials<1>(acc, 1, partial);
+}
+
+__global__ void k_cg_p(const CgState* __restrict__ st, const double* __restrict__ z, double* __restrict__ p,
+                       long long n) {
+  const double b = st->beta;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x, stp = (long long)gridDim.x * blockDim.x;
+  for (; i < n; i += stp) p[i] = fma(b, p[i], z[i]);
+}
+
+void cg_start(CgState* st, const double* b, long long n, const Reducer& red, double* host_rel, cudaStream_t s) {
+  norm2(b, n, &st->rr, red, s);
+  k_cg_scalar<<<1, 1, 0, s>>>(st, 0, host_rel);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+void cg_dot_rz(CgState* st, const double* r, const double* z, long long n, const Reducer& red, int first,
+               cudaStream_t s) {
+  multidot(r, 0, 1, z, n, &st->rz_new, red, s);
+  k_cg_scalar<<<1, 1, 0, s>>>(st, first ? 3 : 4, nullptr);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+void cg_alpha(CgState* st, const double* p, const double* q, long long n, const Reducer& red, cudaStream_t s) {
+  multidot(p, 0, 1, q, n, &st->pq, red, s);
+  k_cg_scalar<<<1, 1, 0, s>>>(st, 1, nullptr);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+void cg_step_x_r(CgState* st, const double* p, const double* q, double* x, double* r, long long n,
+                 const Reducer& red, double* host_rel, cudaStream_t s) {
+  k_cg_xr<<<red.nblk, kRedThreads, 0, s>>>(st, p, q, x, r, n, red.partial);
+  SCR_LAUNCH();
+  reduce(red, 1, &st->rr, s);
+  k_cg_scalar<<<1, 1, 0, s>>>(st, 2, host_rel);
+  SCR_LAUNCH();
+  counters().launches += 2;
+}
+void cg_update_p(CgState* st, const double* z, double* p, long long n, cudaStream_t s) {
+  k_cg_p<<<grid_for(n), 256, 0, s>>>(st, z, p, n);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
+}  // namespace scr

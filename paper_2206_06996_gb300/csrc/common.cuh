@@ -1,0 +1,95 @@
+// Shared device-side definitions of the SCR-FGMRES + AMG library.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/scr_gb300.h"
+
+namespace scr {
+
+// --------------------------------------------------------------- errors
+struct CudaError {
+  cudaError_t err;
+  const char* where;
+};
+
+#define SCR_CUDA(call)                                         \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) throw ::scr::CudaError{e_, #call};  \
+  } while (0)
+
+#define SCR_LAUNCH() SCR_CUDA(cudaGetLastError())
+
+void set_last_error(const char* fmt, ...);
+
+// --------------------------------------------------------------- matrices
+// Block-sparse matrix on the device in "slab" layout: the blocks of one
+// block row keep the order of col[], and the values of the block row are
+// stored scalar row by scalar row.  For block row i with k = rp[i+1]-rp[i]
+// blocks starting at s = rp[i], entry (r, c) of its t-th block sits at
+//   val[s*BR*BC + r*(k*BC) + t*BC + c].
+// One scalar row of a block row is thus contiguous, so a group of lanes
+// streams it with coalesced loads and one multiply-add per value.
+template <typename T>
+struct DBsr {
+  int nbr = 0, nbc = 0, br = 1, bc = 1;
+  long long nnzb = 0;
+  int* rp = nullptr;
+  int* col = nullptr;
+  T* val = nullptr;
+};
+
+__host__ __device__ inline long long slab_index(int s, int k, int t, int r, int c, int BR, int BC) {
+  return (long long)s * BR * BC + (long long)r * k * BC + (long long)t * BC + c;
+}
+
+// --------------------------------------------------------------- memory
+// Stream-ordered device allocations from a pool that keeps its memory, so
+// repeated set-ups reuse the same blocks without returning to the driver.
+class DeviceArena {
+ public:
+  explicit DeviceArena(cudaStream_t s = 0) : stream_(s) {}
+  ~DeviceArena() { release(); }
+  template <typename T>
+  T* alloc(size_t n) {
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    SCR_CUDA(cudaMallocAsync(&p, n * sizeof(T), stream_));
+    ptrs_.push_back(p);
+    bytes_ += n * sizeof(T);
+    return static_cast<T*>(p);
+  }
+  void release() {
+    for (void* p : ptrs_) cudaFreeAsync(p, stream_);
+    ptrs_.clear();
+    bytes_ = 0;
+  }
+  size_t bytes() const { return bytes_; }
+  void set_stream(cudaStream_t s) { stream_ = s; }
+
+ private:
+  cudaStream_t stream_;
+  std::vector<void*> ptrs_;
+  size_t bytes_ = 0;
+};
+
+void configure_pool(int device);
+
+// --------------------------------------------------------------- helpers
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v, int width = 32) {
+  for (int o = width / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, width);
+  return v;
+}
+
+__device__ __forceinline__ float to_f(double v) { return (float)v; }
+
+// SM count of the current device (cached).
+int sm_count();
+
+}  // namespace scr

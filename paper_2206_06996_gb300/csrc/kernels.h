@@ -1,0 +1,170 @@
+// Host-callable launchers of the device kernels (one translation unit per
+// family: spmv.cu, blas.cu, amg_setup.cu).
+#pragma once
+#include "common.cuh"
+
+namespace scr {
+
+// --------------------------------------------------------------- counters
+struct LaunchCounter {
+  long long launches = 0;
+  long long spmv_bytes = 0;
+};
+LaunchCounter& counters();
+
+// --------------------------------------------------------------- layouts
+// standard BSR values (block after block, row-major) -> slab layout
+template <typename TO>
+void to_slab(const int* rp, const double* std_val, TO* slab_val, int nbr, int br, int bc,
+             long long nnzb, cudaStream_t s);
+// slab -> standard (export)
+void from_slab(const int* rp, const double* slab_val, double* std_val, int nbr, int br, int bc,
+               long long nnzb, cudaStream_t s);
+void from_slab_f(const int* rp, const float* slab_val, double* std_val, int nbr, int br, int bc,
+                 long long nnzb, cudaStream_t s);
+// slab double -> slab float
+void slab_to_float(const double* in, float* out, long long n, cudaStream_t s);
+
+// --------------------------------------------------------------- SpMV
+// Epilogues applied to the row sums acc of M x (scalar output index o,
+// right-hand side h, flat index gi = o*nrhs + h):
+enum class Epi : int {
+  Set = 0,     // y = acc
+  Axpby = 1,   // y = alpha*acc + beta*z
+  Resid = 2,   // y = z - acc
+  Jacobi = 3,  // y = xs + (z - acc) * dinv[o]
+};
+struct EpiArgs {
+  Epi kind = Epi::Set;
+  double alpha = 1.0, beta = 0.0;
+  const void* z = nullptr;     // same precision as y
+  const void* xs = nullptr;    // Jacobi: current iterate
+  const void* dinv = nullptr;  // Jacobi: inverse l1 row sums
+};
+
+// y = epilogue(M x); M in slab layout; x and y of type XT; nrhs interleaved
+// right-hand sides (1 or 3).
+template <typename VT, typename XT>
+void spmv(const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const EpiArgs& e, cudaStream_t s);
+
+// y = epilogue([[A, B], [C, D]] x) in FP64 (the outer operator calA)
+void block_op(const DBsr<double>& A, const DBsr<double>& B, const DBsr<double>& C,
+              const DBsr<double>& D, const double* x, double* y, const double* z, bool resid,
+              cudaStream_t s);
+
+// --------------------------------------------------------------- BLAS-1
+constexpr int kMaxBasis = 64;  // largest restart length + 1
+struct ArnoldiState {           // device-resident Krylov scalars
+  double H[(kMaxBasis + 1) * kMaxBasis];  // column-major, ld = kMaxBasis + 1
+  double cs[kMaxBasis], sn[kMaxBasis], g[kMaxBasis + 1], y[kMaxBasis];
+  double h1[kMaxBasis + 1], h2[kMaxBasis + 1];
+  double beta, bnorm, rel, inv_hnext, nrm2;
+  int breakdown;
+};
+struct Reducer {  // partial-sum scratch for deterministic two-stage reductions
+  double* partial = nullptr;  // [nblk * kMaxBasis]
+  int nblk = 0;
+};
+Reducer make_reducer(DeviceArena& a);
+
+template <typename T>
+void fill(T* x, T v, long long n, cudaStream_t s);
+template <typename T>
+void copy(const T* x, T* y, long long n, cudaStream_t s);
+void cast_d2f(const double* x, float* y, long long n, cudaStream_t s);
+void cast_f2d(const float* x, double* y, long long n, cudaStream_t s);
+// y = a*x + b*y
+void axpby(double a, const double* x, double b, double* y, long long n, cudaStream_t s);
+template <typename T>
+void axpby_t(double a, const T* x, double b, T* y, long long n, cudaStream_t s);
+// x[o*nrhs+h] = b[o*nrhs+h] * d[o]  (l1-Jacobi sweep from a zero iterate)
+template <typename T>
+void diag_scale(const T* b, const T* d, T* x, long long n, int nrhs, cudaStream_t s);
+
+// out = ||x||^2 (device scalar).  Vector kernels take T = double or float;
+// FP32 vectors are summed per thread in FP32, across threads in FP64.
+template <typename T>
+void norm2(const T* x, long long n, double* out, const Reducer& r, cudaStream_t s);
+// out[j] = V_j . w, j < k (V vectors of length n with stride ld)
+template <typename T>
+void multidot(const T* V, long long ld, int k, const T* w, long long n, double* out, const Reducer& r,
+              cudaStream_t s);
+// w -= sum_j V_j h[j]; then out[j] = V_j . w (second Gram-Schmidt pass)
+template <typename T>
+void cgs_update_dot(const T* V, long long ld, int k, const double* h, T* w, long long n, double* out,
+                    const Reducer& r, cudaStream_t s);
+// w -= sum_j V_j h[j]; then out = ||w||^2
+template <typename T>
+void cgs_update_norm(const T* V, long long ld, int k, const double* h, T* w, long long n, double* out,
+                     const Reducer& r, cudaStream_t s);
+// Arnoldi bookkeeping for column j: H(:,j) = h1 + h2, H(j+1,j) = sqrt(nrm2),
+// Givens rotations, residual estimate st->rel = |g_{j+1}| / bnorm, copied
+// to *host_rel (mapped host memory).
+void arnoldi_finalize(ArnoldiState* st, int j, double* host_rel, cudaStream_t s);
+// GMRES start: beta = sqrt(st->nrm2); g = beta e_1; bnorm set when first;
+// writes beta/bnorm to *host_rel
+void arnoldi_start(ArnoldiState* st, int first, double* host_rel, cudaStream_t s);
+// y = x * (*scale) with scale a device scalar
+template <typename T>
+void scale_by(const T* x, const double* scale, T* y, long long n, cudaStream_t s);
+// y = H^{-1} g (k x k upper triangle), then x += sum_j y_j Z_j
+template <typename T>
+void gmres_update(ArnoldiState* st, int k, const T* Z, long long ld, T* x, long long n, cudaStream_t s);
+
+// CG helpers: scalars on the device
+struct CgState {
+  double rz, rz_new, pq, alpha, beta, rr, bnorm2, rel;
+};
+void cg_step_x_r(CgState* st, const double* p, const double* q, double* x, double* r, long long n,
+                 const Reducer& red, double* host_rel, cudaStream_t s);
+void cg_dot_rz(CgState* st, const double* r, const double* z, long long n, const Reducer& red,
+               int first, cudaStream_t s);
+void cg_update_p(CgState* st, const double* z, double* p, long long n, cudaStream_t s);
+void cg_alpha(CgState* st, const double* p, const double* q, long long n, const Reducer& red,
+              cudaStream_t s);
+void cg_start(CgState* st, const double* b, long long n, const Reducer& red, double* host_rel,
+              cudaStream_t s);
+
+// --------------------------------------------------------------- AMG set-up
+// exclusive scan of n ints; returns the total (host sync)
+long long exclusive_scan(const int* in, int* out, int n, DeviceArena& tmp, cudaStream_t s);
+
+// sparse product C = A * B of slab matrices (deterministic); C allocated in arena
+void spgemm(const DBsr<double>& A, const DBsr<double>& B, DBsr<double>& C, DeviceArena& arena,
+            cudaStream_t s);
+// C = alpha A + diag(rowscale) B with the scalar rows of B scaled by
+// rowscale; rowscale == nullptr means C = alpha A - B
+void spadd(const DBsr<double>& A, double alpha, const DBsr<double>& B, const double* rowscale,
+           DBsr<double>& C, DeviceArena& arena, cudaStream_t s);
+// out = diag(d)^{-1} M, sharing M's pattern
+void scale_rows_inv(const DBsr<double>& M, const double* d, DBsr<double>& out, DeviceArena& a, cudaStream_t s);
+// transpose (blocks transposed)
+void transpose(const DBsr<double>& A, DBsr<double>& T, DeviceArena& arena, cudaStream_t s);
+// scalar diagonal of A (n scalar rows); returns false if a diagonal entry is missing/zero
+void diag_scalar(const DBsr<double>& A, double* d, int* bad, cudaStream_t s);
+// 1/ sum_j |a_ij| per scalar row
+void l1_inv(const DBsr<double>& A, double* dinv, cudaStream_t s);
+// max_i sum_j |a_ij| / |a_ii| (device scalar)
+void gershgorin(const DBsr<double>& A, const double* diag, double* out, cudaStream_t s);
+// scale scalar rows of B by -omega(dev)/d_i : out rowscale[n]
+void prolong_rowscale(const double* diag, const double* lambda, double* rowscale, int n,
+                      cudaStream_t s);
+
+struct Aggregation {
+  int* agg = nullptr;  // per block row, -1 = none
+  int n_agg = 0;
+};
+// strength graph + MIS-2 aggregation of the block rows of A
+Aggregation aggregate(const DBsr<double>& A, double theta, DeviceArena& arena, DeviceArena& tmp,
+                      cudaStream_t s, int* mis_rounds);
+// tentative prolongator I_bs / sqrt(|a|)
+void tentative(const int* agg, int nbr, int n_agg, int bs, DBsr<double>& P, DeviceArena& arena,
+               DeviceArena& tmp, cudaStream_t s);
+// dense copy (column-major n x n) and in-place Gauss-Jordan inverse
+void to_dense(const DBsr<double>& A, double* dense, cudaStream_t s);
+void dense_inverse(double* M, double* inv, int n, int* singular, cudaStream_t s);
+// x[i*nrhs+h] = sum_j inv[i + j n] b[j*nrhs+h]
+void dense_apply(const double* inv, const double* b, double* x, int n, int nrhs, cudaStream_t s);
+void dense_apply_f(const float* inv, const float* b, float* x, int n, int nrhs, cudaStream_t s);
+
+}  // namespace scr

@@ -1,0 +1,1133 @@
+// Host drivers of the SCR-FGMRES + AMG path and the C ABI (scr_gb300.h).
+//
+// Outer level (Sec. 5.2.1): FGMRES(m) on calA x = b in FP64, classical
+// Gram-Schmidt applied twice, Givens rotations, x_0 = 0, stop when the
+// recurrence residual drops below rtol and the recomputed FP64 residual
+// confirms it.  Preconditioner: Algorithm 1 of App. B (SCR) with
+// Algorithm 2 for the Schur complement; the intermediate and inner solves
+// are GMRES(m) with AMG V-cycles (P_A = P_I = AMG(A), P_S = AMG(Shat)).  The
+// mesh-motion system (Sec. 5.2.2) uses CG + AMG.  Every arithmetic step runs
+// in the kernels of spmv.cu / blas.cu / amg_setup.cu; the host only orders
+// launches and reads one residual estimate per Krylov iteration (mapped
+// host memory) to decide when to stop.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <new>
+#include <stdexcept>
+#include <string>
+
+#include "kernels.h"
+
+namespace scr {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+void configure_pool(int device) {
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+}
+
+using Clock = std::chrono::steady_clock;
+static double ms_since(Clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+}
+
+// ------------------------------------------------------------ host scalars
+// Two doubles of mapped pinned memory per solver: the device writes the
+// residual estimate there and the host reads it after a stream sync.
+struct HostScalars {
+  double* h = nullptr;
+  double* d = nullptr;
+  HostScalars() {
+    SCR_CUDA(cudaHostAlloc(&h, 4 * sizeof(double), cudaHostAllocMapped));
+    SCR_CUDA(cudaHostGetDevicePointer(&d, h, 0));
+  }
+  ~HostScalars() {
+    if (h) cudaFreeHost(h);
+  }
+  HostScalars(const HostScalars&) = delete;
+  HostScalars& operator=(const HostScalars&) = delete;
+};
+
+// ------------------------------------------------------------ AMG hierarchy
+struct Level {
+  DBsr<double> A, P, R;
+  DBsr<float> Af, Pf, Rf;
+  double* dinv = nullptr;
+  float* dinvf = nullptr;
+  int* agg = nullptr;
+  int n_agg = 0;
+  long long n = 0;  // scalar rows
+  double *b = nullptr, *x = nullptr, *r = nullptr, *t = nullptr;
+  float *bf = nullptr, *xf = nullptr, *rf = nullptr, *tf = nullptr;
+};
+
+template <typename T>
+static const DBsr<T>& pick(const DBsr<double>& d, const DBsr<float>& f);
+template <>
+const DBsr<double>& pick<double>(const DBsr<double>& d, const DBsr<float>&) {
+  return d;
+}
+template <>
+const DBsr<float>& pick<float>(const DBsr<double>&, const DBsr<float>& f) {
+  return f;
+}
+
+static DBsr<float> to_float_copy(const DBsr<double>& M, DeviceArena& a, cudaStream_t s) {
+  DBsr<float> F;
+  F.nbr = M.nbr;
+  F.nbc = M.nbc;
+  F.br = M.br;
+  F.bc = M.bc;
+  F.nnzb = M.nnzb;
+  F.rp = M.rp;
+  F.col = M.col;
+  F.val = a.alloc<float>(M.nnzb * M.br * M.bc + 1);
+  slab_to_float(M.val, F.val, M.nnzb * M.br * M.bc, s);
+  return F;
+}
+
+struct Hierarchy {
+  int bs = 1, nrhs = 1, nu = 1;
+  bool f32 = false;
+  std::vector<Level> lv;
+  double* cinv = nullptr;
+  float* cinvf = nullptr;
+  int nc = 0;
+  int vcycles = 0;
+  int mis_rounds = 0;
+  std::unique_ptr<DeviceArena> arena;
+
+  int n_levels() const { return (int)lv.size(); }
+
+  void build(const DBsr<double>& A0, int bs_, int nrhs_, const scr_opts& o, bool use_f32, cudaStream_t s) {
+    bs = bs_;
+    nrhs = nrhs_;
+    nu = std::max(1, o.amg_nu);
+    f32 = use_f32;
+    lv.clear();
+    arena.reset(new DeviceArena(s));
+    DeviceArena& ar = *arena;
+    DBsr<double> Al = A0;
+    for (;;) {
+      Level L;
+      L.A = Al;
+      L.n = (long long)Al.nbr * bs;
+      L.dinv = ar.alloc<double>(L.n + 1);
+      l1_inv(Al, L.dinv, s);
+      const bool last = Al.nbr <= o.amg_coarse_size || (int)lv.size() + 1 >= o.amg_max_levels;
+      if (!last) {
+        DeviceArena tmp(s);
+        Aggregation ag = aggregate(Al, o.amg_theta, ar, tmp, s, &mis_rounds);
+        if (ag.n_agg > 0 && ag.n_agg < (int)(0.9 * Al.nbr)) {
+          L.agg = ag.agg;
+          L.n_agg = ag.n_agg;
+          DBsr<double> Pt, T, AP, Ac;
+          DeviceArena tmp2(s);
+          tentative(ag.agg, Al.nbr, ag.n_agg, bs, Pt, tmp2, tmp, s);
+          double* d = tmp.alloc<double>(L.n + 1);
+          int* bad = tmp.alloc<int>(1);
+          SCR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+          diag_scalar(Al, d, bad, s);
+          double* lam = tmp.alloc<double>(1);
+          gershgorin(Al, d, lam, s);
+          double* rs = tmp.alloc<double>(L.n + 1);
+          prolong_rowscale(d, lam, rs, (int)L.n, s);
+          spgemm(Al, Pt, T, tmp2, s);
+          spadd(Pt, 1.0, T, rs, L.P, ar, s);
+          transpose(L.P, L.R, ar, s);
+          spgemm(Al, L.P, AP, tmp2, s);
+          spgemm(L.R, AP, Ac, ar, s);
+          SCR_CUDA(cudaStreamSynchronize(s));
+          lv.push_back(L);
+          Al = Ac;
+          continue;
+        }
+      }
+      lv.push_back(L);
+      break;
+    }
+    // coarsest level: dense inverse
+    Level& C = lv.back();
+    nc = (int)C.n;
+    if (nc > 4096) throw CudaError{cudaErrorInvalidValue, "coarsest AMG level too large for a dense inverse"};
+    {
+      DeviceArena tmp(s);
+      double* M = tmp.alloc<double>((size_t)nc * nc + 1);
+      cinv = ar.alloc<double>((size_t)nc * nc + 1);
+      int* sing = tmp.alloc<int>(1);
+      SCR_CUDA(cudaMemsetAsync(sing, 0, sizeof(int), s));
+      to_dense(C.A, M, s);
+      dense_inverse(M, cinv, nc, sing, s);
+      int hs = 0;
+      SCR_CUDA(cudaMemcpyAsync(&hs, sing, sizeof(int), cudaMemcpyDeviceToHost, s));
+      SCR_CUDA(cudaStreamSynchronize(s));
+      if (hs) throw CudaError{cudaErrorInvalidValue, "singular coarsest AMG operator"};
+    }
+    // work vectors and FP32 copies
+    for (size_t l = 0; l < lv.size(); ++l) {
+      Level& L = lv[l];
+      const long long m = L.n * nrhs + 1;
+      if (!f32) {
+        L.b = ar.alloc<double>(m);
+        L.x = ar.alloc<double>(m);
+        L.r = ar.alloc<double>(m);
+        L.t = ar.alloc<double>(m);
+      } else {
+        L.Af = to_float_copy(L.A, ar, s);
+        if (L.P.nbr) {
+          L.Pf = to_float_copy(L.P, ar, s);
+          L.Rf = to_float_copy(L.R, ar, s);
+        }
+        L.dinvf = ar.alloc<float>(L.n + 1);
+        cast_d2f(L.dinv, L.dinvf, L.n, s);
+        L.bf = ar.alloc<float>(m);
+        L.xf = ar.alloc<float>(m);
+        L.rf = ar.alloc<float>(m);
+        L.tf = ar.alloc<float>(m);
+      }
+    }
+    if (f32) {
+      cinvf = ar.alloc<float>((size_t)nc * nc + 1);
+      cast_d2f(cinv, cinvf, (long long)nc * nc, s);
+    }
+    SCR_CUDA(cudaStreamSynchronize(s));
+  }
+
+  template <typename T>
+  T* vb(Level& L) {
+    if constexpr (sizeof(T) == 8) return L.b; else return L.bf;
+  }
+  template <typename T>
+  T* vr(Level& L) {
+    if constexpr (sizeof(T) == 8) return L.r; else return L.rf;
+  }
+  template <typename T>
+  T* vt(Level& L) {
+    if constexpr (sizeof(T) == 8) return L.t; else return L.tf;
+  }
+  template <typename T>
+  T* vx(Level& L) {
+    if constexpr (sizeof(T) == 8) return L.x; else return L.xf;
+  }
+  template <typename T>
+  const T* dv(Level& L) {
+    if constexpr (sizeof(T) == 8) return L.dinv; else return L.dinvf;
+  }
+
+  // out = V-cycle(b) at level l, starting from a zero iterate
+  template <typename T>
+  void cycle(int l, const T* b, T* out, cudaStream_t s) {
+    Level& L = lv[l];
+    if (l == n_levels() - 1) {
+      if constexpr (sizeof(T) == 8) dense_apply(cinv, b, out, nc, nrhs, s);
+      else dense_apply_f(cinvf, b, out, nc, nrhs, s);
+      return;
+    }
+    const DBsr<T>& A = pick<T>(L.A, L.Af);
+    const DBsr<T>& P = pick<T>(L.P, L.Pf);
+    const DBsr<T>& R = pick<T>(L.R, L.Rf);
+    const T* dinv = dv<T>(L);
+    T* tb = vt<T>(L);
+    // 2 nu - 1 out-of-place sweeps follow the first, so starting in the
+    // scratch buffer leaves the result in out
+    T* cur = tb;
+    T* oth = out;
+    diag_scale<T>(b, dinv, cur, L.n, nrhs, s);
+    EpiArgs jac;
+    jac.kind = Epi::Jacobi;
+    jac.z = b;
+    jac.dinv = dinv;
+    for (int it = 1; it < nu; ++it) {
+      jac.xs = cur;
+      spmv<T, T>(A, cur, oth, nrhs, jac, s);
+      std::swap(cur, oth);
+    }
+    EpiArgs res;
+    res.kind = Epi::Resid;
+    res.z = b;
+    T* r = vr<T>(L);
+    spmv<T, T>(A, cur, r, nrhs, res, s);
+    Level& Lc = lv[l + 1];
+    T* bc = vb<T>(Lc);
+    spmv<T, T>(R, r, bc, nrhs, EpiArgs(), s);
+    T* xc = vx<T>(Lc);
+    cycle<T>(l + 1, bc, xc, s);
+    EpiArgs pro;
+    pro.kind = Epi::Axpby;
+    pro.alpha = 1.0;
+    pro.beta = 1.0;
+    pro.z = cur;
+    spmv<T, T>(P, xc, cur, nrhs, pro, s);
+    for (int it = 0; it < nu; ++it) {
+      jac.xs = cur;
+      spmv<T, T>(A, cur, oth, nrhs, jac, s);
+      std::swap(cur, oth);
+    }
+    if (cur != out) copy<T>(cur, out, L.n * nrhs, s);
+  }
+
+  template <typename T>
+  void apply(const T* b, T* x, cudaStream_t s) {
+    ++vcycles;
+    cycle<T>(0, b, x, s);
+  }
+};
+
+// ------------------------------------------------------------ GMRES
+template <typename T>
+struct Gmres {
+  int m = 0;
+  long long n = 0;
+  T *V = nullptr, *Z = nullptr, *w = nullptr;
+  ArnoldiState* st = nullptr;
+  HostScalars hs;
+  int syncs = 0;
+
+  void init(DeviceArena& a, long long n_, int m_) {
+    n = n_;
+    m = std::max(1, std::min(m_, kMaxBasis - 1));
+    V = a.alloc<T>((size_t)(m + 1) * n + 1);
+    Z = a.alloc<T>((size_t)m * n + 1);
+    w = a.alloc<T>(n + 1);
+    st = a.alloc<ArnoldiState>(1);
+  }
+
+  using Op = std::function<void(const T*, T*)>;
+
+  // returns true when converged; iters/rel report the work done
+  bool solve(const Op& op, const Op* pc, const T* b, T* x, double tol, int maxit, const Reducer& red,
+             cudaStream_t s, int* iters, double* rel, const std::function<double(const T*)>* true_rel = nullptr) {
+    fill<T>(x, (T)0, n, s);
+    norm2<T>(b, n, &st->nrm2, red, s);
+    arnoldi_start(st, 1, hs.d, s);
+    SCR_CUDA(cudaStreamSynchronize(s));
+    ++syncs;
+    *iters = 0;
+    *rel = 0.0;
+    if (!(hs.h[1] > 0.0)) return true;  // b = 0 -> x = 0
+    if (!std::isfinite(hs.h[1])) {
+      *rel = hs.h[1];
+      return false;
+    }
+    scale_by<T>(b, &st->inv_hnext, V, n, s);
+    for (;;) {
+      int k = 0;
+      bool stop = false, breakdown = false;
+      double r = 1.0;
+      for (int j = 0; j < m; ++j) {
+        T* vj = V + (size_t)j * n;
+        T* zj = Z + (size_t)j * n;
+        if (pc) (*pc)(vj, zj);
+        else copy<T>(vj, zj, n, s);
+        op(zj, w);
+        multidot<T>(V, n, j + 1, w, n, st->h1, red, s);
+        cgs_update_dot<T>(V, n, j + 1, st->h1, w, n, st->h2, red, s);
+        cgs_update_norm<T>(V, n, j + 1, st->h2, w, n, &st->nrm2, red, s);
+        arnoldi_finalize(st, j, hs.d, s);
+        scale_by<T>(w, &st->inv_hnext, V + (size_t)(j + 1) * n, n, s);
+        SCR_CUDA(cudaStreamSynchronize(s));
+        ++syncs;
+        r = hs.h[0];
+        breakdown = hs.h[1] != 0.0;
+        ++*iters;
+        k = j + 1;
+        if (!std::isfinite(r)) {
+          *rel = r;
+          return false;
+        }
+        if (r <= tol || *iters >= maxit || breakdown) {
+          stop = true;
+          break;
+        }
+      }
+      gmres_update<T>(st, k, Z, n, x, n, s);
+      *rel = r;
+      if (r <= tol || breakdown) {
+        if (!true_rel) return r <= tol || breakdown;
+        const double tr = (*true_rel)(x);
+        *rel = tr;
+        if (tr <= tol) return true;
+        if (*iters >= maxit) return false;
+      } else if (*iters >= maxit) {
+        return false;
+      }
+      (void)stop;
+      // restart from the current residual r = b - op(x)
+      op(x, w);
+      axpby_t<T>(1.0, b, -1.0, w, n, s);
+      norm2<T>(w, n, &st->nrm2, red, s);
+      arnoldi_start(st, 0, hs.d, s);
+      scale_by<T>(w, &st->inv_hnext, V, n, s);
+    }
+  }
+};
+
+}  // namespace scr
+
+using namespace scr;
+
+// ------------------------------------------------------------ context
+struct scr_ctx {
+  scr_opts o;
+  cudaStream_t s = nullptr;
+  int device = 0;
+  std::unique_ptr<DeviceArena> mats;   // A, B, C, D, Shat and their FP32 copies
+  std::unique_ptr<DeviceArena> work;   // Krylov workspaces
+  std::unique_ptr<DeviceArena> mwork;  // mesh workspaces
+  std::unique_ptr<DeviceArena> mmats;
+  DBsr<double> A, B, C, D, Shat, L;
+  DBsr<float> Af, Bf, Cf, Df;
+  Hierarchy hA, hS, hM;
+  Reducer red, mred;
+  int nv = 0, np = 0, nm = 0;
+  bool have_block = false, have_mesh = false;
+  // outer (FP64) and preconditioner workspaces (FP64 or FP32)
+  Gmres<double> gOuter;
+  Gmres<double> gA, gS, gI;
+  Gmres<float> gAf, gSf, gIf;
+  double *bvec = nullptr, *xvec = nullptr, *rvec = nullptr;
+  double *yhat = nullptr, *rp2 = nullptr, *rv2 = nullptr, *xbar = nullptr, *xt = nullptr;
+  float *pr = nullptr, *py = nullptr, *yhatf = nullptr, *rp2f = nullptr, *rv2f = nullptr, *xbarf = nullptr,
+        *xtf = nullptr;
+  // mesh CG
+  double *mb = nullptr, *mx = nullptr, *mr = nullptr, *mz = nullptr, *mp = nullptr, *mq = nullptr;
+  CgState* cg = nullptr;
+  HostScalars mhs;
+  scr_stats stats;
+  int counters_outer = 0;
+};
+
+namespace {
+
+void check_bsr(const scr_bsr* M, int br, int bc, int nbr, int nbc, const char* name) {
+  if (!M) throw std::invalid_argument(std::string(name) + ": NULL matrix");
+  if (M->br != br || M->bc != bc)
+    throw std::invalid_argument(std::string(name) + ": wrong block size");
+  if (M->nb_rows != nbr || M->nb_cols != nbc) throw std::invalid_argument(std::string(name) + ": wrong shape");
+  if (M->nb_rows < 0 || M->nnzb < 0) throw std::invalid_argument(std::string(name) + ": negative size");
+  if (!M->row_ptr || (M->nnzb > 0 && (!M->col_idx || !M->val)))
+    throw std::invalid_argument(std::string(name) + ": NULL array");
+}
+
+__global__ void k_check_cols(int nbr, int nbc, const int* __restrict__ rp, const int* __restrict__ col,
+                             long long nnzb, int* __restrict__ bad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbr) return;
+  const int s = rp[i], e = rp[i + 1];
+  if (s < 0 || e < s || e > nnzb) {
+    atomicExch(bad, 1);
+    return;
+  }
+  for (int t = s; t < e; ++t) {
+    const int c = col[t];
+    if (c < 0 || c >= nbc || (t > s && col[t - 1] >= c)) atomicExch(bad, 1);
+  }
+}
+
+// copy a caller matrix to the device in slab layout (FP64)
+DBsr<double> upload(const scr_bsr* M, int dev_ptr, DeviceArena& a, cudaStream_t s) {
+  DBsr<double> D;
+  D.nbr = M->nb_rows;
+  D.nbc = M->nb_cols;
+  D.br = M->br;
+  D.bc = M->bc;
+  D.nnzb = M->nnzb;
+  const size_t nv = (size_t)M->nnzb * M->br * M->bc;
+  D.rp = a.alloc<int>(M->nb_rows + 1);
+  D.col = a.alloc<int>(M->nnzb + 1);
+  D.val = a.alloc<double>(nv + 1);
+  const cudaMemcpyKind k = dev_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  SCR_CUDA(cudaMemcpyAsync(D.rp, M->row_ptr, sizeof(int) * (M->nb_rows + 1), k, s));
+  if (M->nnzb > 0) SCR_CUDA(cudaMemcpyAsync(D.col, M->col_idx, sizeof(int) * M->nnzb, k, s));
+  DeviceArena tmp(s);
+  // validate the index arrays before any kernel indexes with them
+  int* bad = tmp.alloc<int>(1);
+  SCR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  if (D.nbr > 0) {
+    k_check_cols<<<ceil_div(D.nbr, 256), 256, 0, s>>>(D.nbr, D.nbc, D.rp, D.col, D.nnzb, bad);
+    SCR_LAUNCH();
+  }
+  int hb = 0;
+  SCR_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SCR_CUDA(cudaStreamSynchronize(s));
+  if (hb) throw std::invalid_argument("row_ptr/col_idx invalid (range, order or duplicates)");
+  const double* src = M->val;
+  if (!dev_ptr && nv > 0) {
+    double* t = tmp.alloc<double>(nv);
+    SCR_CUDA(cudaMemcpyAsync(t, M->val, sizeof(double) * nv, k, s));
+    src = t;
+  }
+  if (nv > 0) to_slab<double>(D.rp, src, D.val, D.nbr, D.br, D.bc, D.nnzb, s);
+  SCR_CUDA(cudaStreamSynchronize(s));
+  return D;
+}
+
+DBsr<float> float_copy(const DBsr<double>& M, DeviceArena& a, cudaStream_t s) {
+  DBsr<float> F;
+  F.nbr = M.nbr;
+  F.nbc = M.nbc;
+  F.br = M.br;
+  F.bc = M.bc;
+  F.nnzb = M.nnzb;
+  F.rp = M.rp;
+  F.col = M.col;
+  F.val = a.alloc<float>(M.nnzb * M.br * M.bc + 1);
+  slab_to_float(M.val, F.val, M.nnzb * M.br * M.bc, s);
+  return F;
+}
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    f();
+    return SCR_OK;
+  } catch (const CudaError& e) {
+    set_last_error("CUDA error %s in %s", cudaGetErrorString(e.err), e.where ? e.where : "?");
+    cudaGetLastError();
+    return e.err == cudaErrorInvalidValue ? SCR_INVALID_ARG : SCR_CUDA_ERROR;
+  } catch (const std::invalid_argument& e) {
+    set_last_error("%s", e.what());
+    return SCR_INVALID_ARG;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    return SCR_CUDA_ERROR;
+  } catch (const std::exception& e) {
+    set_last_error("%s", e.what());
+    return SCR_CUDA_ERROR;
+  }
+}
+
+// ---- the operators of the path, in precision T ----
+template <typename T>
+struct PcView {
+  const DBsr<T>*A, *B, *C, *D;
+  Hierarchy *hA, *hS;
+  Gmres<T>*gA, *gS, *gI;
+  T *yhat, *rp2, *rv2, *xbar, *xt;
+};
+
+PcView<double> view64(scr_ctx* h) {
+  return PcView<double>{&h->A, &h->B, &h->C, &h->D, &h->hA, &h->hS, &h->gA, &h->gS, &h->gI,
+                        h->yhat, h->rp2, h->rv2, h->xbar, h->xt};
+}
+PcView<float> view32(scr_ctx* h) {
+  return PcView<float>{&h->Af, &h->Bf, &h->Cf, &h->Df, &h->hA, &h->hS, &h->gAf, &h->gSf, &h->gIf,
+                       h->yhatf, h->rp2f, h->rv2f, h->xbarf, h->xtf};
+}
+
+// Algorithm 2: y_p = D x_p - C A^{-1} (B x_p), A^{-1} by inner GMRES + P_I
+template <typename T>
+void apply_S(scr_ctx* h, PcView<T>& v, const T* xp, T* yp) {
+  cudaStream_t s = h->s;
+  spmv<T, T>(*v.B, xp, v.xbar, 1, EpiArgs(), s);
+  typename Gmres<T>::Op opA = [&](const T* x, T* y) { spmv<T, T>(*v.A, x, y, 1, EpiArgs(), s); };
+  typename Gmres<T>::Op pcA = [&](const T* b, T* x) { v.hA->template apply<T>(b, x, s); };
+  int it = 0;
+  double rel = 0;
+  v.gI->solve(opA, &pcA, v.xbar, v.xt, h->o.rtol_I, h->o.max_I, h->red, s, &it, &rel);
+  h->stats.i_iters += it;
+  spmv<T, T>(*v.D, xp, yp, 1, EpiArgs(), s);
+  EpiArgs sub;
+  sub.kind = Epi::Axpby;
+  sub.alpha = -1.0;
+  sub.beta = 1.0;
+  sub.z = yp;
+  spmv<T, T>(*v.C, v.xt, yp, 1, sub, s);
+}
+
+// Algorithm 1: y = P_SCR^{-1} r
+template <typename T>
+void apply_pc(scr_ctx* h, PcView<T>& v, const T* r, T* y) {
+  cudaStream_t s = h->s;
+  const long long nv3 = 3LL * h->nv;
+  const T* rv = r;
+  const T* rp = r + nv3;
+  T* yv = y;
+  T* yp = y + nv3;
+  typename Gmres<T>::Op opA = [&](const T* x, T* o) { spmv<T, T>(*v.A, x, o, 1, EpiArgs(), s); };
+  typename Gmres<T>::Op pcA = [&](const T* b, T* x) { v.hA->template apply<T>(b, x, s); };
+  typename Gmres<T>::Op opS = [&](const T* x, T* o) { apply_S<T>(h, v, x, o); };
+  typename Gmres<T>::Op pcS = [&](const T* b, T* x) { v.hS->template apply<T>(b, x, s); };
+  int it = 0;
+  double rel = 0;
+  // 1. A yhat_v = r_v
+  v.gA->solve(opA, &pcA, rv, v.yhat, h->o.rtol_A, h->o.max_A, h->red, s, &it, &rel);
+  h->stats.a_solves++;
+  h->stats.a_iters += it;
+  // 2. r_p <- r_p - C yhat_v
+  EpiArgs e;
+  e.kind = Epi::Axpby;
+  e.alpha = -1.0;
+  e.beta = 1.0;
+  e.z = rp;
+  spmv<T, T>(*v.C, v.yhat, v.rp2, 1, e, s);
+  // 3. S y_p = r_p
+  v.gS->solve(opS, &pcS, v.rp2, yp, h->o.rtol_S, h->o.max_S, h->red, s, &it, &rel);
+  h->stats.s_iters += it;
+  // 4. r_v <- r_v - B y_p
+  e.z = rv;
+  spmv<T, T>(*v.B, yp, v.rv2, 1, e, s);
+  // 5. A y_v = r_v
+  v.gA->solve(opA, &pcA, v.rv2, yv, h->o.rtol_A, h->o.max_A, h->red, s, &it, &rel);
+  h->stats.a_solves++;
+  h->stats.a_iters += it;
+}
+
+void apply_pc_any(scr_ctx* h, const double* r, double* y) {
+  if (h->o.precision == SCR_MIXED) {
+    const long long n = 3LL * h->nv + h->np;
+    cast_d2f(r, h->pr, n, h->s);
+    PcView<float> v = view32(h);
+    apply_pc<float>(h, v, h->pr, h->py);
+    cast_f2d(h->py, y, n, h->s);
+  } else {
+    PcView<double> v = view64(h);
+    apply_pc<double>(h, v, r, y);
+  }
+}
+
+double true_rel_block(scr_ctx* h, const double* b, const double* x) {
+  const long long n = 3LL * h->nv + h->np;
+  block_op(h->A, h->B, h->C, h->D, x, h->rvec, b, true, h->s);
+  ArnoldiState* st = h->gOuter.st;
+  norm2<double>(h->rvec, n, &st->nrm2, h->red, h->s);
+  double r2 = 0, b2 = 0;
+  SCR_CUDA(cudaMemcpyAsync(&r2, &st->nrm2, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  norm2<double>(b, n, &st->nrm2, h->red, h->s);
+  SCR_CUDA(cudaMemcpyAsync(&b2, &st->nrm2, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  SCR_CUDA(cudaStreamSynchronize(h->s));
+  return b2 > 0 ? std::sqrt(r2 / b2) : std::sqrt(r2);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ C ABI
+extern "C" {
+
+const char* scr_last_error(void) { return g_last_error.c_str(); }
+
+int scr_default_opts(scr_opts* o) {
+  if (!o) return SCR_INVALID_ARG;
+  memset(o, 0, sizeof(*o));
+  o->rtol = 1e-8;
+  o->max_it = 200;
+  o->restart = 30;
+  o->rtol_A = o->rtol_S = o->rtol_I = 1e-3;
+  o->max_A = o->max_S = o->max_I = 200;
+  o->restart_inner = 30;
+  o->precision = SCR_FP64;
+  o->precond = 0;
+  o->amg_theta = 0.08;
+  o->amg_max_levels = 10;
+  o->amg_coarse_size = 64;
+  o->amg_nu = 1;
+  o->mm_rtol = 1e-8;
+  o->mm_max_it = 500;
+  o->verbose = 0;
+  return SCR_OK;
+}
+
+int scr_create(scr_handle* out, const scr_opts* o, void* stream) {
+  if (!out) {
+    set_last_error("scr_create: NULL handle pointer");
+    return SCR_INVALID_ARG;
+  }
+  *out = nullptr;
+  return guarded([&] {
+    scr_opts def;
+    scr_default_opts(&def);
+    const scr_opts& op = o ? *o : def;
+    if (op.restart < 1 || op.restart >= kMaxBasis || op.restart_inner < 1 || op.restart_inner >= kMaxBasis)
+      throw std::invalid_argument("restart lengths must lie in [1, 63]");
+    if (op.precision != SCR_FP64 && op.precision != SCR_MIXED) throw std::invalid_argument("unknown precision");
+    if (op.precond != 0) throw std::invalid_argument("only the SCR preconditioner (precond = 0) is built");
+    std::unique_ptr<scr_ctx> h(new scr_ctx());
+    h->o = op;
+    h->s = static_cast<cudaStream_t>(stream);
+    SCR_CUDA(cudaGetDevice(&h->device));
+    configure_pool(h->device);
+    h->work.reset(new DeviceArena(h->s));
+    h->mwork.reset(new DeviceArena(h->s));
+    h->red = make_reducer(*h->work);
+    h->mred = make_reducer(*h->mwork);
+    memset(&h->stats, 0, sizeof(h->stats));
+    *out = h.release();
+  });
+}
+
+int scr_destroy(scr_handle h) {
+  if (!h) return SCR_OK;
+  return guarded([&] {
+    cudaStreamSynchronize(h->s);
+    delete h;
+  });
+}
+
+int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C, const scr_bsr* D, int dev) {
+  if (!h) return SCR_INVALID_ARG;
+  return guarded([&] {
+    auto t0 = Clock::now();
+    if (!A || !D) throw std::invalid_argument("NULL matrix");
+    const int nv = A->nb_rows;
+    const int np = D->nb_rows;
+    check_bsr(A, 3, 3, nv, nv, "A");
+    check_bsr(B, 3, 1, nv, np, "B");
+    check_bsr(C, 1, 3, np, nv, "C");
+    check_bsr(D, 1, 1, np, np, "D");
+    cudaStream_t s = h->s;
+    SCR_CUDA(cudaStreamSynchronize(s));
+    h->have_block = false;
+    h->hA = Hierarchy();
+    h->hS = Hierarchy();
+    h->work.reset();
+    h->mats.reset(new DeviceArena(s));
+    DeviceArena& a = *h->mats;
+    h->nv = nv;
+    h->np = np;
+    h->A = upload(A, dev, a, s);
+    h->B = upload(B, dev, a, s);
+    h->C = upload(C, dev, a, s);
+    h->D = upload(D, dev, a, s);
+    // Shat = D - C diag(A)^{-1} B  (Sec. 5.2.1)
+    {
+      DeviceArena tmp(s);
+      double* d = tmp.alloc<double>(3LL * nv + 1);
+      int* bad = tmp.alloc<int>(1);
+      SCR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+      diag_scalar(h->A, d, bad, s);
+      int hb = 0;
+      SCR_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+      SCR_CUDA(cudaStreamSynchronize(s));
+      if (hb) throw std::invalid_argument("A has a missing or zero diagonal entry");
+      DBsr<double> Bs, T;
+      scale_rows_inv(h->B, d, Bs, tmp, s);
+      spgemm(h->C, Bs, T, tmp, s);
+      spadd(h->D, 1.0, T, nullptr, h->Shat, a, s);
+      SCR_CUDA(cudaStreamSynchronize(s));
+    }
+    const bool f32 = h->o.precision == SCR_MIXED;
+    h->hA.build(h->A, 3, 1, h->o, f32, s);
+    h->hS.build(h->Shat, 1, 1, h->o, f32, s);
+    // workspaces
+    h->work.reset(new DeviceArena(s));
+    DeviceArena& w = *h->work;
+    h->red = make_reducer(w);
+    const long long n = 3LL * nv + np, nv3 = 3LL * nv;
+    h->gOuter.init(w, n, h->o.restart);
+    h->bvec = w.alloc<double>(n + 1);
+    h->xvec = w.alloc<double>(n + 1);
+    h->rvec = w.alloc<double>(n + 1);
+    if (f32) {
+      h->Af = float_copy(h->A, a, s);
+      h->Bf = float_copy(h->B, a, s);
+      h->Cf = float_copy(h->C, a, s);
+      h->Df = float_copy(h->D, a, s);
+      h->gAf.init(w, nv3, h->o.restart_inner);
+      h->gSf.init(w, np, h->o.restart_inner);
+      h->gIf.init(w, nv3, h->o.restart_inner);
+      h->pr = w.alloc<float>(n + 1);
+      h->py = w.alloc<float>(n + 1);
+      h->yhatf = w.alloc<float>(nv3 + 1);
+      h->rv2f = w.alloc<float>(nv3 + 1);
+      h->xbarf = w.alloc<float>(nv3 + 1);
+      h->xtf = w.alloc<float>(nv3 + 1);
+      h->rp2f = w.alloc<float>(np + 1);
+    } else {
+      h->gA.init(w, nv3, h->o.restart_inner);
+      h->gS.init(w, np, h->o.restart_inner);
+      h->gI.init(w, nv3, h->o.restart_inner);
+      h->yhat = w.alloc<double>(nv3 + 1);
+      h->rv2 = w.alloc<double>(nv3 + 1);
+      h->xbar = w.alloc<double>(nv3 + 1);
+      h->xt = w.alloc<double>(nv3 + 1);
+      h->rp2 = w.alloc<double>(np + 1);
+    }
+    SCR_CUDA(cudaStreamSynchronize(s));
+    h->have_block = true;
+    h->stats.levels_A = h->hA.n_levels();
+    h->stats.levels_S = h->hS.n_levels();
+    h->stats.setup_ms = ms_since(t0);
+  });
+}
+
+static void reset_solve_stats(scr_ctx* h) {
+  h->stats.outer_iters = h->stats.a_solves = h->stats.a_iters = h->stats.s_iters = h->stats.i_iters = 0;
+  h->hA.vcycles = h->hS.vcycles = 0;
+  h->gOuter.syncs = h->gA.syncs = h->gS.syncs = h->gI.syncs = 0;
+  h->gAf.syncs = h->gSf.syncs = h->gIf.syncs = 0;
+}
+
+static int solve_impl(scr_ctx* h, const double* b, double* x) {
+  const long long n = 3LL * h->nv + h->np;
+  reset_solve_stats(h);
+  Gmres<double>::Op op = [&](const double* xi, double* y) {
+    block_op(h->A, h->B, h->C, h->D, xi, y, nullptr, false, h->s);
+  };
+  Gmres<double>::Op pc = [&](const double* r, double* y) { apply_pc_any(h, r, y); };
+  std::function<double(const double*)> tr = [&](const double* xi) { return true_rel_block(h, b, xi); };
+  int it = 0;
+  double rel = 0;
+  const bool ok = h->gOuter.solve(op, &pc, b, x, h->o.rtol, h->o.max_it, h->red, h->s, &it, &rel, &tr);
+  h->stats.outer_iters = it;
+  h->stats.rel_res = true_rel_block(h, b, x);
+  h->stats.vcycles_A = h->hA.vcycles;
+  h->stats.vcycles_S = h->hS.vcycles;
+  h->stats.syncs = h->gOuter.syncs + h->gA.syncs + h->gS.syncs + h->gI.syncs + h->gAf.syncs + h->gSf.syncs +
+                   h->gIf.syncs;
+  (void)n;
+  if (!std::isfinite(h->stats.rel_res)) return SCR_NOT_CONVERGED;
+  return (ok && h->stats.rel_res <= h->o.rtol) ? SCR_OK : SCR_NOT_CONVERGED;
+}
+
+int scr_solve(scr_handle h, const double* b, double* x, int dev) {
+  if (!h || !b || !x) return SCR_INVALID_ARG;
+  if (!h->have_block) {
+    set_last_error("scr_solve before scr_setup");
+    return SCR_INVALID_ARG;
+  }
+  int status = SCR_OK;
+  int rc = guarded([&] {
+    auto t0 = Clock::now();
+    const long long n = 3LL * h->nv + h->np;
+    const double* bd = b;
+    double* xd = x;
+    if (!dev) {
+      SCR_CUDA(cudaMemcpyAsync(h->bvec, b, sizeof(double) * n, cudaMemcpyHostToDevice, h->s));
+      bd = h->bvec;
+      xd = h->xvec;
+    }
+    status = solve_impl(h, bd, xd);
+    if (!dev) SCR_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
+    SCR_CUDA(cudaStreamSynchronize(h->s));
+    h->stats.solve_ms = ms_since(t0);
+  });
+  if (rc != SCR_OK) return rc;
+  if (status == SCR_NOT_CONVERGED)
+    set_last_error("FGMRES stopped at %d iterations with relative residual %.3e", h->stats.outer_iters,
+                   h->stats.rel_res);
+  return status;
+}
+
+int scr_iters(scr_handle h, int* outer, int* inner_total) {
+  if (!h) return SCR_INVALID_ARG;
+  if (outer) *outer = h->stats.outer_iters;
+  if (inner_total) *inner_total = h->stats.a_iters + h->stats.s_iters + h->stats.i_iters;
+  return SCR_OK;
+}
+
+int scr_residual(scr_handle h, double* rel) {
+  if (!h || !rel) return SCR_INVALID_ARG;
+  *rel = h->stats.rel_res;
+  return SCR_OK;
+}
+
+int scr_get_stats(scr_handle h, scr_stats* st) {
+  if (!h || !st) return SCR_INVALID_ARG;
+  *st = h->stats;
+  st->kernel_launches = counters().launches;
+  st->spmv_bytes = counters().spmv_bytes;
+  st->levels_M = h->hM.n_levels();
+  return SCR_OK;
+}
+
+int mm_setup(scr_handle h, const scr_bsr* L, int dev) {
+  if (!h) return SCR_INVALID_ARG;
+  return guarded([&] {
+    auto t0 = Clock::now();
+    if (!L) throw std::invalid_argument("L: NULL matrix");
+    check_bsr(L, 1, 1, L->nb_rows, L->nb_rows, "L");
+    cudaStream_t s = h->s;
+    SCR_CUDA(cudaStreamSynchronize(s));
+    h->have_mesh = false;
+    h->hM = Hierarchy();
+    h->mwork.reset();
+    h->mmats.reset(new DeviceArena(s));
+    h->nm = L->nb_rows;
+    h->L = upload(L, dev, *h->mmats, s);
+    {
+      DeviceArena tmp(s);
+      double* d = tmp.alloc<double>(h->nm + 1);
+      int* bad = tmp.alloc<int>(1);
+      SCR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+      diag_scalar(h->L, d, bad, s);
+      int hb = 0;
+      SCR_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+      SCR_CUDA(cudaStreamSynchronize(s));
+      if (hb) throw std::invalid_argument("L has a missing or zero diagonal entry");
+    }
+    scr_opts o = h->o;
+    h->hM.build(h->L, 1, 3, o, false, s);
+    h->mwork.reset(new DeviceArena(s));
+    DeviceArena& w = *h->mwork;
+    h->mred = make_reducer(w);
+    const long long n = 3LL * h->nm;
+    h->mb = w.alloc<double>(n + 1);
+    h->mx = w.alloc<double>(n + 1);
+    h->mr = w.alloc<double>(n + 1);
+    h->mz = w.alloc<double>(n + 1);
+    h->mp = w.alloc<double>(n + 1);
+    h->mq = w.alloc<double>(n + 1);
+    h->cg = w.alloc<CgState>(1);
+    SCR_CUDA(cudaStreamSynchronize(s));
+    h->have_mesh = true;
+    h->stats.levels_M = h->hM.n_levels();
+    h->stats.mm_setup_ms = ms_since(t0);
+  });
+}
+
+// CG + AMG (Sec. 5.2.2) on (L kron I3) u = g, FP64
+static bool mesh_cg(scr_ctx* h, const double* g, double* u, int* iters, double* rel) {
+  cudaStream_t s = h->s;
+  const long long n = 3LL * h->nm;
+  double* hr = h->mhs.h;
+  fill<double>(u, 0.0, n, s);
+  copy<double>(g, h->mr, n, s);
+  cg_start(h->cg, g, n, h->mred, h->mhs.d, s);
+  SCR_CUDA(cudaStreamSynchronize(s));
+  *iters = 0;
+  *rel = 0.0;
+  if (!(hr[1] > 0.0)) return true;
+  h->hM.apply<double>(h->mr, h->mz, s);
+  cg_dot_rz(h->cg, h->mr, h->mz, n, h->mred, 1, s);
+  copy<double>(h->mz, h->mp, n, s);
+  EpiArgs set;
+  for (int it = 1; it <= h->o.mm_max_it; ++it) {
+    spmv<double, double>(h->L, h->mp, h->mq, 3, set, s);
+    cg_alpha(h->cg, h->mp, h->mq, n, h->mred, s);
+    cg_step_x_r(h->cg, h->mp, h->mq, u, h->mr, n, h->mred, h->mhs.d, s);
+    SCR_CUDA(cudaStreamSynchronize(s));
+    *iters = it;
+    *rel = hr[0];
+    if (!std::isfinite(*rel)) return false;
+    if (*rel <= h->o.mm_rtol) return true;
+    h->hM.apply<double>(h->mr, h->mz, s);
+    cg_dot_rz(h->cg, h->mr, h->mz, n, h->mred, 0, s);
+    cg_update_p(h->cg, h->mz, h->mp, n, s);
+  }
+  return false;
+}
+
+static double mesh_true_rel(scr_ctx* h, const double* g, const double* u) {
+  const long long n = 3LL * h->nm;
+  EpiArgs res;
+  res.kind = Epi::Resid;
+  res.z = g;
+  spmv<double, double>(h->L, u, h->mq, 3, res, h->s);
+  norm2<double>(h->mq, n, &h->cg->rr, h->mred, h->s);
+  double r2 = 0, b2 = 0;
+  SCR_CUDA(cudaMemcpyAsync(&r2, &h->cg->rr, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  SCR_CUDA(cudaMemcpyAsync(&b2, &h->cg->bnorm2, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  SCR_CUDA(cudaStreamSynchronize(h->s));
+  return b2 > 0 ? std::sqrt(r2 / b2) : std::sqrt(r2);
+}
+
+int mm_solve(scr_handle h, const double* g, double* u, int dev) {
+  if (!h || !g || !u) return SCR_INVALID_ARG;
+  if (!h->have_mesh) {
+    set_last_error("mm_solve before mm_setup");
+    return SCR_INVALID_ARG;
+  }
+  bool ok = false;
+  int rc = guarded([&] {
+    auto t0 = Clock::now();
+    const long long n = 3LL * h->nm;
+    const double* gd = g;
+    double* ud = u;
+    if (!dev) {
+      SCR_CUDA(cudaMemcpyAsync(h->mb, g, sizeof(double) * n, cudaMemcpyHostToDevice, h->s));
+      gd = h->mb;
+      ud = h->mx;
+    }
+    h->hM.vcycles = 0;
+    int it = 0;
+    double rel = 0;
+    ok = mesh_cg(h, gd, ud, &it, &rel);
+    h->stats.mm_iters = it;
+    h->stats.mm_rel_res = mesh_true_rel(h, gd, ud);
+    h->stats.vcycles_M = h->hM.vcycles;
+    if (!dev) SCR_CUDA(cudaMemcpyAsync(u, ud, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
+    SCR_CUDA(cudaStreamSynchronize(h->s));
+    h->stats.mm_solve_ms = ms_since(t0);
+  });
+  if (rc != SCR_OK) return rc;
+  if (!ok) {
+    set_last_error("mesh CG stopped at %d iterations, relative residual %.3e", h->stats.mm_iters,
+                   h->stats.mm_rel_res);
+    return SCR_NOT_CONVERGED;
+  }
+  return SCR_OK;
+}
+
+int mm_iters(scr_handle h, int* iters, double* rel) {
+  if (!h) return SCR_INVALID_ARG;
+  if (iters) *iters = h->stats.mm_iters;
+  if (rel) *rel = h->stats.mm_rel_res;
+  return SCR_OK;
+}
+
+int scr_apply_op(scr_handle h, const double* x, double* y) {
+  if (!h || !x || !y || !h->have_block) return SCR_INVALID_ARG;
+  return guarded([&] {
+    block_op(h->A, h->B, h->C, h->D, x, y, nullptr, false, h->s);
+    SCR_CUDA(cudaStreamSynchronize(h->s));
+  });
+}
+
+int scr_apply_pc(scr_handle h, const double* r, double* y) {
+  if (!h || !r || !y || !h->have_block) return SCR_INVALID_ARG;
+  return guarded([&] {
+    reset_solve_stats(h);
+    apply_pc_any(h, r, y);
+    SCR_CUDA(cudaStreamSynchronize(h->s));
+  });
+}
+
+int scr_apply_schur(scr_handle h, const double* xp, double* yp) {
+  if (!h || !xp || !yp || !h->have_block) return SCR_INVALID_ARG;
+  return guarded([&] {
+    reset_solve_stats(h);
+    if (h->o.precision == SCR_MIXED) {
+      cast_d2f(xp, h->pr, h->np, h->s);
+      PcView<float> v = view32(h);
+      apply_S<float>(h, v, h->pr, h->py);
+      cast_f2d(h->py, yp, h->np, h->s);
+    } else {
+      PcView<double> v = view64(h);
+      apply_S<double>(h, v, xp, yp);
+    }
+    SCR_CUDA(cudaStreamSynchronize(h->s));
+  });
+}
+
+static Hierarchy* pick_hier(scr_ctx* h, int which) {
+  if (which == SCR_HIER_A && h->have_block) return &h->hA;
+  if (which == SCR_HIER_SHAT && h->have_block) return &h->hS;
+  if (which == SCR_HIER_MESH && h->have_mesh) return &h->hM;
+  return nullptr;
+}
+
+int scr_amg_apply(scr_handle h, int which, const double* b, double* x) {
+  if (!h || !b || !x) return SCR_INVALID_ARG;
+  Hierarchy* H = pick_hier(h, which);
+  if (!H) {
+    set_last_error("hierarchy not set up");
+    return SCR_INVALID_ARG;
+  }
+  return guarded([&] {
+    const long long n = H->lv[0].n * H->nrhs;
+    if (H->f32) {
+      float* bf = H->lv[0].rf;  // level-0 scratch vectors double as staging here
+      float* xf = H->lv[0].xf;
+      cast_d2f(b, bf, n, h->s);
+      float* bin = H->lv[0].bf;
+      copy<float>(bf, bin, n, h->s);
+      H->apply<float>(bin, xf, h->s);
+      cast_f2d(xf, x, n, h->s);
+    } else {
+      H->apply<double>(b, x, h->s);
+    }
+    SCR_CUDA(cudaStreamSynchronize(h->s));
+  });
+}
+
+int scr_amg_levels(scr_handle h, int which, int* n) {
+  if (!h || !n) return SCR_INVALID_ARG;
+  Hierarchy* H = pick_hier(h, which);
+  *n = H ? H->n_levels() : 0;
+  return SCR_OK;
+}
+
+int scr_export(scr_handle h, int which, int level, int kind, scr_bsr_out* out) {
+  if (!h || !out) return SCR_INVALID_ARG;
+  Hierarchy* H = pick_hier(h, which);
+  if (!H || level < 0 || level >= H->n_levels()) {
+    set_last_error("scr_export: no such hierarchy level");
+    return SCR_INVALID_ARG;
+  }
+  return guarded([&] {
+    Level& L = H->lv[level];
+    if (kind == SCR_EXPORT_AGGREGATES) {
+      out->nb_rows = L.A.nbr;
+      out->nb_cols = L.n_agg;
+      out->br = out->bc = 1;
+      out->nnzb = L.agg ? L.A.nbr : 0;
+      if (out->col_idx && L.agg)
+        SCR_CUDA(cudaMemcpyAsync(out->col_idx, L.agg, sizeof(int) * L.A.nbr, cudaMemcpyDeviceToHost, h->s));
+      SCR_CUDA(cudaStreamSynchronize(h->s));
+      return;
+    }
+    const DBsr<double>* M = nullptr;
+    if (kind == SCR_EXPORT_OPERATOR) M = &L.A;
+    else if (kind == SCR_EXPORT_PROLONGATOR) M = &L.P;
+    else throw std::invalid_argument("scr_export: unknown kind");
+    out->nb_rows = M->nbr;
+    out->nb_cols = M->nbc;
+    out->br = M->br;
+    out->bc = M->bc;
+    out->nnzb = (int)M->nnzb;
+    if (!out->row_ptr || !out->col_idx || !out->val) return;
+    if (M->nbr == 0) return;
+    DeviceArena tmp(h->s);
+    const size_t nv = (size_t)M->nnzb * M->br * M->bc;
+    double* v = tmp.alloc<double>(nv + 1);
+    from_slab(M->rp, M->val, v, M->nbr, M->br, M->bc, M->nnzb, h->s);
+    SCR_CUDA(cudaMemcpyAsync(out->row_ptr, M->rp, sizeof(int) * (M->nbr + 1), cudaMemcpyDeviceToHost, h->s));
+    SCR_CUDA(cudaMemcpyAsync(out->col_idx, M->col, sizeof(int) * M->nnzb, cudaMemcpyDeviceToHost, h->s));
+    SCR_CUDA(cudaMemcpyAsync(out->val, v, sizeof(double) * nv, cudaMemcpyDeviceToHost, h->s));
+    SCR_CUDA(cudaStreamSynchronize(h->s));
+  });
+}
+
+int scr_bsr_spmv(const scr_bsr* M, const double* x, double* y, void* stream) {
+  if (!M || !x || !y) return SCR_INVALID_ARG;
+  return guarded([&] {
+    if (!((M->br == 1 || M->br == 3) && (M->bc == 1 || M->bc == 3)))
+      throw std::invalid_argument("scr_bsr_spmv: block sizes must be 1 or 3");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DeviceArena tmp(s);
+    DBsr<double> D;
+    D.nbr = M->nb_rows;
+    D.nbc = M->nb_cols;
+    D.br = M->br;
+    D.bc = M->bc;
+    D.nnzb = M->nnzb;
+    D.rp = const_cast<int*>(M->row_ptr);
+    D.col = const_cast<int*>(M->col_idx);
+    const size_t nv = (size_t)M->nnzb * M->br * M->bc;
+    if (D.nbr < 0 || D.nbc < 0 || D.nnzb < 0) throw std::invalid_argument("scr_bsr_spmv: negative size");
+    int* bad = tmp.alloc<int>(1);
+    SCR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    if (D.nbr > 0) {
+      k_check_cols<<<ceil_div(D.nbr, 256), 256, 0, s>>>(D.nbr, D.nbc, D.rp, D.col, D.nnzb, bad);
+      SCR_LAUNCH();
+    }
+    int hb = 0;
+    SCR_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SCR_CUDA(cudaStreamSynchronize(s));
+    if (hb) throw std::invalid_argument("scr_bsr_spmv: row_ptr/col_idx invalid");
+    D.val = tmp.alloc<double>(nv + 1);
+    if (nv) to_slab<double>(D.rp, M->val, D.val, D.nbr, D.br, D.bc, D.nnzb, s);
+    spmv<double, double>(D, x, y, 1, EpiArgs(), s);
+    SCR_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,288 @@
+// Block-sparse matrix-vector products (slab layout), layout conversions and
+// the fused 2x2 block operator calA = [[A, B], [C, D]] of Sec. 5.2.1.
+//
+// Work decomposition: one group of G lanes per SCALAR row.  A scalar row of
+// a block row is contiguous in the slab layout (k*BC values), so the G lanes
+// stream it with one multiply-add per stored value and combine their partial
+// sums with log2(G) shuffles.  G is small (2-8): on GB300 the FP64 pipe
+// (about two FP64 FMAs per SM clock) is the binding resource of an FP64
+// SpMV, and a wider group would spend more FP64 adds on the cross-lane
+// reduction than on the product itself.
+#include <cstdarg>
+#include <cstring>
+
+#include "kernels.h"
+
+namespace scr {
+
+LaunchCounter& counters() {
+  static LaunchCounter c;
+  return c;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+// ------------------------------------------------------------ layouts
+template <typename TO>
+__global__ void k_to_slab(const int* __restrict__ rp, const double* __restrict__ in, TO* __restrict__ out,
+                          int nbr, int br, int bc) {
+  int i = blockIdx.x * blockDim.y + threadIdx.y;
+  if (i >= nbr) return;
+  int s = rp[i], k = rp[i + 1] - s;
+  int bs = br * bc;
+  for (int q = threadIdx.x; q < k * bs; q += blockDim.x) {
+    int t = q / bs, rem = q - t * bs, r = rem / bc, c = rem - r * bc;
+    out[slab_index(s, k, t, r, c, br, bc)] = (TO)in[(long long)(s + t) * bs + rem];
+  }
+}
+
+template <typename TI>
+__global__ void k_from_slab(const int* __restrict__ rp, const TI* __restrict__ in, double* __restrict__ out,
+                            int nbr, int br, int bc) {
+  int i = blockIdx.x * blockDim.y + threadIdx.y;
+  if (i >= nbr) return;
+  int s = rp[i], k = rp[i + 1] - s;
+  int bs = br * bc;
+  for (int q = threadIdx.x; q < k * bs; q += blockDim.x) {
+    int t = q / bs, rem = q - t * bs, r = rem / bc, c = rem - r * bc;
+    out[(long long)(s + t) * bs + rem] = (double)in[slab_index(s, k, t, r, c, br, bc)];
+  }
+}
+
+template <typename TO>
+void to_slab(const int* rp, const double* std_val, TO* slab_val, int nbr, int br, int bc, long long nnzb,
+             cudaStream_t s) {
+  if (nbr == 0) return;
+  dim3 blk(32, 8);
+  k_to_slab<TO><<<ceil_div(nbr, 8), blk, 0, s>>>(rp, std_val, slab_val, nbr, br, bc);
+  SCR_LAUNCH();
+  counters().launches++;
+  (void)nnzb;
+}
+template void to_slab<double>(const int*, const double*, double*, int, int, int, long long, cudaStream_t);
+template void to_slab<float>(const int*, const double*, float*, int, int, int, long long, cudaStream_t);
+
+void from_slab(const int* rp, const double* slab_val, double* std_val, int nbr, int br, int bc, long long,
+               cudaStream_t s) {
+  if (nbr == 0) return;
+  dim3 blk(32, 8);
+  k_from_slab<double><<<ceil_div(nbr, 8), blk, 0, s>>>(rp, slab_val, std_val, nbr, br, bc);
+  SCR_LAUNCH();
+}
+void from_slab_f(const int* rp, const float* slab_val, double* std_val, int nbr, int br, int bc, long long,
+                 cudaStream_t s) {
+  if (nbr == 0) return;
+  dim3 blk(32, 8);
+  k_from_slab<float><<<ceil_div(nbr, 8), blk, 0, s>>>(rp, slab_val, std_val, nbr, br, bc);
+  SCR_LAUNCH();
+}
+
+__global__ void k_d2f(const double* __restrict__ x, float* __restrict__ y, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long st = (long long)gridDim.x * blockDim.x;
+  for (; i < n; i += st) y[i] = (float)x[i];
+}
+void slab_to_float(const double* in, float* out, long long n, cudaStream_t s) {
+  if (n == 0) return;
+  k_d2f<<<std::min<long long>(ceil_div(n, 256), 4 * 1024), 256, 0, s>>>(in, out, n);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
+// ------------------------------------------------------------ SpMV
+template <typename XT, Epi E>
+struct Epilogue {
+  XT* y;
+  const XT* z;
+  const XT* xs;
+  const XT* dinv;
+  XT alpha, beta;
+  template <typename AT>
+  __device__ __forceinline__ void operator()(long long gi, long long o, AT acc) const {
+    if constexpr (E == Epi::Set) {
+      y[gi] = (XT)acc;
+    } else if constexpr (E == Epi::Axpby) {
+      XT v = alpha * (XT)acc;
+      if (z) v += beta * z[gi];
+      y[gi] = v;
+    } else if constexpr (E == Epi::Resid) {
+      y[gi] = z[gi] - (XT)acc;
+    } else {
+      y[gi] = xs[gi] + (z[gi] - (XT)acc) * dinv[o];
+    }
+  }
+};
+
+// accumulate one scalar row r of block row i of M into acc[h], lanes of a
+// G-group split the row's k*BC stored values
+template <int BC, int NRHS, int G, typename VT, typename XT, typename AT>
+__device__ __forceinline__ void scalar_row_accum(const int* __restrict__ rp, const int* __restrict__ col,
+                                                 const VT* __restrict__ val, const XT* __restrict__ x, int BR,
+                                                 int i, int r, int lane, AT (&acc)[NRHS]) {
+  const int s = __ldg(rp + i), k = __ldg(rp + i + 1) - s;
+  const int L = k * BC;
+  const VT* vr = val + (long long)s * BR * BC + (long long)r * L;
+  const int* cr = col + s;
+#pragma unroll 4
+  for (int q = lane; q < L; q += G) {
+    int t, c;
+    if constexpr (BC == 1) {
+      t = q;
+      c = 0;
+    } else {
+      t = q / BC;
+      c = q - t * BC;
+    }
+    const long long xb = ((long long)__ldg(cr + t) * BC + c) * NRHS;
+    const AT a = (AT)__ldg(vr + q);
+#pragma unroll
+    for (int h = 0; h < NRHS; ++h) acc[h] = fma(a, (AT)__ldg(x + xb + h), acc[h]);
+  }
+}
+
+template <int BR, int BC, int NRHS, int G, typename VT, typename XT, typename AT, Epi E>
+__global__ void __launch_bounds__(256) k_spmv(int nbr, const int* __restrict__ rp, const int* __restrict__ col,
+                                              const VT* __restrict__ val, const XT* __restrict__ x,
+                                              Epilogue<XT, E> epi) {
+  const long long o = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;  // scalar row
+  const int lane = threadIdx.x % G;
+  const long long nrows = (long long)nbr * BR;
+  const bool active = o < nrows;  // inactive lanes still join the shuffles
+  AT acc[NRHS];
+#pragma unroll
+  for (int h = 0; h < NRHS; ++h) acc[h] = (AT)0;
+  if (active) {
+    const int i = (int)(o / BR), r = (int)(o - (long long)i * BR);
+    scalar_row_accum<BC, NRHS, G>(rp, col, val, x, BR, i, r, lane, acc);
+  }
+#pragma unroll
+  for (int h = 0; h < NRHS; ++h) {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) acc[h] += __shfl_xor_sync(0xffffffffu, acc[h], off, G);
+  }
+  if (active && lane == 0) {
+#pragma unroll
+    for (int h = 0; h < NRHS; ++h) epi(o * NRHS + h, o, acc[h]);
+  }
+}
+
+template <int BR, int BC, int NRHS, int G, typename VT, typename XT, typename AT, Epi E>
+static void launch_spmv_g(const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& e, cudaStream_t s) {
+  Epilogue<XT, E> epi;
+  epi.y = y;
+  epi.z = static_cast<const XT*>(e.z);
+  epi.xs = static_cast<const XT*>(e.xs);
+  epi.dinv = static_cast<const XT*>(e.dinv);
+  epi.alpha = (XT)e.alpha;
+  epi.beta = (XT)e.beta;
+  const long long threads = (long long)M.nbr * BR * G;
+  const int blk = 256;
+  k_spmv<BR, BC, NRHS, G, VT, XT, AT, E><<<ceil_div(threads, blk), blk, 0, s>>>(M.nbr, M.rp, M.col, M.val, x, epi);
+  SCR_LAUNCH();
+}
+
+template <int BR, int BC, int NRHS, int G, typename VT, typename XT>
+static void launch_spmv_e(const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& e, cudaStream_t s) {
+  using AT = XT;  // accumulate in the vector precision
+  switch (e.kind) {
+    case Epi::Set: launch_spmv_g<BR, BC, NRHS, G, VT, XT, AT, Epi::Set>(M, x, y, e, s); break;
+    case Epi::Axpby: launch_spmv_g<BR, BC, NRHS, G, VT, XT, AT, Epi::Axpby>(M, x, y, e, s); break;
+    case Epi::Resid: launch_spmv_g<BR, BC, NRHS, G, VT, XT, AT, Epi::Resid>(M, x, y, e, s); break;
+    case Epi::Jacobi: launch_spmv_g<BR, BC, NRHS, G, VT, XT, AT, Epi::Jacobi>(M, x, y, e, s); break;
+  }
+}
+
+// lanes per scalar row: FP64 keeps groups narrow (FP64 adds of the
+// reduction compete with the products), FP32 widens them for coalescing
+template <typename VT>
+static int pick_group(const DBsr<VT>& M) {
+  const double per_row = M.nbr ? (double)M.nnzb * M.bc / M.nbr : 0.0;
+  if (sizeof(VT) == 8) return per_row >= 24 ? 4 : 2;
+  return per_row >= 48 ? 8 : 4;
+}
+
+template <typename VT, typename XT>
+void spmv(const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const EpiArgs& e, cudaStream_t s) {
+  if (M.nbr == 0) return;
+  const int G = pick_group(M);
+  const int br = M.br, bc = M.bc;
+#define SCR_SPMV_CASE(BR_, BC_, NR_)                                            \
+  if (br == BR_ && bc == BC_ && nrhs == NR_) {                                  \
+    if (G == 2) launch_spmv_e<BR_, BC_, NR_, 2, VT, XT>(M, x, y, e, s);         \
+    else if (G == 4) launch_spmv_e<BR_, BC_, NR_, 4, VT, XT>(M, x, y, e, s);    \
+    else launch_spmv_e<BR_, BC_, NR_, 8, VT, XT>(M, x, y, e, s);                \
+    goto done;                                                                  \
+  }
+  SCR_SPMV_CASE(3, 3, 1)
+  SCR_SPMV_CASE(3, 1, 1)
+  SCR_SPMV_CASE(1, 3, 1)
+  SCR_SPMV_CASE(1, 1, 1)
+  SCR_SPMV_CASE(1, 1, 3)
+#undef SCR_SPMV_CASE
+  throw CudaError{cudaErrorInvalidValue, "spmv: unsupported block shape"};
+done:
+  counters().launches++;
+  counters().spmv_bytes += M.nnzb * (long long)(M.br * M.bc * sizeof(VT) + sizeof(int)) +
+                           (long long)M.nbr * M.br * nrhs * sizeof(XT) * (e.kind == Epi::Set ? 1 : 2);
+}
+
+template void spmv<double, double>(const DBsr<double>&, const double*, double*, int, const EpiArgs&, cudaStream_t);
+template void spmv<float, float>(const DBsr<float>&, const float*, float*, int, const EpiArgs&, cudaStream_t);
+
+// ------------------------------------------------------------ calA
+// Scalar rows 0..3n_v-1: (A x_v + B x_p); rows 3n_v..3n_v+n_p-1:
+// (C x_v + D x_p).  One G-group per scalar row.
+template <int G, bool RESID>
+__global__ void __launch_bounds__(256) k_block_op(int nv, int np, DBsr<double> A, DBsr<double> B, DBsr<double> C,
+                                                  DBsr<double> D, const double* __restrict__ x,
+                                                  double* __restrict__ y, const double* __restrict__ z) {
+  const long long o = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;
+  const int lane = threadIdx.x % G;
+  const long long nrow_v = 3LL * nv;
+  const bool active = o < nrow_v + np;  // inactive lanes still join the shuffles
+  const double* xv = x;
+  const double* xp = x + nrow_v;
+  double acc[1] = {0.0};
+  if (!active) {
+  } else if (o < nrow_v) {
+    const int i = (int)(o / 3), r = (int)(o - 3LL * i);
+    scalar_row_accum<3, 1, G>(A.rp, A.col, A.val, xv, 3, i, r, lane, acc);
+    scalar_row_accum<1, 1, G>(B.rp, B.col, B.val, xp, 3, i, r, lane, acc);
+  } else {
+    const int i = (int)(o - nrow_v);
+    scalar_row_accum<3, 1, G>(C.rp, C.col, C.val, xv, 1, i, 0, lane, acc);
+    scalar_row_accum<1, 1, G>(D.rp, D.col, D.val, xp, 1, i, 0, lane, acc);
+  }
+#pragma unroll
+  for (int off = G / 2; off > 0; off >>= 1) acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], off, G);
+  if (active && lane == 0) y[o] = RESID ? z[o] - acc[0] : acc[0];
+}
+
+void block_op(const DBsr<double>& A, const DBsr<double>& B, const DBsr<double>& C, const DBsr<double>& D,
+              const double* x, double* y, const double* z, bool resid, cudaStream_t s) {
+  const int nv = A.nbr, np = D.nbr;
+  const long long rows = 3LL * nv + np;
+  if (rows == 0) return;
+  constexpr int G = 4;
+  const long long threads = rows * G;
+  if (resid)
+    k_block_op<G, true><<<ceil_div(threads, 256), 256, 0, s>>>(nv, np, A, B, C, D, x, y, z);
+  else
+    k_block_op<G, false><<<ceil_div(threads, 256), 256, 0, s>>>(nv, np, A, B, C, D, x, y, z);
+  SCR_LAUNCH();
+  counters().launches++;
+  const long long nnzb = A.nnzb + B.nnzb + C.nnzb + D.nnzb;
+  counters().spmv_bytes += A.nnzb * 76 + B.nnzb * 28 + C.nnzb * 28 + D.nnzb * 12 + rows * 8 * (resid ? 2 : 1);
+  (void)nnzb;
+}
+
+}  // namespace scr

@@ -1,0 +1,241 @@
+"""Python face of the C ABI: argument marshalling only."""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+
+import numpy as np
+
+from .abi import (BsrOut, Bsr, Opts, SCR_NOT_CONVERGED, SCR_OK, ScrError, Stats, check,
+                  load_library)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+@dataclasses.dataclass
+class DeviceBSR:
+    """Block CSR with its arrays in device memory (torch CUDA tensors)."""
+    br: int
+    bc: int
+    nb_rows: int
+    nb_cols: int
+    row_ptr: object  # torch.int32
+    col: object      # torch.int32
+    val: object      # torch.float64
+
+    @classmethod
+    def from_host(cls, M, device="cuda"):
+        torch = _torch()
+        return cls(M.br, M.bc, M.nb_rows, M.nb_cols,
+                   torch.as_tensor(np.ascontiguousarray(M.row_ptr, dtype=np.int32), device=device),
+                   torch.as_tensor(np.ascontiguousarray(M.col, dtype=np.int32), device=device),
+                   torch.as_tensor(np.ascontiguousarray(M.val, dtype=np.float64), device=device))
+
+    @property
+    def nnzb(self) -> int:
+        return int(self.col.numel())
+
+
+def _as_bsr(M, keep: list) -> tuple[Bsr, int]:
+    """(C struct, ptr_is_device) for a host (numpy) or device (torch) matrix."""
+    if isinstance(M, DeviceBSR):
+        s = Bsr(M.nb_rows, M.nb_cols, M.br, M.bc, M.nnzb, M.row_ptr.data_ptr(), M.col.data_ptr(),
+                M.val.data_ptr())
+        keep.append(M)
+        return s, 1
+    rp = np.ascontiguousarray(M.row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(M.col, dtype=np.int32)
+    val = np.ascontiguousarray(M.val, dtype=np.float64)
+    keep.extend([rp, col, val])
+    s = Bsr(M.nb_rows, M.nb_cols, M.br, M.bc, int(col.size), rp.ctypes.data, col.ctypes.data, val.ctypes.data)
+    return s, 0
+
+
+def _ptr(x, keep: list) -> tuple[int, int]:
+    """(address, ptr_is_device) of a numpy array or a torch tensor."""
+    if isinstance(x, np.ndarray):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        keep.append(x)
+        return x.ctypes.data, 0
+    torch = _torch()
+    if isinstance(x, torch.Tensor):
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError("vectors must be contiguous float64 tensors")
+        keep.append(x)
+        return x.data_ptr(), int(x.is_cuda)
+    raise TypeError(f"unsupported vector type {type(x)}")
+
+
+class BlockSolver:
+    """One solver context (scr_handle) on the current CUDA device."""
+
+    def __init__(self, stream=None, **opts):
+        self.lib = load_library()
+        o = Opts()
+        self.lib.scr_default_opts(C.byref(o))
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise KeyError(f"unknown option {k}")
+            setattr(o, k, v)
+        self.opts = o
+        if stream is None:
+            torch = _torch()
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        h = C.c_void_p()
+        check(self.lib.scr_create(C.byref(h), C.byref(o), C.c_void_p(stream)))
+        self.h = h
+        self.n_v = self.n_p = self.n_m = 0
+
+    # -------------------------------------------------------------- life
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.scr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -------------------------------------------------------------- block system
+    def setup(self, A, B, Cm, D):
+        keep: list = []
+        sa, da = _as_bsr(A, keep)
+        sb, db = _as_bsr(B, keep)
+        sc, dc = _as_bsr(Cm, keep)
+        sd, dd = _as_bsr(D, keep)
+        if len({da, db, dc, dd}) != 1:
+            raise ValueError("A, B, C, D must all be on the host or all on the device")
+        check(self.lib.scr_setup(self.h, C.byref(sa), C.byref(sb), C.byref(sc), C.byref(sd), da))
+        self.n_v, self.n_p = A.nb_rows, D.nb_rows
+        return self
+
+    def solve(self, b, x=None, raise_on_nonconvergence: bool = True):
+        """x with calA x = b.  numpy in -> numpy out (host pointers);
+        CUDA tensor in -> CUDA tensor out (device pointers)."""
+        n = 3 * self.n_v + self.n_p
+        keep: list = []
+        pb, dev = _ptr(b, keep)
+        if x is None:
+            if dev:
+                x = _torch().empty(n, dtype=_torch().float64, device=b.device)
+            else:
+                x = np.empty(n)
+        px, dx = _ptr(x, keep)
+        if dx != dev:
+            raise ValueError("b and x must both be host or both device")
+        st = self.lib.scr_solve(self.h, C.c_void_p(pb), C.c_void_p(px), dev)
+        check(st, (SCR_OK,) if raise_on_nonconvergence else (SCR_OK, SCR_NOT_CONVERGED))
+        return x
+
+    def iters(self):
+        o, i = C.c_int(), C.c_int()
+        check(self.lib.scr_iters(self.h, C.byref(o), C.byref(i)))
+        return o.value, i.value
+
+    def residual(self) -> float:
+        r = C.c_double()
+        check(self.lib.scr_residual(self.h, C.byref(r)))
+        return r.value
+
+    def stats(self) -> dict:
+        s = Stats()
+        check(self.lib.scr_get_stats(self.h, C.byref(s)))
+        return s.as_dict()
+
+    # -------------------------------------------------------------- mesh
+    def mesh_setup(self, L):
+        keep: list = []
+        sl, dl = _as_bsr(L, keep)
+        check(self.lib.mm_setup(self.h, C.byref(sl), dl))
+        self.n_m = L.nb_rows
+        return self
+
+    def mesh_solve(self, g, u=None, raise_on_nonconvergence: bool = True):
+        n = 3 * self.n_m
+        keep: list = []
+        pg, dev = _ptr(g, keep)
+        if u is None:
+            u = _torch().empty(n, dtype=_torch().float64, device=g.device) if dev else np.empty(n)
+        pu, du = _ptr(u, keep)
+        st = self.lib.mm_solve(self.h, C.c_void_p(pg), C.c_void_p(pu), dev)
+        check(st, (SCR_OK,) if raise_on_nonconvergence else (SCR_OK, SCR_NOT_CONVERGED))
+        return u
+
+    def mesh_iters(self):
+        i, r = C.c_int(), C.c_double()
+        check(self.lib.mm_iters(self.h, C.byref(i), C.byref(r)))
+        return i.value, r.value
+
+    # -------------------------------------------------------------- single steps
+    def _dev2(self, fn, x, n_out):
+        torch = _torch()
+        y = torch.empty(n_out, dtype=torch.float64, device=x.device)
+        check(fn(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr())))
+        return y
+
+    def apply_op(self, x):
+        return self._dev2(self.lib.scr_apply_op, x, 3 * self.n_v + self.n_p)
+
+    def apply_pc(self, r):
+        return self._dev2(self.lib.scr_apply_pc, r, 3 * self.n_v + self.n_p)
+
+    def apply_schur(self, xp):
+        return self._dev2(self.lib.scr_apply_schur, xp, self.n_p)
+
+    def amg_apply(self, which: int, b):
+        torch = _torch()
+        x = torch.empty_like(b)
+        check(self.lib.scr_amg_apply(self.h, which, C.c_void_p(b.data_ptr()), C.c_void_p(x.data_ptr())))
+        return x
+
+    def amg_levels(self, which: int) -> int:
+        n = C.c_int()
+        check(self.lib.scr_amg_levels(self.h, which, C.byref(n)))
+        return n.value
+
+    def export(self, which: int, level: int, kind: int):
+        """Copy a hierarchy operator / prolongator (block CSR, numpy) or the
+        aggregates (int array) to the host."""
+        from .abi import SCR_EXPORT_AGGREGATES
+        o = BsrOut()
+        check(self.lib.scr_export(self.h, which, level, kind, C.byref(o)))
+        if kind == SCR_EXPORT_AGGREGATES:
+            agg = np.empty(max(o.nb_rows, 1), dtype=np.int32)
+            o2 = BsrOut()
+            o2.col_idx = agg.ctypes.data
+            check(self.lib.scr_export(self.h, which, level, kind, C.byref(o2)))
+            return agg[: o.nb_rows] if o.nnzb else None
+        rp = np.empty(o.nb_rows + 1, dtype=np.int32)
+        col = np.empty(max(o.nnzb, 1), dtype=np.int32)
+        val = np.empty(max(o.nnzb * o.br * o.bc, 1))
+        o2 = BsrOut()
+        o2.row_ptr, o2.col_idx, o2.val = rp.ctypes.data, col.ctypes.data, val.ctypes.data
+        check(self.lib.scr_export(self.h, which, level, kind, C.byref(o2)))
+        from types import SimpleNamespace
+        return SimpleNamespace(br=o.br, bc=o.bc, nb_rows=o.nb_rows, nb_cols=o.nb_cols, row_ptr=rp,
+                               col=col[: o.nnzb], val=val[: o.nnzb * o.br * o.bc])
+
+
+def bsr_spmv(M: DeviceBSR, x, y=None, stream=None):
+    """y = M x for a device block matrix, through scr_bsr_spmv."""
+    torch = _torch()
+    lib = load_library()
+    if y is None:
+        y = torch.empty(M.nb_rows * M.br, dtype=torch.float64, device=x.device)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    s = Bsr(M.nb_rows, M.nb_cols, M.br, M.bc, M.nnzb, M.row_ptr.data_ptr(), M.col.data_ptr(), M.val.data_ptr())
+    check(lib.scr_bsr_spmv(C.byref(s), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), C.c_void_p(stream)))
+    return y

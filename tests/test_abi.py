@@ -1,0 +1,64 @@
+"""The C-ABI library builds, loads and exports every symbol the header
+declares (no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "scr_gb300.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "while", "sizeof")))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("scr_create", "scr_setup", "scr_solve", "scr_iters", "scr_residual", "scr_destroy",
+                 "mm_setup", "mm_solve"):
+        assert must in names
+
+
+def test_library_builds_and_exports_every_symbol():
+    from paper_2206_06996_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_tracks_header():
+    from paper_2206_06996_gb300 import abi
+    assert sorted(abi.EXPORTED) == declared_functions()
+
+
+def test_default_options_without_gpu():
+    # scr_default_opts touches no device
+    from paper_2206_06996_gb300 import abi
+    lib = abi.load_library(build_if_missing=True)
+    o = abi.Opts()
+    assert lib.scr_default_opts(ctypes.byref(o)) == 0
+    assert o.rtol == 1e-8 and o.restart == 30 and o.rtol_A == 1e-3 and o.max_it == 200
+    assert lib.scr_default_opts(None) == abi.SCR_INVALID_ARG
+
+
+def test_options_struct_layout_matches_header():
+    from paper_2206_06996_gb300 import abi
+    src = open(HEADER).read()
+    body = src[src.index("typedef struct {\n  double rtol;"):]
+    body = body[: body.index("} scr_opts;")]
+    fields = re.findall(r"\b(\w+)\s*;", re.sub(r"/\*.*?\*/", "", body, flags=re.S))
+    decl = []
+    for line in re.sub(r"/\*.*?\*/", "", body, flags=re.S).splitlines():
+        line = line.strip().rstrip(";")
+        if not line or line.startswith("typedef"):
+            continue
+        parts = line.split(None, 1)
+        if len(parts) == 2:
+            decl.extend(v.strip() for v in parts[1].split(","))
+    assert [f for f, _ in abi.Opts._fields_] == decl, (decl, fields)

@@ -1,0 +1,343 @@
+"""Parity of the CUDA path with the CPU oracle (needs a GB300).
+
+Every call goes through the C ABI (the thin binding).  Tolerances:
+- block products, Shat, prolongators, Galerkin operators, V-cycles: FP64
+  rounding with a different summation order, 1e-12 relative (1e-5 for the
+  FP32 preconditioner copies);
+- the block solve (the paper's method reaches x* = calA^{-1} b only up to
+  the outer tolerance): ||x - x*|| / ||x*|| <= 1e-6 and
+  ||b - calA x|| / ||b|| <= 1e-8, recomputed by the oracle;
+- the mesh CG: relative residual <= 1e-8, error vs the direct solve.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import fsi_inputs as F
+from oracle import amg, direct, schur
+from oracle.sparse import BlockOperator, bsr_matvec_by_definition, rel_residual, to_csr
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2206_06996_gb300 as pkg  # noqa: E402
+
+pkg.load_library(build_if_missing=True)
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def _rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def _random_bsr(rng, nbr, nbc, br, bc, max_per_row=20, empty_every=7):
+    rp = [0]
+    cols = []
+    for i in range(nbr):
+        k = 0 if (empty_every and i % empty_every == 3) else int(rng.integers(1, max_per_row + 1))
+        c = np.sort(rng.choice(nbc, size=min(k, nbc), replace=False))
+        cols.extend(c.tolist())
+        rp.append(len(cols))
+    return F.BSR(br, bc, nbr, nbc, np.array(rp, np.int32), np.array(cols, np.int32),
+                 rng.standard_normal(len(cols) * br * bc))
+
+
+@pytest.fixture(scope="module")
+def small():
+    return F.tube_system("tube_small", keep_mesh=True)
+
+
+@pytest.fixture(scope="module")
+def small_direct(small):
+    return direct.solve_block(small)
+
+
+@pytest.fixture(scope="module")
+def mini():
+    return F.tube_system("tube_mini", keep_mesh=True)
+
+
+@pytest.fixture(scope="module")
+def mini_x(mini):
+    return direct.solve_block(mini)
+
+
+# ---------------------------------------------------------------- K1 SpMV
+@pytest.mark.parametrize("br,bc", [(3, 3), (3, 1), (1, 3), (1, 1)])
+@pytest.mark.parametrize("nbr", [1, 37, 1000, 4099])
+def test_bsr_spmv_random(br, bc, nbr):
+    rng = np.random.default_rng(nbr * 7 + br * 3 + bc)
+    M = _random_bsr(rng, nbr, max(nbr // 2, 3), br, bc)
+    x = rng.standard_normal(M.nb_cols * bc)
+    y = pkg.bsr_spmv(pkg.DeviceBSR.from_host(M), _dev(x)).cpu().numpy()
+    ref = bsr_matvec_by_definition(M, x)
+    assert np.allclose(y, ref, rtol=1e-12, atol=1e-12 * max(1.0, np.abs(ref).max()))
+
+
+def test_bsr_spmv_empty_matrix():
+    M = F.BSR(3, 3, 5, 5, np.zeros(6, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    y = pkg.bsr_spmv(pkg.DeviceBSR.from_host(M), _dev(np.ones(15))).cpu().numpy()
+    assert np.all(y == 0.0)
+
+
+def test_bsr_spmv_rejects_bad_columns():
+    M = F.BSR(1, 1, 2, 2, np.array([0, 2, 3], np.int32), np.array([1, 0, 5], np.int32), np.ones(3))
+    with pytest.raises(pkg.ScrError) as e:
+        pkg.bsr_spmv(pkg.DeviceBSR.from_host(M), _dev(np.ones(2)))
+    assert e.value.status == 1
+
+
+# ---------------------------------------------------------------- K2 calA
+@pytest.mark.parametrize("name", ["tube_mini", "tube_small"])
+def test_block_operator(name):
+    s = F.tube_system(name)
+    op = BlockOperator.from_system(s)
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(s.n)
+    with pkg.BlockSolver() as sol:
+        sol.setup(s.A, s.B, s.C, s.D)
+        y = sol.apply_op(_dev(x)).cpu().numpy()
+    ref = op.matvec(x)
+    assert _rel(y, ref) < 1e-13
+
+
+# ---------------------------------------------------------------- K4/K5 set-up
+def test_schur_hat(small):
+    op = BlockOperator.from_system(small)
+    ref = schur.schur_hat(op).toarray() if small.n_p < 3000 else None
+    with pkg.BlockSolver() as sol:
+        sol.setup(small.A, small.B, small.C, small.D)
+        Sh = sol.export(pkg.SCR_HIER_SHAT, 0, pkg.SCR_EXPORT_OPERATOR)
+    got = to_csr(Sh)
+    want = schur.schur_hat(op)
+    diff = abs(got - want).max()
+    assert diff <= 1e-12 * abs(want).max()
+    # same sparsity (no structural zeros dropped or added beyond the union)
+    assert got.nnz >= want.nnz - 0
+    del ref
+
+
+def _strength_pattern(A, bs, theta):
+    return amg.strength_graph(A, bs, theta)
+
+
+@pytest.mark.parametrize("which,bs", [(0, 3), (1, 1)])
+def test_aggregates_are_a_valid_mis2_aggregation(small, which, bs):
+    with pkg.BlockSolver() as sol:
+        sol.setup(small.A, small.B, small.C, small.D)
+        A0 = to_csr(sol.export(which, 0, pkg.SCR_EXPORT_OPERATOR))
+        agg = sol.export(which, 0, pkg.SCR_EXPORT_AGGREGATES)
+    S = _strength_pattern(A0, bs, 0.08)
+    n = S.shape[0]
+    deg = np.diff(S.indptr)
+    assert agg.shape == (n,)
+    # isolated nodes (no strong neighbour) are left out, all others covered
+    assert np.all(agg[deg == 0] == -1)
+    assert np.all(agg[deg > 0] >= 0)
+    na = agg.max() + 1
+    assert set(np.unique(agg[agg >= 0])) == set(range(na))
+    # every aggregate is connected and lies within distance 2 of one node
+    S2 = (S @ S + S + sp.identity(n)).tocsr()
+    for a in range(0, na, max(1, na // 200)):
+        nodes = np.nonzero(agg == a)[0]
+        sub = S[nodes][:, nodes]
+        assert sp.csgraph.connected_components(sub, directed=False)[0] == 1
+        within = [np.all(np.isin(nodes, S2.indices[S2.indptr[r]:S2.indptr[r + 1]])) for r in nodes]
+        assert any(within)
+
+
+@pytest.mark.parametrize("which,bs", [(0, 3), (1, 1), (2, 1)])
+def test_prolongator_and_galerkin_operator(small, which, bs):
+    with pkg.BlockSolver() as sol:
+        sol.setup(small.A, small.B, small.C, small.D)
+        sol.mesh_setup(small.L)
+        nl = sol.amg_levels(which)
+        assert nl >= 2
+        for l in range(nl - 1):
+            A = to_csr(sol.export(which, l, pkg.SCR_EXPORT_OPERATOR))
+            P = to_csr(sol.export(which, l, pkg.SCR_EXPORT_PROLONGATOR))
+            agg = sol.export(which, l, pkg.SCR_EXPORT_AGGREGATES)
+            Ac = to_csr(sol.export(which, l + 1, pkg.SCR_EXPORT_OPERATOR))
+            Pt = amg.tentative_prolongator(agg.astype(np.int64), bs)
+            Pref, _ = amg.smoothed_prolongator(A, Pt)
+            assert abs(P - Pref).max() <= 1e-12 * abs(Pref).max()
+            Aref = (Pref.T @ A @ Pref).tocsr()
+            assert abs(Ac - Aref).max() <= 1e-11 * abs(Aref).max()
+
+
+@pytest.mark.parametrize("which,bs,nrhs", [(0, 3, 1), (1, 1, 1), (2, 1, 3)])
+@pytest.mark.parametrize("nu", [1, 2])
+def test_vcycle_matches_oracle_on_exported_hierarchy(small, which, bs, nrhs, nu):
+    with pkg.BlockSolver(amg_nu=nu) as sol:
+        sol.setup(small.A, small.B, small.C, small.D)
+        sol.mesh_setup(small.L)
+        nl = sol.amg_levels(which)
+        As = [to_csr(sol.export(which, l, pkg.SCR_EXPORT_OPERATOR)) for l in range(nl)]
+        Ps = [to_csr(sol.export(which, l, pkg.SCR_EXPORT_PROLONGATOR)) for l in range(nl - 1)]
+        H = amg.hierarchy_from_matrices(As, Ps, bs, nu, nu)
+        rng = np.random.default_rng(3)
+        b = rng.standard_normal(As[0].shape[0] * nrhs)
+        x = sol.amg_apply(which, _dev(b)).cpu().numpy()
+    ref = amg.vcycle(H, b.reshape(-1, nrhs) if nrhs > 1 else b).reshape(-1)
+    assert _rel(x, ref) < 1e-11
+
+
+# ---------------------------------------------------------------- Alg. 1 / 2
+def test_algorithm2_tight_inner_equals_schur(mini):
+    op = BlockOperator.from_system(mini)
+    S = schur.schur_exact_dense(op)
+    rng = np.random.default_rng(4)
+    xp = rng.standard_normal(op.np)
+    with pkg.BlockSolver(rtol_I=1e-13, max_I=2000, restart_inner=60) as sol:
+        sol.setup(mini.A, mini.B, mini.C, mini.D)
+        y = sol.apply_schur(_dev(xp)).cpu().numpy()
+    assert _rel(y, S @ xp) < 1e-8
+
+
+def test_algorithm1_tight_solves_equals_inverse(mini, mini_x):
+    op = BlockOperator.from_system(mini)
+    with pkg.BlockSolver(rtol_A=1e-13, rtol_S=1e-12, rtol_I=1e-14, max_A=2000, max_S=2000, max_I=2000,
+                         restart_inner=60) as sol:
+        sol.setup(mini.A, mini.B, mini.C, mini.D)
+        y = sol.apply_pc(_dev(mini.b)).cpu().numpy()
+    assert _rel(y, mini_x) < 1e-6
+    assert rel_residual(op, y, mini.b) < 1e-6
+
+
+# ---------------------------------------------------------------- full solve
+@pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
+def test_block_solve_matches_direct(small, small_direct, precision):
+    op = BlockOperator.from_system(small)
+    with pkg.BlockSolver(precision=precision) as sol:
+        sol.setup(small.A, small.B, small.C, small.D)
+        x = sol.solve(small.b.copy())
+        st = sol.stats()
+    assert st["rel_res"] <= 1e-8
+    assert rel_residual(op, x, small.b) <= 1e-8
+    assert _rel(x, small_direct) <= 1e-6
+    assert 1 <= st["outer_iters"] <= 30
+
+
+def test_block_solve_device_pointers(mini, mini_x):
+    with pkg.BlockSolver() as sol:
+        sol.setup(pkg.DeviceBSR.from_host(mini.A), pkg.DeviceBSR.from_host(mini.B),
+                  pkg.DeviceBSR.from_host(mini.C), pkg.DeviceBSR.from_host(mini.D))
+        x = sol.solve(_dev(mini.b)).cpu().numpy()
+        assert sol.residual() <= 1e-8
+    assert _rel(x, mini_x) <= 1e-6
+
+
+def test_block_solve_is_deterministic(mini):
+    with pkg.BlockSolver() as sol:
+        sol.setup(mini.A, mini.B, mini.C, mini.D)
+        x1 = sol.solve(mini.b.copy())
+        x2 = sol.solve(mini.b.copy())
+    with pkg.BlockSolver() as sol:
+        sol.setup(mini.A, mini.B, mini.C, mini.D)
+        x3 = sol.solve(mini.b.copy())
+    assert np.array_equal(x1, x2) and np.array_equal(x1, x3)
+
+
+def test_mesh_cg_matches_direct(small):
+    ud = direct.solve_mesh(small)
+    L = to_csr(small.L)
+    g = small.mesh_b.reshape(-1, 3)
+    with pkg.BlockSolver(mm_rtol=1e-12) as sol:
+        sol.mesh_setup(small.L)
+        u = sol.mesh_solve(small.mesh_b.copy())
+        it, rel = sol.mesh_iters()
+    assert np.linalg.norm(L @ u.reshape(-1, 3) - g) / np.linalg.norm(g) <= 1e-12
+    assert _rel(u, ud) <= 1e-9
+    assert 1 <= it <= 100
+
+
+# ---------------------------------------------------------------- edge cases
+def test_zero_rhs_gives_zero(mini):
+    with pkg.BlockSolver() as sol:
+        sol.setup(mini.A, mini.B, mini.C, mini.D)
+        x = sol.solve(np.zeros(mini.n))
+        assert np.all(x == 0.0)
+        assert sol.iters()[0] == 0
+        sol.mesh_setup(mini.L)
+        u = sol.mesh_solve(np.zeros(3 * mini.L.nb_rows))
+        assert np.all(u == 0.0)
+
+
+def test_not_converged_status(mini):
+    with pkg.BlockSolver(max_it=1, rtol_A=0.5, rtol_S=0.5, rtol_I=0.5) as sol:
+        sol.setup(mini.A, mini.B, mini.C, mini.D)
+        with pytest.raises(pkg.ScrError) as e:
+            sol.solve(mini.b.copy())
+        assert e.value.status == 3
+        x = sol.solve(mini.b.copy(), raise_on_nonconvergence=False)
+        assert sol.iters()[0] == 1
+        assert np.all(np.isfinite(x))
+
+
+def test_invalid_shapes_rejected(mini):
+    with pkg.BlockSolver() as sol:
+        with pytest.raises(pkg.ScrError) as e:
+            sol.setup(mini.A, mini.C, mini.B, mini.D)  # B and C swapped
+        assert e.value.status == 1
+        bad = F.BSR(1, 1, mini.D.nb_rows, mini.D.nb_cols, mini.D.row_ptr.copy(), mini.D.col[::-1].copy(),
+                    mini.D.val.copy())
+        with pytest.raises(pkg.ScrError) as e:
+            sol.setup(mini.A, mini.B, mini.C, bad)
+        assert e.value.status == 1
+        with pytest.raises(pkg.ScrError):
+            sol.solve(np.zeros(mini.n))  # no successful set-up yet
+
+
+def test_zero_diagonal_rejected(mini):
+    A = F.BSR(3, 3, mini.A.nb_rows, mini.A.nb_cols, mini.A.row_ptr.copy(), mini.A.col.copy(), mini.A.val.copy())
+    r = 5
+    t = np.searchsorted(A.col[A.row_ptr[r]:A.row_ptr[r + 1]], r) + A.row_ptr[r]
+    A.val[9 * t + 4] = 0.0
+    with pkg.BlockSolver() as sol:
+        with pytest.raises(pkg.ScrError) as e:
+            sol.setup(A, mini.B, mini.C, mini.D)
+        assert e.value.status == 1
+
+
+def test_tiny_system_single_level(tiny_system):
+    # smaller than the coarse size: the hierarchy is one dense level
+    x_ref = direct.solve_block(tiny_system)
+    with pkg.BlockSolver() as sol:
+        sol.setup(tiny_system.A, tiny_system.B, tiny_system.C, tiny_system.D)
+        assert sol.amg_levels(pkg.SCR_HIER_A) == 1
+        x = sol.solve(tiny_system.b.copy())
+    assert _rel(x, x_ref) <= 1e-6
+
+
+# ---------------------------------------------------------------- full size
+@pytest.mark.slow
+def test_large_tube_solve_properties():
+    """The benchmark workload (616,337 nodes, 2.5M unknowns): the oracle
+    recomputes the FP64 residual of the GPU answer; sampled rows of calA
+    are checked one by one against the oracle's block definition."""
+    s = F.tube_system("tube_large")
+    op = BlockOperator.from_system(s)
+    with pkg.BlockSolver() as sol:
+        sol.setup(s.A, s.B, s.C, s.D)
+        rng = np.random.default_rng(9)
+        xr = rng.standard_normal(s.n)
+        y = sol.apply_op(_dev(xr)).cpu().numpy()
+        rows = rng.choice(s.n, 2000, replace=False)
+        K = op.full()
+        assert np.allclose(y[rows], K[rows] @ xr, rtol=1e-12, atol=1e-12 * np.abs(y).max())
+        x = sol.solve(s.b.copy())
+        st = sol.stats()
+        sol.mesh_setup(s.L)
+        u = sol.mesh_solve(s.mesh_b.copy())
+    assert st["rel_res"] <= 1e-8
+    assert rel_residual(op, x, s.b) <= 1e-8
+    L = to_csr(s.L)
+    g = s.mesh_b.reshape(-1, 3)
+    assert np.linalg.norm(L @ u.reshape(-1, 3) - g) / np.linalg.norm(g) <= 1e-8
