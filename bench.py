@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark of the SCR-FGMRES + AMG path on one GB300 (or N replicas).
+
+One step = the whole linear-solver path of one Newton step on the refined
+straight tube (96 circ x (11 lumen + 5 wall) rings x 400 axial layers:
+616,337 nodes, 2,503,844 block unknowns, 423,857 mesh nodes):
+
+  scr_setup  (upload of A, B, C, D into the solver layout, Shat = D - C
+              diag(A)^{-1} B, AMG hierarchies of A and Shat)
+  scr_solve  (FGMRES + SCR to ||b - calA x|| / ||b|| <= 1e-8, FP64 check)
+  mm_setup + mm_solve  (mesh-motion AMG hierarchy, CG to 1e-8)
+
+The matrices (about 1.5 GB) exceed the 129 MB L2, so no flush is needed
+between steps.  `value` is solves per second over the device-resident
+timed region; `e2e` repeats the step through host pinned buffers (every
+matrix and right-hand side copied in, both solutions copied out).
+
+Multi-GPU: the path does not partition a single solve; with N ranks each
+rank solves its own copy of the workload (independent problems, no
+collective on the data path), `scaling` = "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "tube_large"
+METRIC = "SCR-FGMRES+AMG solves/s to rel-res 1e-8 (mixed vs FP64) on 1 GB300; % HBM peak"
+UNIT = "solves/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--skip-mixed", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# FP64 FMA rate of GB300: 2 FP64 FMA per SM per clock (152 SMs); measured
+# 0.600 TFMA/s at 1995 MHz with an independent-chain FMA loop
+FP64_FMA_PER_SM_CLK = 2
+N_SM = 152
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def allmax(pg, v: float, device):
+    if pg is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def bytes_of_system(s) -> int:
+    n = 0
+    for M in (s.A, s.B, s.C, s.D, s.L):
+        n += M.row_ptr.nbytes + M.col.nbytes + M.val.nbytes
+    return n
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_step_sample(sample_name: str = "tube_small"):
+    """Time one full oracle step (setup, SCR-FGMRES, mesh AMG-CG) on the
+    coarser member of the tube family; returns (seconds, unknowns)."""
+    import fsi_inputs as F
+    from oracle import scr as oscr
+    s = F.tube_system(sample_name)
+    t0 = time.perf_counter()
+    out = oscr.solve_system(s)
+    dt = time.perf_counter() - t0
+    assert out["info"].converged
+    return dt, s.n
+
+
+def cpu_threads() -> int:
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return 1
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle as it stands, on the host cores."""
+    world, rank, local, pg = dist_init()
+    if rank != 0:
+        return
+    import fsi_inputs as F
+    n_large = 3 * F.build_mesh(F.make_params(**F.PRESETS[args.workload])).n_nodes
+    m = F.build_mesh(F.make_params(**F.PRESETS[args.workload]))
+    n_large = 3 * m.n_nodes + m.n_p
+    for _ in range(args.warmup):
+        oracle_step_sample()
+    times = []
+    n_small = None
+    for _ in range(args.steps):
+        dt, n_small = oracle_step_sample()
+        times.append(dt)
+    sec = sum(times) / len(times)
+    scaled = 1.0 / (sec * n_large / n_small)
+    cores = cpu_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": scaled, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * n_large / n_small * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload} (2,503,844 unknowns); each step one full oracle step on "
+                               f"tube_small ({n_small} unknowns), scaled by the unknown ratio",
+                   "precision": "fp64"},
+        "cpu_baseline": {"value": scaled, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"one oracle step (setup + SCR-FGMRES + mesh CG) on tube_small "
+                                   f"({n_small} unknowns) per bench step, {sec:.2f} s each, scaled "
+                                   f"x{n_small / n_large:.5f} to the {n_large}-unknown workload"},
+        "e2e": {"value": scaled, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    world, rank, local, pg = dist_init()
+    import numpy as np
+    import torch
+
+    import fsi_inputs as F
+    import paper_2206_06996_gb300 as pkg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkg.load_library()
+    t_in = time.perf_counter()
+    s = F.tube_system(args.workload)
+    t_in = time.perf_counter() - t_in
+    prec = pkg.SCR_MIXED if args.precision == "mixed" else pkg.SCR_FP64
+
+    Ad, Bd, Cd, Dd, Ld = (pkg.DeviceBSR.from_host(M, device=dev) for M in (s.A, s.B, s.C, s.D, s.L))
+    bd = torch.as_tensor(s.b, device=dev)
+    gd = torch.as_tensor(s.mesh_b, device=dev)
+    xd = torch.empty_like(bd)
+    ud = torch.empty_like(gd)
+    stream = torch.cuda.current_stream(dev)
+
+    def make_solver(p):
+        return pkg.BlockSolver(precision=p)
+
+    def step_device(sol):
+        sol.setup(Ad, Bd, Cd, Dd)
+        sol.solve(bd, xd)
+        sol.mesh_setup(Ld)
+        sol.mesh_solve(gd, ud)
+
+    def timed(sol, fn, k, profile=False):
+        barrier(pg)
+        torch.cuda.synchronize(dev)
+        launches0 = sol.stats()["kernel_launches"]
+        prof = None
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(k):
+            fn(sol)
+            if profile and i == 0:
+                pass
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(pg)
+        ms = e0.elapsed_time(e1) / k
+        launches = (sol.stats()["kernel_launches"] - launches0) // k
+        return ms, launches, prof
+
+    sol = make_solver(prec)
+    for _ in range(args.warmup):
+        step_device(sol)
+    # timed region with the dominant kernel's launches bracketed by events
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(pg)
+    torch.cuda.synchronize(dev)
+    launches0 = sol.stats()["kernel_launches"]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    kprof = None
+    for i in range(args.steps):
+        sol.setup(Ad, Bd, Cd, Dd)
+        if i == 0:
+            sol.profile_begin(pkg.abi.SCR_PROF_SPMV_A, 40000)
+        sol.solve(bd, xd)
+        if i == 0:
+            kprof = sol.profile_end()
+        sol.mesh_setup(Ld)
+        sol.mesh_solve(gd, ud)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(pg)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = (sol.stats()["kernel_launches"] - launches0) // args.steps
+    st = sol.stats()
+    ms = allmax(pg, ms, dev)
+    value = world * 1000.0 / ms
+    # residual check of the timed answer by the same FP64 operator
+    rel_res = st["rel_res"]
+
+    # mixed precision, same step (reported beside the FP64 headline)
+    mixed = None
+    if prec == pkg.SCR_FP64 and not args.skip_mixed:
+        solm = make_solver(pkg.SCR_MIXED)
+        for _ in range(max(1, args.warmup)):
+            step_device(solm)
+        msm, _, _ = timed(solm, step_device, args.steps)
+        stm = solm.stats()
+        msm = allmax(pg, msm, dev)
+        mixed = {"value": world * 1000.0 / msm, "ms_per_step": msm, "outer_iters": stm["outer_iters"],
+                 "rel_res": stm["rel_res"], "speedup_vs_fp64": ms / msm,
+                 "solve_ms": stm["solve_ms"], "setup_ms": stm["setup_ms"]}
+        solm.close()
+
+    # end to end through the public API with host pinned buffers
+    e2e = None
+    if not args.no_e2e:
+        Ah, Bh, Ch, Dh, Lh = (pkg.DeviceBSR.pinned(M) for M in (s.A, s.B, s.C, s.D, s.L))
+        bh = torch.as_tensor(s.b).pin_memory()
+        gh = torch.as_tensor(s.mesh_b).pin_memory()
+        xh = torch.empty_like(bh).pin_memory()
+        uh = torch.empty_like(gh).pin_memory()
+
+        def step_host(sol_):
+            sol_.setup(Ah, Bh, Ch, Dh)
+            sol_.solve(bh, xh)
+            sol_.mesh_setup(Lh)
+            sol_.mesh_solve(gh, uh)
+
+        step_host(sol)
+        mse, _, _ = timed(sol, step_host, args.steps)
+        mse = allmax(pg, mse, dev)
+        h2d = sum(M.nbytes() for M in (Ah, Bh, Ch, Dh, Lh)) + bh.numel() * 8 + gh.numel() * 8
+        d2h = xh.numel() * 8 + uh.numel() * 8
+        e2e = {"value": world * 1000.0 / mse, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": mse}
+
+    if rank != 0:
+        return
+    hbm, peak_kind = peaks()
+    roof = None
+    if kprof and kprof["timed"] > 0:
+        per_launch_s = kprof["ms"] * 1e-3 / kprof["timed"]
+        bytes_pl = kprof["bytes"] / kprof["timed"]
+        flops_pl = kprof["flops"] / kprof["timed"]
+        achieved_gbs = bytes_pl / per_launch_s * 1e-9
+        if prec == pkg.SCR_FP64:
+            # one FP64 FMA per stored value: the FP64 pipe binds before HBM
+            clk = (clocks.get("sm_mhz") or 1995.0) * 1e6
+            fma_peak = FP64_FMA_PER_SM_CLK * N_SM * clk
+            t_alu = flops_pl / 2.0 / fma_peak
+            t_hbm = bytes_pl / (hbm * 1e9)
+            if t_alu > t_hbm:
+                roof = {"bound": "alu", "achieved": flops_pl / per_launch_s * 1e-12,
+                        "peak": 2.0 * fma_peak * 1e-12, "unit": "TFLOP/s",
+                        "frac": (flops_pl / per_launch_s) / (2.0 * fma_peak),
+                        "hbm_achieved_gbs": achieved_gbs, "hbm_frac": achieved_gbs / hbm,
+                        "peak_note": f"FP64 pipe: {FP64_FMA_PER_SM_CLK} FMA/SM/clk x {N_SM} SMs at the median "
+                                     f"sampled SM clock; HBM {peak_kind} {hbm:.0f} GB/s"}
+        if roof is None:
+            roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved_gbs / hbm, "peak_note": f"{peak_kind} HBM copy bandwidth"}
+        roof.update({"kernel": "k_spmv<3,3,1> (level-0 A product)", "launches_per_step": kprof["launches"],
+                     "timed_launches": kprof["timed"], "bytes_per_launch": bytes_pl,
+                     "us_per_launch": per_launch_s * 1e6,
+                     "share_of_step": kprof["ms"] / ms, "traffic": None})
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            dt, n_small = oracle_step_sample()
+            cpu = {"value": 1.0 / (dt * s.n / n_small), "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                   "sample": f"one oracle step (setup + SCR-FGMRES + mesh CG) on tube_small ({n_small} "
+                             f"unknowns) in {dt:.2f} s, scaled x{n_small / s.n:.5f} to the {s.n}-unknown workload"}
+        except Exception as e:  # pragma: no cover
+            cpu = {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle", "sample": f"failed: {e}"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == pkg.SCR_FP64 else "f64+f32",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: straight tube 96x(11+5)x400, {s.n_v} nodes, {s.n} unknowns, "
+                               f"{s.L.nb_rows} mesh nodes", "precision": args.precision,
+                   "step": "scr_setup + scr_solve + mm_setup + mm_solve", "l2": "inputs > L2 (no flush)",
+                   "parallelism": f"replicas x{world}"},
+        "rel_res": rel_res, "outer_iters": st["outer_iters"], "inner_iters": st["a_iters"] + st["s_iters"] + st["i_iters"],
+        "mesh_iters": st["mm_iters"], "setup_ms": st["setup_ms"], "solve_ms": st["solve_ms"],
+        "mm_setup_ms": st["mm_setup_ms"], "mm_solve_ms": st["mm_solve_ms"],
+        "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "mixed": mixed,
+        "clocks": clocks, "inputs_build_s": t_in,
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -197,6 +197,26 @@ int scr_amg_apply(scr_handle h, int which, const double* b, double* x);
 /* Number of levels of hierarchy `which` (0 if not set up). */
 int scr_amg_levels(scr_handle h, int which, int* n_levels);
 
+/* ---------------- kernel timing (CUDA events on the handle's stream) ----
+   Between scr_profile_begin and scr_profile_end every launch of the chosen
+   kernel class is bracketed by a pair of CUDA events recorded on the
+   launching stream; scr_profile_end waits for the stream and returns the
+   launch count, the summed event time and the algorithmic bytes and
+   flops of those launches (bytes: stored values and column indices once,
+   the source vector once, the destination written once plus the vectors
+   the epilogue reads; flops: 2 per stored scalar and right-hand side). */
+#define SCR_PROF_SPMV_A 0   /* products with A (level 0, solver precision) */
+#define SCR_PROF_BLOCK_OP 1 /* the fused calA product */
+typedef struct {
+  long long launches;  /* launches of the class in the region */
+  long long timed;     /* launches with an event pair (capacity-limited) */
+  double ms;           /* summed event time of the timed launches */
+  double bytes;        /* algorithmic bytes of the timed launches */
+  double flops;        /* flops of the timed launches */
+} scr_kprof;
+int scr_profile_begin(scr_handle h, int kernel_class, int capacity);
+int scr_profile_end(scr_handle h, scr_kprof* out);
+
 /* Copy a level operator, prolongator or the aggregates of a hierarchy to
    host arrays in the block CSR layout above.  Call once with NULL arrays to
    receive the sizes, then again with arrays of those sizes. */

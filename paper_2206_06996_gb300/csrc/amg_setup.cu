@@ -471,12 +471,21 @@ void tentative(const int* agg, int nbr, int n_agg, int bs, DBsr<double>& P, Devi
 }
 
 // ------------------------------------------------------------ SpGEMM
-constexpr int kHashSlots = 1024;  // per warp in shared memory
+// Row-wise product C = A * B, one warp per output row.  The symbolic phases
+// insert the column indices of the row's partial products into a hash table
+// (shared memory for short rows; otherwise the warp's private slice of a
+// bounded global scratch, reused row after row by a persistent grid), count
+// them, write them out and sort them.  The numeric phase walks A's row in
+// order and lets the lanes add the products of one B row at a time into the
+// output row (distinct columns per step, so every output entry receives its
+// terms in a fixed order).
+constexpr int kHashSlots = 1024;          // per warp in shared memory
+constexpr int kGlobalSlots = 1 << 16;     // per warp in global scratch
 constexpr int kSpgemmWarps = 4;
 
 __device__ __forceinline__ unsigned hash_col(int c) { return (unsigned)c * 2654435761u; }
 
-__global__ void k_spgemm_ub(DBsr<double> A, DBsr<double> B, int* __restrict__ ub, int* __restrict__ gsize) {
+__global__ void k_spgemm_ub(DBsr<double> A, DBsr<double> B, int* __restrict__ ub) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.nbr) return;
   long long u = 0;
@@ -484,26 +493,32 @@ __global__ void k_spgemm_ub(DBsr<double> A, DBsr<double> B, int* __restrict__ ub
     const int j = A.col[t];
     u += B.rp[j + 1] - B.rp[j];
   }
-  const int ui = (int)min(u, (long long)0x3fffffff);
-  ub[i] = ui;
-  int g = 0;
-  if (ui > kHashSlots / 2) {
-    g = 1;
-    while (g < 2 * ui) g <<= 1;
-  }
-  gsize[i] = g;
+  ub[i] = (int)min(u, (long long)0x3fffffff);
+}
+
+// table size for a row with upper bound ub (0: shared-memory table)
+__device__ __forceinline__ int global_table_size(int ub) {
+  if (ub <= kHashSlots / 2) return 0;
+  int g = 1;
+  while (g < 2 * ub && g < kGlobalSlots) g <<= 1;
+  return g;
 }
 
 // insert the columns of row i of A*B into a warp's hash table; returns the
-// number of new keys this lane inserted
-__device__ int spgemm_insert(const DBsr<double>& A, const DBsr<double>& B, int i, int* table, int hsize, int lane) {
+// number of new keys this lane inserted; a table that fills up sets *err
+__device__ int spgemm_insert(const DBsr<double>& A, const DBsr<double>& B, int i, int* table, int hsize, int lane,
+                             int* err) {
   int mine = 0;
   for (int t = A.rp[i]; t < A.rp[i + 1]; ++t) {
     const int j = A.col[t];
     for (int u = B.rp[j] + lane; u < B.rp[j + 1]; u += 32) {
       const int key = B.col[u];
       unsigned h = hash_col(key) & (hsize - 1);
-      for (;;) {
+      for (int probe = 0;; ++probe) {
+        if (probe >= hsize) {
+          atomicExch(err, 1);
+          return mine;
+        }
         const int prev = atomicCAS(table + h, -1, key);
         if (prev == -1) {
           ++mine;
@@ -518,71 +533,62 @@ __device__ int spgemm_insert(const DBsr<double>& A, const DBsr<double>& B, int i
 }
 
 __global__ void __launch_bounds__(32 * kSpgemmWarps) k_spgemm_count(DBsr<double> A, DBsr<double> B,
-                                                                   const int* __restrict__ ub,
-                                                                   const int* __restrict__ gsize,
-                                                                   const int* __restrict__ goff, int* __restrict__ gtab,
-                                                                   int* __restrict__ cnt) {
+                                                                   const int* __restrict__ ub, int* __restrict__ gtab,
+                                                                   int* __restrict__ cnt, int* __restrict__ err) {
   __shared__ int smem[kSpgemmWarps][kHashSlots];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * kSpgemmWarps + w;
-  if (i >= A.nbr) return;
-  int* table;
-  int hsize;
-  if (gsize[i] > 0) {
-    table = gtab + goff[i];
-    hsize = gsize[i];
-  } else {
-    table = smem[w];
-    hsize = kHashSlots;
+  const int gw = blockIdx.x * kSpgemmWarps + w, nw = gridDim.x * kSpgemmWarps;
+  int* gtab_w = gtab + (long long)gw * kGlobalSlots;
+  for (int i = gw; i < A.nbr; i += nw) {
+    const int gs = global_table_size(ub[i]);
+    int* table = gs ? gtab_w : smem[w];
+    const int hsize = gs ? gs : kHashSlots;
+    for (int h = lane; h < hsize; h += 32) table[h] = -1;
+    __syncwarp();
+    const int mine = spgemm_insert(A, B, i, table, hsize, lane, err);
+    const int tot = warp_sum(mine);
+    if (lane == 0) cnt[i] = tot;
+    __syncwarp();
   }
-  for (int h = lane; h < hsize; h += 32) table[h] = -1;
-  __syncwarp();
-  const int mine = spgemm_insert(A, B, i, table, hsize, lane);
-  const int tot = warp_sum(mine);
-  if (lane == 0) cnt[i] = tot;
-  (void)ub;
 }
 
 __global__ void __launch_bounds__(32 * kSpgemmWarps) k_spgemm_fill(DBsr<double> A, DBsr<double> B,
-                                                                  const int* __restrict__ gsize,
-                                                                  const int* __restrict__ goff, int* __restrict__ gtab,
-                                                                  DBsr<double> C) {
+                                                                  const int* __restrict__ ub, int* __restrict__ gtab,
+                                                                  DBsr<double> C, int* __restrict__ err) {
   __shared__ int smem[kSpgemmWarps][kHashSlots];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * kSpgemmWarps + w;
-  if (i >= A.nbr) return;
-  int* table;
-  int hsize;
-  if (gsize[i] > 0) {
-    table = gtab + goff[i];
-    hsize = gsize[i];
-  } else {
-    table = smem[w];
-    hsize = kHashSlots;
-  }
-  for (int h = lane; h < hsize; h += 32) table[h] = -1;
-  __syncwarp();
-  spgemm_insert(A, B, i, table, hsize, lane);
-  __syncwarp();
-  // compact the keys into the front of C's row (unsorted) ...
-  const int base = C.rp[i], cnt = C.rp[i + 1] - base;
-  int o = 0;
-  for (int h0 = 0; h0 < hsize; h0 += 32) {
-    const int h = h0 + lane;
-    const int key = h < hsize ? table[h] : -1;
-    const unsigned m = __ballot_sync(0xffffffffu, key >= 0);
-    if (key >= 0) C.col[base + o + __popc(m & ((1u << lane) - 1))] = key;
-    o += __popc(m);
-  }
-  __syncwarp();
-  // ... copy them to the table and rank-sort them back into C's row
-  for (int e = lane; e < cnt; e += 32) table[e] = C.col[base + e];
-  __syncwarp();
-  for (int e = lane; e < cnt; e += 32) {
-    const int v = table[e];
-    int rank = 0;
-    for (int f = 0; f < cnt; ++f) rank += table[f] < v;
-    C.col[base + rank] = v;
+  const int gw = blockIdx.x * kSpgemmWarps + w, nw = gridDim.x * kSpgemmWarps;
+  int* gtab_w = gtab + (long long)gw * kGlobalSlots;
+  for (int i = gw; i < A.nbr; i += nw) {
+    const int gs = global_table_size(ub[i]);
+    int* table = gs ? gtab_w : smem[w];
+    const int hsize = gs ? gs : kHashSlots;
+    for (int h = lane; h < hsize; h += 32) table[h] = -1;
+    __syncwarp();
+    spgemm_insert(A, B, i, table, hsize, lane, err);
+    __syncwarp();
+    // compact the keys into the front of C's row (unsorted) ...
+    const int base = C.rp[i], cnt = C.rp[i + 1] - base;
+    int o = 0;
+    for (int h0 = 0; h0 < hsize; h0 += 32) {
+      const int h = h0 + lane;
+      const int key = h < hsize ? table[h] : -1;
+      const unsigned m = __ballot_sync(0xffffffffu, key >= 0);
+      if (key >= 0 && o + __popc(m & ((1u << lane) - 1)) < cnt)
+        C.col[base + o + __popc(m & ((1u << lane) - 1))] = key;
+      o += __popc(m);
+    }
+    __syncwarp();
+    // ... copy them into the table and rank-sort them back into C's row
+    for (int e = lane; e < cnt; e += 32) table[e] = C.col[base + e];
+    __syncwarp();
+    for (int e = lane; e < cnt; e += 32) {
+      const int v = table[e];
+      int rank = 0;
+      for (int f = 0; f < cnt; ++f) rank += table[f] < v;
+      C.col[base + rank] = v;
+    }
+    __syncwarp();
   }
 }
 
@@ -608,6 +614,7 @@ __global__ void __launch_bounds__(32 * kSpgemmWarps) k_spgemm_numeric(DBsr<doubl
     for (int u = lane; u < bk; u += 32) {
       const int c = B.col[bs + u];
       const int pos = find_in_row(C.col, cs, cs + ck, c) - cs;
+      if (pos >= ck) continue;  // cannot happen for a consistent symbolic phase
       double b[BK][BC];
 #pragma unroll
       for (int m = 0; m < BK; ++m)
@@ -627,11 +634,6 @@ __global__ void __launch_bounds__(32 * kSpgemmWarps) k_spgemm_numeric(DBsr<doubl
   }
 }
 
-__global__ void k_goff_sizes(int n, const int* __restrict__ gsize, int* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = gsize[i];
-}
-
 void spgemm(const DBsr<double>& A, const DBsr<double>& B, DBsr<double>& C, DeviceArena& arena, cudaStream_t s) {
   if (A.bc != B.br || A.nbc != B.nbr) throw CudaError{cudaErrorInvalidValue, "spgemm: shape mismatch"};
   DeviceArena tmp(s);
@@ -649,21 +651,26 @@ void spgemm(const DBsr<double>& A, const DBsr<double>& B, DBsr<double>& C, Devic
     return;
   }
   int* ub = tmp.alloc<int>(n);
-  int* gsize = tmp.alloc<int>(n + 1);
-  int* goff = tmp.alloc<int>(n + 1);
   int* cnt = tmp.alloc<int>(n + 1);
-  k_spgemm_ub<<<ceil_div(n, 256), 256, 0, s>>>(A, B, ub, gsize);
+  int* err = tmp.alloc<int>(1);
+  SCR_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+  k_spgemm_ub<<<ceil_div(n, 256), 256, 0, s>>>(A, B, ub);
   SCR_LAUNCH();
-  const long long gtot = exclusive_scan(gsize, goff, n, tmp, s);
-  int* gtab = tmp.alloc<int>(gtot + 1);
-  const int grid = ceil_div(n, kSpgemmWarps);
-  k_spgemm_count<<<grid, 32 * kSpgemmWarps, 0, s>>>(A, B, ub, gsize, goff, gtab, cnt);
+  // persistent grid: 4 blocks of 4 warps per SM, each warp owning a slice
+  const int pgrid = std::min(ceil_div(n, kSpgemmWarps), 4 * sm_count());
+  int* gtab = tmp.alloc<int>((size_t)pgrid * kSpgemmWarps * kGlobalSlots);
+  k_spgemm_count<<<pgrid, 32 * kSpgemmWarps, 0, s>>>(A, B, ub, gtab, cnt, err);
   SCR_LAUNCH();
-  C.nnzb = exclusive_scan(cnt, C.rp, n, tmp, s);
+  C.nnzb = exclusive_scan(cnt, C.rp, n, tmp, s);  // synchronises
+  int herr = 0;
+  SCR_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SCR_CUDA(cudaStreamSynchronize(s));
+  if (herr) throw CudaError{cudaErrorInvalidValue, "spgemm: a product row exceeds the hash-table capacity"};
   C.col = arena.alloc<int>(C.nnzb + 1);
   C.val = arena.alloc<double>(C.nnzb * C.br * C.bc + 1);
-  k_spgemm_fill<<<grid, 32 * kSpgemmWarps, 0, s>>>(A, B, gsize, goff, gtab, C);
+  k_spgemm_fill<<<pgrid, 32 * kSpgemmWarps, 0, s>>>(A, B, ub, gtab, C, err);
   SCR_LAUNCH();
+  const int grid = ceil_div(n, kSpgemmWarps);
   const int br = A.br, bk = A.bc, bc = B.bc;
   if (br == 3 && bk == 3 && bc == 3) k_spgemm_numeric<3, 3, 3><<<grid, 32 * kSpgemmWarps, 0, s>>>(A, B, C);
   else if (br == 1 && bk == 3 && bc == 1) k_spgemm_numeric<1, 3, 1><<<grid, 32 * kSpgemmWarps, 0, s>>>(A, B, C);

@@ -12,6 +12,22 @@ struct LaunchCounter {
 };
 LaunchCounter& counters();
 
+// Event-pair timing of one kernel class (selected by the matrix value
+// pointer for SpMV, or the block operator) inside a profiling region.
+struct KernelProfiler {
+  bool active = false;
+  int kclass = 0;
+  const void* target = nullptr;  // SpMV: value array of the profiled matrix
+  int cap = 0, used = 0;
+  long long launches = 0;
+  double bytes = 0, flops = 0;
+  std::vector<cudaEvent_t> ev;  // 2 * cap
+};
+KernelProfiler& profiler();
+// returns the pair index to close with prof_stop, or -1
+int prof_start(int kclass, const void* key, cudaStream_t s);
+void prof_stop(int idx, double bytes, double flops, cudaStream_t s);
+
 // --------------------------------------------------------------- layouts
 // standard BSR values (block after block, row-major) -> slab layout
 template <typename TO>

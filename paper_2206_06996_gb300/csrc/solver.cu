@@ -117,7 +117,8 @@ struct Hierarchy {
 
   int n_levels() const { return (int)lv.size(); }
 
-  void build(const DBsr<double>& A0, int bs_, int nrhs_, const scr_opts& o, bool use_f32, cudaStream_t s) {
+  void build(const DBsr<double>& A0, int bs_, int nrhs_, const scr_opts& o, bool use_f32, cudaStream_t s,
+             const DBsr<float>* A0f = nullptr) {
     bs = bs_;
     nrhs = nrhs_;
     nu = std::max(1, o.amg_nu);
@@ -191,7 +192,7 @@ struct Hierarchy {
         L.r = ar.alloc<double>(m);
         L.t = ar.alloc<double>(m);
       } else {
-        L.Af = to_float_copy(L.A, ar, s);
+        L.Af = (l == 0 && A0f) ? *A0f : to_float_copy(L.A, ar, s);
         if (L.P.nbr) {
           L.Pf = to_float_copy(L.P, ar, s);
           L.Rf = to_float_copy(L.R, ar, s);
@@ -724,7 +725,13 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
       SCR_CUDA(cudaStreamSynchronize(s));
     }
     const bool f32 = h->o.precision == SCR_MIXED;
-    h->hA.build(h->A, 3, 1, h->o, f32, s);
+    if (f32) {
+      h->Af = float_copy(h->A, a, s);
+      h->Bf = float_copy(h->B, a, s);
+      h->Cf = float_copy(h->C, a, s);
+      h->Df = float_copy(h->D, a, s);
+    }
+    h->hA.build(h->A, 3, 1, h->o, f32, s, f32 ? &h->Af : nullptr);
     h->hS.build(h->Shat, 1, 1, h->o, f32, s);
     // workspaces
     h->work.reset(new DeviceArena(s));
@@ -736,10 +743,6 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
     h->xvec = w.alloc<double>(n + 1);
     h->rvec = w.alloc<double>(n + 1);
     if (f32) {
-      h->Af = float_copy(h->A, a, s);
-      h->Bf = float_copy(h->B, a, s);
-      h->Cf = float_copy(h->C, a, s);
-      h->Df = float_copy(h->D, a, s);
       h->gAf.init(w, nv3, h->o.restart_inner);
       h->gSf.init(w, np, h->o.restart_inner);
       h->gIf.init(w, nv3, h->o.restart_inner);
@@ -1093,6 +1096,51 @@ int scr_export(scr_handle h, int which, int level, int kind, scr_bsr_out* out) {
     SCR_CUDA(cudaMemcpyAsync(out->col_idx, M->col, sizeof(int) * M->nnzb, cudaMemcpyDeviceToHost, h->s));
     SCR_CUDA(cudaMemcpyAsync(out->val, v, sizeof(double) * nv, cudaMemcpyDeviceToHost, h->s));
     SCR_CUDA(cudaStreamSynchronize(h->s));
+  });
+}
+
+int scr_profile_begin(scr_handle h, int kclass, int capacity) {
+  if (!h || capacity < 0 || (kclass != SCR_PROF_SPMV_A && kclass != SCR_PROF_BLOCK_OP)) return SCR_INVALID_ARG;
+  if (!h->have_block) {
+    set_last_error("scr_profile_begin before scr_setup");
+    return SCR_INVALID_ARG;
+  }
+  return guarded([&] {
+    KernelProfiler& p = profiler();
+    while ((int)p.ev.size() < 2 * capacity) {
+      cudaEvent_t e;
+      SCR_CUDA(cudaEventCreate(&e));
+      p.ev.push_back(e);
+    }
+    p.active = true;
+    p.kclass = kclass;
+    p.target = kclass == SCR_PROF_SPMV_A
+                   ? (h->o.precision == SCR_MIXED ? (const void*)h->Af.val : (const void*)h->A.val)
+                   : nullptr;
+    p.cap = capacity;
+    p.used = 0;
+    p.launches = 0;
+    p.bytes = p.flops = 0;
+  });
+}
+
+int scr_profile_end(scr_handle h, scr_kprof* out) {
+  if (!h || !out) return SCR_INVALID_ARG;
+  return guarded([&] {
+    KernelProfiler& p = profiler();
+    SCR_CUDA(cudaStreamSynchronize(h->s));
+    double ms = 0;
+    for (int i = 0; i < p.used; ++i) {
+      float t = 0;
+      SCR_CUDA(cudaEventElapsedTime(&t, p.ev[2 * i], p.ev[2 * i + 1]));
+      ms += t;
+    }
+    out->launches = p.launches;
+    out->timed = p.used;
+    out->ms = ms;
+    out->bytes = p.bytes;
+    out->flops = p.flops;
+    p.active = false;
   });
 }
 

@@ -20,6 +20,29 @@ LaunchCounter& counters() {
   return c;
 }
 
+KernelProfiler& profiler() {
+  static KernelProfiler p;
+  return p;
+}
+
+int prof_start(int kclass, const void* key, cudaStream_t s) {
+  KernelProfiler& p = profiler();
+  if (!p.active || p.kclass != kclass || (key && key != p.target)) return -1;
+  p.launches++;
+  if (p.used >= p.cap) return -1;
+  const int i = p.used++;
+  SCR_CUDA(cudaEventRecord(p.ev[2 * i], s));
+  return i;
+}
+
+void prof_stop(int idx, double bytes, double flops, cudaStream_t s) {
+  if (idx < 0) return;
+  KernelProfiler& p = profiler();
+  SCR_CUDA(cudaEventRecord(p.ev[2 * idx + 1], s));
+  p.bytes += bytes;
+  p.flops += flops;
+}
+
 int sm_count() {
   static int n = 0;
   if (!n) {
@@ -215,6 +238,7 @@ void spmv(const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const EpiArgs& e, cud
   if (M.nbr == 0) return;
   const int G = pick_group(M);
   const int br = M.br, bc = M.bc;
+  const int pidx = prof_start(0, M.val, s);
 #define SCR_SPMV_CASE(BR_, BC_, NR_)                                            \
   if (br == BR_ && bc == BC_ && nrhs == NR_) {                                  \
     if (G == 2) launch_spmv_e<BR_, BC_, NR_, 2, VT, XT>(M, x, y, e, s);         \
@@ -231,8 +255,18 @@ void spmv(const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const EpiArgs& e, cud
   throw CudaError{cudaErrorInvalidValue, "spmv: unsupported block shape"};
 done:
   counters().launches++;
-  counters().spmv_bytes += M.nnzb * (long long)(M.br * M.bc * sizeof(VT) + sizeof(int)) +
-                           (long long)M.nbr * M.br * nrhs * sizeof(XT) * (e.kind == Epi::Set ? 1 : 2);
+  {
+    // algorithmic bytes: stored values + column indices + row pointers once,
+    // the source vector once, the result written once, plus what the
+    // epilogue reads (z, the current iterate, the inverse diagonal)
+    const double nrow = (double)M.nbr * M.br;
+    double b = (double)M.nnzb * (M.br * M.bc * sizeof(VT) + sizeof(int)) + (M.nbr + 1.0) * sizeof(int) +
+               (double)M.nbc * M.bc * nrhs * sizeof(XT) + nrow * nrhs * sizeof(XT);
+    if (e.kind == Epi::Resid || (e.kind == Epi::Axpby && e.z)) b += nrow * nrhs * sizeof(XT);
+    if (e.kind == Epi::Jacobi) b += 2.0 * nrow * nrhs * sizeof(XT) + nrow * sizeof(XT);
+    counters().spmv_bytes += (long long)b;
+    prof_stop(pidx, b, 2.0 * (double)M.nnzb * M.br * M.bc * nrhs, s);
+  }
 }
 
 template void spmv<double, double>(const DBsr<double>&, const double*, double*, int, const EpiArgs&, cudaStream_t);
@@ -274,15 +308,17 @@ void block_op(const DBsr<double>& A, const DBsr<double>& B, const DBsr<double>& 
   if (rows == 0) return;
   constexpr int G = 4;
   const long long threads = rows * G;
+  const int pidx = prof_start(1, nullptr, s);
   if (resid)
     k_block_op<G, true><<<ceil_div(threads, 256), 256, 0, s>>>(nv, np, A, B, C, D, x, y, z);
   else
     k_block_op<G, false><<<ceil_div(threads, 256), 256, 0, s>>>(nv, np, A, B, C, D, x, y, z);
   SCR_LAUNCH();
   counters().launches++;
-  const long long nnzb = A.nnzb + B.nnzb + C.nnzb + D.nnzb;
-  counters().spmv_bytes += A.nnzb * 76 + B.nnzb * 28 + C.nnzb * 28 + D.nnzb * 12 + rows * 8 * (resid ? 2 : 1);
-  (void)nnzb;
+  const double b = A.nnzb * 76.0 + B.nnzb * 28.0 + C.nnzb * 28.0 + D.nnzb * 12.0 +
+                   (A.nbr + D.nbr + 2.0) * 8.0 + rows * 8.0 * (resid ? 3 : 2);
+  counters().spmv_bytes += (long long)b;
+  prof_stop(pidx, b, 2.0 * (9.0 * A.nnzb + 3.0 * B.nnzb + 3.0 * C.nnzb + D.nnzb), s);
 }
 
 }  // namespace scr

@@ -6,7 +6,7 @@ import dataclasses
 
 import numpy as np
 
-from .abi import (BsrOut, Bsr, Opts, SCR_NOT_CONVERGED, SCR_OK, ScrError, Stats, check,
+from .abi import (BsrOut, Bsr, KProf, Opts, SCR_NOT_CONVERGED, SCR_OK, ScrError, Stats, check,
                   load_library)
 
 
@@ -27,6 +27,17 @@ class DeviceBSR:
     val: object      # torch.float64
 
     @classmethod
+    def pinned(cls, M):
+        """Host copy in page-locked memory (fast host-to-device copies)."""
+        torch = _torch()
+        t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a, dtype=dt)).pin_memory()
+        return cls(M.br, M.bc, M.nb_rows, M.nb_cols, t(M.row_ptr, np.int32), t(M.col, np.int32),
+                   t(M.val, np.float64))
+
+    def nbytes(self) -> int:
+        return sum(int(a.numel() * a.element_size()) for a in (self.row_ptr, self.col, self.val))
+
+    @classmethod
     def from_host(cls, M, device="cuda"):
         torch = _torch()
         return cls(M.br, M.bc, M.nb_rows, M.nb_cols,
@@ -40,12 +51,13 @@ class DeviceBSR:
 
 
 def _as_bsr(M, keep: list) -> tuple[Bsr, int]:
-    """(C struct, ptr_is_device) for a host (numpy) or device (torch) matrix."""
+    """(C struct, ptr_is_device) for a host (numpy), pinned-host or device
+    (torch) matrix."""
     if isinstance(M, DeviceBSR):
         s = Bsr(M.nb_rows, M.nb_cols, M.br, M.bc, M.nnzb, M.row_ptr.data_ptr(), M.col.data_ptr(),
                 M.val.data_ptr())
         keep.append(M)
-        return s, 1
+        return s, int(M.row_ptr.is_cuda)
     rp = np.ascontiguousarray(M.row_ptr, dtype=np.int32)
     col = np.ascontiguousarray(M.col, dtype=np.int32)
     val = np.ascontiguousarray(M.val, dtype=np.float64)
@@ -184,6 +196,14 @@ class BlockSolver:
         y = torch.empty(n_out, dtype=torch.float64, device=x.device)
         check(fn(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr())))
         return y
+
+    def profile_begin(self, kernel_class: int = 0, capacity: int = 20000):
+        check(self.lib.scr_profile_begin(self.h, kernel_class, capacity))
+
+    def profile_end(self) -> dict:
+        p = KProf()
+        check(self.lib.scr_profile_end(self.h, C.byref(p)))
+        return {f: getattr(p, f) for f, _ in KProf._fields_}
 
     def apply_op(self, x):
         return self._dev2(self.lib.scr_apply_op, x, 3 * self.n_v + self.n_p)
