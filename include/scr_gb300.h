@@ -89,6 +89,11 @@ typedef struct {
   int amg_max_levels; /* 10 */
   int amg_coarse_size;/* block rows at which coarsening stops, 64 */
   int amg_nu;         /* l1-Jacobi sweeps before and after the coarse correction, 1 */
+  double amg_trunc;   /* prolongator truncation factor (AMG settings table: 0.3) */
+  int amg_pmax;       /* at most this many blocks per prolongator row (AMG settings table: 5; 0 = no cap) */
+  int autotune;       /* 1: time the SpMV lane-group widths at set-up and keep the fastest */
+  int amg_smoother;   /* 0: l1-Jacobi (amg_nu sweeps); 1: Chebyshev on D^{-1}A (default) */
+  int amg_degree;     /* Chebyshev degree, 3 */
   double mm_rtol;     /* mesh CG relative residual, 1e-8 */
   int mm_max_it;      /* mesh CG iteration cap, 500 */
   int verbose;        /* 0 quiet */
@@ -100,6 +105,9 @@ typedef struct {
   const int* col_idx;
   const double* val;
 } scr_bsr;
+
+#define SCR_SMOOTH_L1 0
+#define SCR_SMOOTH_CHEB 1
 
 /* destination of scr_export (host pointers; pass NULL arrays to query sizes) */
 typedef struct {

@@ -17,12 +17,21 @@ statement of that method (Vanek, Mandel, Brezina 1996):
    P_tent[i, a] = I_bs / sqrt(|a|) for node i in aggregate a;
 4. smoothed prolongator P = (I - omega D^{-1} A) P_tent with D the scalar
    diagonal of A and omega = 4 / (3 lambda), lambda the Gershgorin bound
-   max_i sum_j |a_ij| / |a_ii| of D^{-1} A;
+   max_i sum_j |a_ij| / |a_ii| of D^{-1} A, then truncated as the paper's
+   AMG settings do for interpolation (truncation factor, at most P_max
+   entries per row; table of AMG settings, Sec. 5.2): in each block row keep
+   the blocks whose Frobenius norm is at least trunc times the row's largest
+   and, among those, the P_max largest (ties: smaller column first); each
+   scalar row is rescaled so that its sum is unchanged;
 5. Galerkin coarse operator A_c = P^T A P, restriction R = P^T;
-6. V-cycle: l1-Jacobi smoothing x <- x + D_l1^{-1} (b - A x) with
-   D_l1 = diag(sum_j |a_ij|), nu_pre sweeps from x = 0, residual,
-   restriction, recursion, prolongation, nu_post sweeps; exact dense LU
-   on the coarsest level.
+6. V-cycle: pre-smoothing from x = 0, residual, restriction, recursion,
+   prolongation, post-smoothing; exact dense LU on the coarsest level.
+   Smoothers: l1-Jacobi x <- x + D_l1^{-1} (b - A x), D_l1 = diag(sum_j
+   |a_ij|) (nu sweeps), or Chebyshev of degree k on D^{-1} A over
+   [lambda/30, lambda], lambda = 1.1 x the power-iteration estimate of the
+   largest eigenvalue of D^{-1} A (20 iterations from a fixed start
+   vector), written as the three-term recurrence of Chebyshev acceleration
+   (Saad, Iterative Methods for Sparse Linear Systems, Alg. 12.1).
 """
 from __future__ import annotations
 
@@ -42,6 +51,8 @@ class Level:
     R: sp.csr_matrix | None = None
     agg: np.ndarray | None = None
     omega: float = 0.0
+    dinv: np.ndarray | None = None   # 1 / diag(A)
+    lam: float = 0.0                 # 1.1 x power-iteration estimate of rho(D^{-1} A)
 
 
 @dataclasses.dataclass
@@ -50,6 +61,8 @@ class Hierarchy:
     coarse_lu: tuple
     nu_pre: int = 1
     nu_post: int = 1
+    smoother: str = "l1"     # "l1" or "cheb"
+    cheb_degree: int = 3
 
     @property
     def n_levels(self) -> int:
@@ -159,12 +172,118 @@ def smoothed_prolongator(A: sp.csr_matrix, Pt: sp.csr_matrix):
     return P, omega
 
 
+def truncate_prolongator(P: sp.csr_matrix, bs: int, trunc: float, pmax: int) -> sp.csr_matrix:
+    """Interpolation truncation of step 4 (blocks of size bs)."""
+    if trunc <= 0.0 and pmax <= 0:
+        return P
+    B = sp.bsr_matrix(P, blocksize=(bs, bs))
+    B.sort_indices()
+    nbr = B.shape[0] // bs
+    rows = np.repeat(np.arange(nbr), np.diff(B.indptr))
+    cols = B.indices
+    norms = np.sqrt((B.data ** 2).sum(axis=(1, 2)))
+    rowmax = np.zeros(nbr)
+    np.maximum.at(rowmax, rows, norms)
+    keep = (norms > 0) & (norms >= trunc * rowmax[rows])
+    if pmax > 0:
+        # rank within the row by (norm descending, column ascending)
+        order = np.lexsort((cols, -norms, rows))
+        rank = np.empty_like(order)
+        start = B.indptr[rows[order]]
+        rank[order] = np.arange(order.size) - start
+        # ranks count every block; the candidate set is a prefix of that order
+        cand_rank = np.zeros_like(rank)
+        kept_sorted = keep[order]
+        csum = np.cumsum(kept_sorted)
+        row_first = B.indptr[:-1]
+        before = np.zeros(nbr, dtype=np.int64)
+        nz = np.diff(B.indptr) > 0
+        before[nz] = (csum - kept_sorted)[row_first[nz] - 0]
+        cand_rank[order] = csum - kept_sorted - before[rows[order]]
+        keep &= cand_rank < pmax
+    data = B.data.copy()
+    # row sums per scalar row before and after
+    s_all = np.zeros((nbr, bs))
+    s_kept = np.zeros((nbr, bs))
+    np.add.at(s_all, rows, data.sum(axis=2))
+    np.add.at(s_kept, rows, (data * keep[:, None, None]).sum(axis=2))
+    scale = np.where(s_kept != 0.0, s_all / np.where(s_kept != 0.0, s_kept, 1.0), 1.0)
+    data = data * scale[rows][:, :, None]
+    k = np.nonzero(keep)[0]
+    indptr = np.concatenate([[0], np.cumsum(np.bincount(rows[k], minlength=nbr))])
+    out = sp.bsr_matrix((data[k], cols[k], indptr), shape=P.shape).tocsr()
+    out.sort_indices()
+    return out
+
+
+POWER_ITERS = 20
+
+
+def power_start(n: int) -> np.ndarray:
+    """Fixed start vector 1 + ((i * 2654435761) mod 2^32 mod 1000) / 1000."""
+    i = np.arange(n, dtype=np.uint64)
+    return 1.0 + (((i * np.uint64(2654435761)) % np.uint64(2 ** 32)) % np.uint64(1000)).astype(np.float64) / 1000.0
+
+
+def power_lambda(A: sp.csr_matrix, dinv: np.ndarray, iters: int = POWER_ITERS) -> float:
+    """Power iteration on D^{-1} A: v <- w / ||w||, w = D^{-1} A v, from the
+    normalised fixed start vector; returns 1.1 ||w|| of the last step."""
+    v = power_start(A.shape[0])
+    v = v / np.linalg.norm(v)
+    lam = 0.0
+    for _ in range(iters):
+        w = (A @ v) * dinv
+        lam = np.linalg.norm(w)
+        if lam == 0.0:
+            break
+        v = w / lam
+    return 1.1 * lam
+
+
+def cheb_coefficients(lam: float, degree: int):
+    """theta and the (alpha_j, beta_j) of the Chebyshev recurrence on
+    [lam/30, lam]."""
+    lo, hi = lam / 30.0, lam
+    theta, delta = (hi + lo) / 2.0, (hi - lo) / 2.0
+    sigma = theta / delta
+    rho = 1.0 / sigma
+    steps = []
+    for _ in range(degree - 1):
+        rho_new = 1.0 / (2.0 * sigma - rho)
+        steps.append((rho_new * rho, 2.0 * rho_new / delta))
+        rho = rho_new
+    return theta, steps
+
+
+def cheb_smooth(A, dinv, lam, degree, x, b, from_zero: bool):
+    """Degree-`degree` Chebyshev smoothing of A x = b (preconditioned by
+    D^{-1}); x may be (n,) or (n, k)."""
+    theta, steps = cheb_coefficients(lam, degree)
+    dv = dinv if b.ndim == 1 else dinv[:, None]
+    r = b * dv if from_zero else (b - A @ x) * dv
+    d = r / theta
+    x = d.copy() if from_zero else x + d
+    for a, c in steps:
+        r = r - (A @ d) * dv
+        d = a * d + c * r
+        x = x + d
+    return x
+
+
 def l1_diag(A: sp.csr_matrix) -> np.ndarray:
     return np.asarray(abs(A).sum(axis=1)).ravel()
 
 
+def _finish_levels(levels, smoother: str):
+    for lev in levels:
+        lev.dinv = 1.0 / lev.A.diagonal()
+        if smoother == "cheb":
+            lev.lam = power_lambda(lev.A, lev.dinv)
+
+
 def setup(A: sp.csr_matrix, bs: int, theta: float = 0.08, max_levels: int = 10,
-          coarse_size: int = 64, nu_pre: int = 1, nu_post: int = 1) -> Hierarchy:
+          coarse_size: int = 64, nu_pre: int = 1, nu_post: int = 1, trunc: float = 0.0,
+          pmax: int = 0, smoother: str = "l1", cheb_degree: int = 3) -> Hierarchy:
     """Build the hierarchy (steps 1-5); coarse_size counts block rows."""
     levels = []
     Al = A.tocsr()
@@ -181,6 +300,7 @@ def setup(A: sp.csr_matrix, bs: int, theta: float = 0.08, max_levels: int = 10,
             break
         Pt = tentative_prolongator(agg, bs)
         P, omega = smoothed_prolongator(Al, Pt)
+        P = truncate_prolongator(P, bs, trunc, pmax)
         R = P.T.tocsr()
         Ac = (R @ Al @ P).tocsr()
         Ac.sum_duplicates()
@@ -188,10 +308,13 @@ def setup(A: sp.csr_matrix, bs: int, theta: float = 0.08, max_levels: int = 10,
         lev.P, lev.R, lev.agg, lev.omega = P, R, agg, omega
         Al = Ac
     lu = sla.lu_factor(levels[-1].A.toarray())
-    return Hierarchy(levels=levels, coarse_lu=lu, nu_pre=nu_pre, nu_post=nu_post)
+    _finish_levels(levels, smoother)
+    return Hierarchy(levels=levels, coarse_lu=lu, nu_pre=nu_pre, nu_post=nu_post, smoother=smoother,
+                     cheb_degree=cheb_degree)
 
 
-def hierarchy_from_matrices(As, Ps, bs: int, nu_pre: int = 1, nu_post: int = 1) -> Hierarchy:
+def hierarchy_from_matrices(As, Ps, bs: int, nu_pre: int = 1, nu_post: int = 1, smoother: str = "l1",
+                            cheb_degree: int = 3) -> Hierarchy:
     """A hierarchy from given operators (A_0..A_L) and prolongators
     (P_0..P_{L-1}), e.g. ones exported from another implementation."""
     levels = []
@@ -203,7 +326,9 @@ def hierarchy_from_matrices(As, Ps, bs: int, nu_pre: int = 1, nu_post: int = 1) 
             lev.R = lev.P.T.tocsr()
         levels.append(lev)
     lu = sla.lu_factor(levels[-1].A.toarray())
-    return Hierarchy(levels=levels, coarse_lu=lu, nu_pre=nu_pre, nu_post=nu_post)
+    _finish_levels(levels, smoother)
+    return Hierarchy(levels=levels, coarse_lu=lu, nu_pre=nu_pre, nu_post=nu_post, smoother=smoother,
+                     cheb_degree=cheb_degree)
 
 
 def vcycle(H: Hierarchy, b: np.ndarray, level: int = 0) -> np.ndarray:
@@ -212,6 +337,11 @@ def vcycle(H: Hierarchy, b: np.ndarray, level: int = 0) -> np.ndarray:
     b = np.asarray(b, dtype=np.float64)
     if level == H.n_levels - 1:
         return sla.lu_solve(H.coarse_lu, b)
+    if H.smoother == "cheb":
+        x = cheb_smooth(lev.A, lev.dinv, lev.lam, H.cheb_degree, None, b, True)
+        r = b - lev.A @ x
+        x = x + lev.P @ vcycle(H, lev.R @ r, level + 1)
+        return cheb_smooth(lev.A, lev.dinv, lev.lam, H.cheb_degree, x, b, False)
     d = lev.dl1 if b.ndim == 1 else lev.dl1[:, None]
     x = np.zeros_like(b)
     for _ in range(H.nu_pre):

@@ -45,6 +45,10 @@ class SolverOptions:
     amg_coarse: int = 64
     amg_max_levels: int = 10
     nu: int = 1
+    amg_trunc: float = 0.3
+    amg_pmax: int = 5
+    smoother: str = "cheb"
+    cheb_degree: int = 3
     mm_rtol: float = 1e-8
     mm_max_it: int = 500
 
@@ -64,8 +68,10 @@ class SCRSolver:
         self.op = BlockOperator.from_system(system)
         o = self.opts
         self.Shat = schur_hat(self.op)
-        self.amg_A = amg.setup(self.op.A, 3, o.amg_theta, o.amg_max_levels, o.amg_coarse, o.nu, o.nu)
-        self.amg_S = amg.setup(self.Shat, 1, o.amg_theta, o.amg_max_levels, o.amg_coarse, o.nu, o.nu)
+        self.amg_A = amg.setup(self.op.A, 3, o.amg_theta, o.amg_max_levels, o.amg_coarse, o.nu, o.nu,
+                               o.amg_trunc, o.amg_pmax, o.smoother, o.cheb_degree)
+        self.amg_S = amg.setup(self.Shat, 1, o.amg_theta, o.amg_max_levels, o.amg_coarse, o.nu, o.nu,
+                               o.amg_trunc, o.amg_pmax, o.smoother, o.cheb_degree)
         self.cnt = Counters()
 
     # Algorithm 2 ------------------------------------------------------
@@ -119,7 +125,8 @@ class MeshSolver:
         self.opts = opts or SolverOptions()
         o = self.opts
         self.L = to_csr(system.L)
-        self.H = amg.setup(self.L, 1, o.amg_theta, o.amg_max_levels, o.amg_coarse, o.nu, o.nu)
+        self.H = amg.setup(self.L, 1, o.amg_theta, o.amg_max_levels, o.amg_coarse, o.nu, o.nu,
+                           o.amg_trunc, o.amg_pmax, o.smoother, o.cheb_degree)
 
     def solve(self, g: np.ndarray, tol: float | None = None):
         o = self.opts

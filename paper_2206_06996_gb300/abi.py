@@ -28,7 +28,9 @@ class Opts(C.Structure):
         ("max_A", C.c_int), ("max_S", C.c_int), ("max_I", C.c_int), ("restart_inner", C.c_int),
         ("precision", C.c_int), ("precond", C.c_int),
         ("amg_theta", C.c_double), ("amg_max_levels", C.c_int), ("amg_coarse_size", C.c_int),
-        ("amg_nu", C.c_int), ("mm_rtol", C.c_double), ("mm_max_it", C.c_int), ("verbose", C.c_int),
+        ("amg_nu", C.c_int), ("amg_trunc", C.c_double), ("amg_pmax", C.c_int), ("autotune", C.c_int),
+        ("amg_smoother", C.c_int), ("amg_degree", C.c_int),
+        ("mm_rtol", C.c_double), ("mm_max_it", C.c_int), ("verbose", C.c_int),
     ]
 
 

@@ -125,6 +125,67 @@ void diag_scalar(const DBsr<double>& A, double* d, int* bad, cudaStream_t s) {
   counters().launches++;
 }
 
+// per scalar row: 1 / a_ii
+__global__ void k_inv_diag(DBsr<double> A, double* __restrict__ dinv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.nbr) return;
+  const int s = A.rp[i], e = A.rp[i + 1], k = e - s;
+  const int p = find_in_row(A.col, s, e, i);
+  for (int r = 0; r < A.br; ++r) {
+    double v = 0.0;
+    if (p < e && A.col[p] == i) v = A.val[slab_index(s, k, p - s, r, r, A.br, A.bc)];
+    dinv[(long long)i * A.br + r] = v != 0.0 ? 1.0 / v : 0.0;
+  }
+}
+
+void inv_diag(const DBsr<double>& A, double* dinv, cudaStream_t s) {
+  if (A.nbr == 0) return;
+  k_inv_diag<<<ceil_div(A.nbr, 256), 256, 0, s>>>(A, dinv);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
+// start vector of the power iteration: 1 + ((i * 2654435761) mod 2^32 mod 1000) / 1000
+__global__ void k_power_start(double* __restrict__ v, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned h = (unsigned)((unsigned long long)i * 2654435761ULL);
+  v[i] = 1.0 + (double)(h % 1000u) / 1000.0;
+}
+
+__global__ void k_rsqrt_scalar(const double* __restrict__ in, double* __restrict__ out) {
+  const double v = *in;
+  *out = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
+}
+
+double power_lambda(const DBsr<double>& A, const double* dinv, int iters, cudaStream_t s) {
+  const long long n = (long long)A.nbr * A.br;
+  if (n == 0) return 0.0;
+  DeviceArena tmp(s);
+  Reducer red = make_reducer(tmp);
+  double* v = tmp.alloc<double>(n);
+  double* w = tmp.alloc<double>(n);
+  double* nrm = tmp.alloc<double>(2);
+  k_power_start<<<ceil_div(n, 256), 256, 0, s>>>(v, n);
+  SCR_LAUNCH();
+  norm2<double>(v, n, nrm, red, s);
+  k_rsqrt_scalar<<<1, 1, 0, s>>>(nrm, nrm + 1);
+  scale_by<double>(v, nrm + 1, v, n, s);
+  for (int it = 0; it < iters; ++it) {
+    spmv<double, double>(A, v, w, 1, EpiArgs(), s);
+    diag_scale<double>(w, dinv, w, n, 1, s);
+    norm2<double>(w, n, nrm, red, s);
+    k_rsqrt_scalar<<<1, 1, 0, s>>>(nrm, nrm + 1);
+    scale_by<double>(w, nrm + 1, v, n, s);
+  }
+  SCR_LAUNCH();
+  double h = 0.0;
+  SCR_CUDA(cudaMemcpyAsync(&h, nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+  SCR_CUDA(cudaStreamSynchronize(s));
+  counters().launches += 2 + 2 * iters;
+  return 1.1 * std::sqrt(h);
+}
+
 // per scalar row: 1 / sum_j |a_ij|
 __global__ void k_l1_inv(DBsr<double> A, double* __restrict__ dinv) {
   const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -749,6 +810,130 @@ void spadd(const DBsr<double>& A, double alpha, const DBsr<double>& B, const dou
   SCR_CUDA(cudaStreamSynchronize(s));
 }
 
+// ------------------------------------------------------------ truncation
+// Per block row: the candidates are the blocks with norm >= trunc * row max
+// (and > 0); when more than pmax remain, the pmax-th candidate in the order
+// (norm descending, column ascending) becomes the cut (cn, cc): a candidate
+// is kept iff norm > cn or (norm == cn and col <= cc).
+__global__ void k_trunc_select(DBsr<double> P, const double* __restrict__ norms, double trunc, int pmax,
+                               double* __restrict__ tmin, double* __restrict__ cn, int* __restrict__ cc,
+                               int* __restrict__ cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.nbr) return;
+  const int s = P.rp[i], e = P.rp[i + 1];
+  double m = 0.0;
+  for (int t = s; t < e; ++t) m = fmax(m, norms[t]);
+  const double lo = trunc * m;
+  int ncand = 0;
+  for (int t = s; t < e; ++t) ncand += (norms[t] > 0.0 && norms[t] >= lo);
+  double pn = INFINITY;
+  int pc = -1;
+  int kept = ncand;
+  if (pmax > 0 && ncand > pmax) {
+    for (int q = 0; q < pmax; ++q) {
+      double bn = -1.0;
+      int bc = 0x7fffffff;
+      for (int t = s; t < e; ++t) {
+        const double v = norms[t];
+        const int c = P.col[t];
+        if (!(v > 0.0 && v >= lo)) continue;
+        const bool after = v < pn || (v == pn && c > pc);
+        if (!after) continue;
+        if (v > bn || (v == bn && c < bc)) {
+          bn = v;
+          bc = c;
+        }
+      }
+      pn = bn;
+      pc = bc;
+    }
+    kept = pmax;
+  } else {
+    pn = -1.0;
+    pc = 0x7fffffff;
+  }
+  tmin[i] = lo;
+  cn[i] = pn;
+  cc[i] = pc;
+  cnt[i] = kept;
+}
+
+__device__ __forceinline__ bool trunc_kept(double v, int c, double lo, double cn, int cc) {
+  return v > 0.0 && v >= lo && (v > cn || (v == cn && c <= cc));
+}
+
+__global__ void k_trunc_fill(DBsr<double> P, const double* __restrict__ norms, const double* __restrict__ tmin,
+                             const double* __restrict__ cn, const int* __restrict__ cc, DBsr<double> O) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.nbr) return;
+  const int BR = P.br, BC = P.bc;
+  const int s = P.rp[i], k = P.rp[i + 1] - s;
+  const int os = O.rp[i], ok = O.rp[i + 1] - os;
+  for (int r = 0; r < BR; ++r) {
+    double sall = 0.0, skept = 0.0;
+    for (int t = 0; t < k; ++t) {
+      const bool kp = trunc_kept(norms[s + t], P.col[s + t], tmin[i], cn[i], cc[i]);
+      for (int c = 0; c < BC; ++c) {
+        const double v = P.val[slab_index(s, k, t, r, c, BR, BC)];
+        sall += v;
+        if (kp) skept += v;
+      }
+    }
+    const double sc = skept != 0.0 ? sall / skept : 1.0;
+    int o = 0;
+    for (int t = 0; t < k; ++t) {
+      if (!trunc_kept(norms[s + t], P.col[s + t], tmin[i], cn[i], cc[i])) continue;
+      if (r == 0) O.col[os + o] = P.col[s + t];
+      for (int c = 0; c < BC; ++c) O.val[slab_index(os, ok, o, r, c, BR, BC)] = P.val[slab_index(s, k, t, r, c, BR, BC)] * sc;
+      ++o;
+    }
+  }
+}
+
+__global__ void k_row_block_norms(DBsr<double> A, double* __restrict__ bnorm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.nbr) return;
+  const int s = A.rp[i], k = A.rp[i + 1] - s;
+  for (int t = 0; t < k; ++t) {
+    double acc = 0.0;
+    for (int r = 0; r < A.br; ++r)
+      for (int c = 0; c < A.bc; ++c) {
+        const double v = A.val[slab_index(s, k, t, r, c, A.br, A.bc)];
+        acc += v * v;
+      }
+    bnorm[s + t] = sqrt(acc);
+  }
+}
+
+void truncate_rows(const DBsr<double>& P, double trunc, int pmax, DBsr<double>& O, DeviceArena& a, cudaStream_t s) {
+  DeviceArena tmp(s);
+  const int n = P.nbr;
+  O.nbr = n;
+  O.nbc = P.nbc;
+  O.br = P.br;
+  O.bc = P.bc;
+  O.rp = a.alloc<int>(n + 1);
+  double* norms = tmp.alloc<double>(P.nnzb + 1);
+  double* tmin = tmp.alloc<double>(n + 1);
+  double* cn = tmp.alloc<double>(n + 1);
+  int* cc = tmp.alloc<int>(n + 1);
+  int* cnt = tmp.alloc<int>(n + 1);
+  if (n > 0) {
+    k_row_block_norms<<<ceil_div(n, 256), 256, 0, s>>>(P, norms);
+    k_trunc_select<<<ceil_div(n, 256), 256, 0, s>>>(P, norms, trunc, pmax, tmin, cn, cc, cnt);
+    SCR_LAUNCH();
+  }
+  O.nnzb = exclusive_scan(cnt, O.rp, n, tmp, s);
+  O.col = a.alloc<int>(O.nnzb + 1);
+  O.val = a.alloc<double>(O.nnzb * O.br * O.bc + 1);
+  if (n > 0) {
+    k_trunc_fill<<<ceil_div(n, 256), 256, 0, s>>>(P, norms, tmin, cn, cc, O);
+    SCR_LAUNCH();
+  }
+  counters().launches += 3;
+  SCR_CUDA(cudaStreamSynchronize(s));
+}
+
 // ------------------------------------------------------------ transpose
 __global__ void k_tr_count(DBsr<double> A, int* __restrict__ cnt) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -756,39 +941,39 @@ __global__ void k_tr_count(DBsr<double> A, int* __restrict__ cnt) {
   atomicAdd(cnt + A.col[t], 1);
 }
 
-__global__ void k_tr_rows(DBsr<double> A, int* __restrict__ cursor, int* __restrict__ tcol, int* __restrict__ src) {
+__global__ void k_tr_rows(DBsr<double> A, int* __restrict__ cursor, int* __restrict__ ucol, int* __restrict__ usrc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= A.nbr) return;
   for (int t = A.rp[i]; t < A.rp[i + 1]; ++t) {
     const int p = atomicAdd(cursor + A.col[t], 1);
-    tcol[p] = i;
-    src[p] = t;
+    ucol[p] = i;
+    usrc[p] = t;
   }
 }
 
-__global__ void k_tr_sort_fill(DBsr<double> A, DBsr<double> T, int* __restrict__ src) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+// one warp per row of T: rank-sort the (unordered) source rows, then copy
+// the blocks transposed in that order
+__global__ void k_tr_sort_fill(DBsr<double> A, DBsr<double> T, const int* __restrict__ ucol,
+                               const int* __restrict__ usrc, int* __restrict__ ssrc) {
+  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (j >= T.nbr) return;
   const int s = T.rp[j], e = T.rp[j + 1], k = e - s;
-  // insertion sort of the row by source row index
-  for (int a = s + 1; a < e; ++a) {
-    const int c = T.col[a], sr = src[a];
-    int b = a - 1;
-    while (b >= s && T.col[b] > c) {
-      T.col[b + 1] = T.col[b];
-      src[b + 1] = src[b];
-      --b;
-    }
-    T.col[b + 1] = c;
-    src[b + 1] = sr;
+  for (int q = lane; q < k; q += 32) {
+    const int v = ucol[s + q];
+    int rank = 0;
+    for (int p = 0; p < k; ++p) rank += ucol[s + p] < v;
+    T.col[s + rank] = v;
+    ssrc[s + rank] = usrc[s + q];
   }
-  for (int p = 0; p < k; ++p) {
-    const int t = src[s + p];
+  __syncwarp();
+  const int bs = A.br * A.bc;
+  for (int q = lane; q < k * bs; q += 32) {
+    const int p = q / bs, rem = q - p * bs, r = rem / A.bc, c = rem - r * A.bc;
+    const int t = ssrc[s + p];
     const int i = T.col[s + p];
     const int as = A.rp[i], ak = A.rp[i + 1] - as;
-    for (int r = 0; r < A.br; ++r)
-      for (int c = 0; c < A.bc; ++c)
-        T.val[slab_index(s, k, p, c, r, T.br, T.bc)] = A.val[slab_index(as, ak, t - as, r, c, A.br, A.bc)];
+    T.val[slab_index(s, k, p, c, r, T.br, T.bc)] = A.val[slab_index(as, ak, t - as, r, c, A.br, A.bc)];
   }
 }
 
@@ -804,7 +989,9 @@ void transpose(const DBsr<double>& A, DBsr<double>& T, DeviceArena& arena, cudaS
   T.val = arena.alloc<double>(A.nnzb * A.br * A.bc + 1);
   int* cnt = tmp.alloc<int>(T.nbr + 1);
   int* cursor = tmp.alloc<int>(T.nbr + 1);
-  int* src = tmp.alloc<int>(A.nnzb + 1);
+  int* ucol = tmp.alloc<int>(A.nnzb + 1);
+  int* usrc = tmp.alloc<int>(A.nnzb + 1);
+  int* ssrc = tmp.alloc<int>(A.nnzb + 1);
   SCR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (T.nbr + 1), s));
   if (A.nnzb > 0) {
     k_tr_count<<<ceil_div(A.nnzb, 256), 256, 0, s>>>(A, cnt);
@@ -813,11 +1000,11 @@ void transpose(const DBsr<double>& A, DBsr<double>& T, DeviceArena& arena, cudaS
   exclusive_scan(cnt, T.rp, T.nbr, tmp, s);
   SCR_CUDA(cudaMemcpyAsync(cursor, T.rp, sizeof(int) * (T.nbr + 1), cudaMemcpyDeviceToDevice, s));
   if (A.nbr > 0) {
-    k_tr_rows<<<ceil_div(A.nbr, 256), 256, 0, s>>>(A, cursor, T.col, src);
+    k_tr_rows<<<ceil_div(A.nbr, 256), 256, 0, s>>>(A, cursor, ucol, usrc);
     SCR_LAUNCH();
   }
   if (T.nbr > 0) {
-    k_tr_sort_fill<<<ceil_div(T.nbr, 128), 128, 0, s>>>(A, T, src);
+    k_tr_sort_fill<<<ceil_div((long long)T.nbr * 32, 256), 256, 0, s>>>(A, T, ucol, usrc, ssrc);
     SCR_LAUNCH();
   }
   counters().launches += 3;

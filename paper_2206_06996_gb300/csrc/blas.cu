@@ -132,6 +132,30 @@ void diag_scale(const T* b, const T* d, T* x, long long n, int nrhs, cudaStream_
   counters().launches++;
 }
 template void diag_scale<double>(const double*, const double*, double*, long long, int, cudaStream_t);
+
+template <typename T>
+__global__ void k_cheb_zero(const T* __restrict__ b, const T* __restrict__ d, T* __restrict__ r, T* __restrict__ dv,
+                            T* __restrict__ x, T inv_theta, long long n, int nrhs) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+  for (; i < n * nrhs; i += st) {
+    const T ri = b[i] * d[i / nrhs];
+    const T di = ri * inv_theta;
+    r[i] = ri;
+    dv[i] = di;
+    x[i] = di;
+  }
+}
+template <typename T>
+void cheb_zero(const T* b, const T* d, T* r, T* dv, T* x, double inv_theta, long long n, int nrhs, cudaStream_t s) {
+  if (n <= 0) return;
+  k_cheb_zero<T><<<grid_for(n * nrhs), 256, 0, s>>>(b, d, r, dv, x, (T)inv_theta, n, nrhs);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+template void cheb_zero<double>(const double*, const double*, double*, double*, double*, double, long long, int,
+                                cudaStream_t);
+template void cheb_zero<float>(const float*, const float*, float*, float*, float*, double, long long, int,
+                               cudaStream_t);
 template void diag_scale<float>(const float*, const float*, float*, long long, int, cudaStream_t);
 template void scale_by<float>(const float*, const double*, float*, long long, cudaStream_t);
 

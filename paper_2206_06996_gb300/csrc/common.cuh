@@ -40,6 +40,7 @@ struct DBsr {
   int* rp = nullptr;
   int* col = nullptr;
   T* val = nullptr;
+  int g = 0;  // lanes per scalar row in products with this matrix (0: heuristic)
 };
 
 __host__ __device__ inline long long slab_index(int s, int k, int t, int r, int c, int BR, int BC) {

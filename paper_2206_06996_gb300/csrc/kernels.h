@@ -45,23 +45,33 @@ void slab_to_float(const double* in, float* out, long long n, cudaStream_t s);
 // Epilogues applied to the row sums acc of M x (scalar output index o,
 // right-hand side h, flat index gi = o*nrhs + h):
 enum class Epi : int {
-  Set = 0,     // y = acc
-  Axpby = 1,   // y = alpha*acc + beta*z
-  Resid = 2,   // y = z - acc
-  Jacobi = 3,  // y = xs + (z - acc) * dinv[o]
+  Set = 0,        // y = acc
+  Axpby = 1,      // y = alpha*acc + beta*z
+  Resid = 2,      // y = z - acc
+  Jacobi = 3,     // y = xs + (z - acc) * dinv[o]
+  ChebFirst = 4,  // r = (z - acc) dinv[o]; dout = alpha r; y = xs + dout   (x = xs)
+  ChebStep = 5,   // r -= acc dinv[o]; dout = alpha x + beta r; xsol += dout (x = d)
 };
 struct EpiArgs {
   Epi kind = Epi::Set;
   double alpha = 1.0, beta = 0.0;
   const void* z = nullptr;     // same precision as y
-  const void* xs = nullptr;    // Jacobi: current iterate
-  const void* dinv = nullptr;  // Jacobi: inverse l1 row sums
+  const void* xs = nullptr;    // Jacobi / ChebFirst: current iterate
+  const void* dinv = nullptr;  // inverse l1 row sums (Jacobi) or inverse diagonal (Chebyshev)
+  void* r = nullptr;           // Chebyshev: preconditioned residual (in/out)
+  void* dout = nullptr;        // Chebyshev: next direction
+  void* xsol = nullptr;        // ChebStep: iterate updated in place
 };
 
 // y = epilogue(M x); M in slab layout; x and y of type XT; nrhs interleaved
 // right-hand sides (1 or 3).
 template <typename VT, typename XT>
 void spmv(const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const EpiArgs& e, cudaStream_t s);
+
+// time the lane-group widths for products of M with nrhs right-hand sides
+// and store the fastest in M.g; returns the chosen width
+template <typename VT>
+int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s);
 
 // y = epilogue([[A, B], [C, D]] x) in FP64 (the outer operator calA)
 void block_op(const DBsr<double>& A, const DBsr<double>& B, const DBsr<double>& C,
@@ -96,6 +106,10 @@ void axpby_t(double a, const T* x, double b, T* y, long long n, cudaStream_t s);
 // x[o*nrhs+h] = b[o*nrhs+h] * d[o]  (l1-Jacobi sweep from a zero iterate)
 template <typename T>
 void diag_scale(const T* b, const T* d, T* x, long long n, int nrhs, cudaStream_t s);
+// Chebyshev start from a zero iterate: r = b d, dv = r / theta, x = dv
+template <typename T>
+void cheb_zero(const T* b, const T* d, T* r, T* dv, T* x, double inv_theta, long long n, int nrhs,
+               cudaStream_t s);
 
 // out = ||x||^2 (device scalar).  Vector kernels take T = double or float;
 // FP32 vectors are summed per thread in FP32, across threads in FP64.
@@ -154,10 +168,20 @@ void spadd(const DBsr<double>& A, double alpha, const DBsr<double>& B, const dou
            DBsr<double>& C, DeviceArena& arena, cudaStream_t s);
 // out = diag(d)^{-1} M, sharing M's pattern
 void scale_rows_inv(const DBsr<double>& M, const double* d, DBsr<double>& out, DeviceArena& a, cudaStream_t s);
+// interpolation truncation: keep the blocks of each row whose norm is at
+// least trunc * the row maximum, at most pmax of them (largest first, ties
+// by smaller column), rescale each scalar row to its original sum
+void truncate_rows(const DBsr<double>& P, double trunc, int pmax, DBsr<double>& out, DeviceArena& a,
+                   cudaStream_t s);
 // transpose (blocks transposed)
 void transpose(const DBsr<double>& A, DBsr<double>& T, DeviceArena& arena, cudaStream_t s);
 // scalar diagonal of A (n scalar rows); returns false if a diagonal entry is missing/zero
 void diag_scalar(const DBsr<double>& A, double* d, int* bad, cudaStream_t s);
+// 1 / a_ii per scalar row (0 where the diagonal is zero)
+void inv_diag(const DBsr<double>& A, double* dinv, cudaStream_t s);
+// 1.1 x the power-iteration estimate (iters steps) of rho(D^{-1} A), from
+// the fixed start vector 1 + ((i * 2654435761) mod 2^32 mod 1000) / 1000
+double power_lambda(const DBsr<double>& A, const double* dinv, int iters, cudaStream_t s);
 // 1/ sum_j |a_ij| per scalar row
 void l1_inv(const DBsr<double>& A, double* dinv, cudaStream_t s);
 // max_i sum_j |a_ij| / |a_ii| (device scalar)

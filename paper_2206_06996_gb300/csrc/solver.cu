@@ -70,8 +70,13 @@ struct HostScalars {
 struct Level {
   DBsr<double> A, P, R;
   DBsr<float> Af, Pf, Rf;
-  double* dinv = nullptr;
+  double* dinv = nullptr;   // l1-Jacobi: 1 / sum_j |a_ij|
   float* dinvf = nullptr;
+  double* dd = nullptr;     // Chebyshev: 1 / a_ii
+  float* ddf = nullptr;
+  double lam = 0.0;         // Chebyshev interval [lam/30, lam]
+  double *d0 = nullptr, *d1 = nullptr;
+  float *d0f = nullptr, *d1f = nullptr;
   int* agg = nullptr;
   int n_agg = 0;
   long long n = 0;  // scalar rows
@@ -100,12 +105,15 @@ static DBsr<float> to_float_copy(const DBsr<double>& M, DeviceArena& a, cudaStre
   F.rp = M.rp;
   F.col = M.col;
   F.val = a.alloc<float>(M.nnzb * M.br * M.bc + 1);
+  F.g = 0;
   slab_to_float(M.val, F.val, M.nnzb * M.br * M.bc, s);
   return F;
 }
 
 struct Hierarchy {
   int bs = 1, nrhs = 1, nu = 1;
+  int smoother = SCR_SMOOTH_CHEB, degree = 3;
+  double cheb_theta_inv = 0.0;
   bool f32 = false;
   std::vector<Level> lv;
   double* cinv = nullptr;
@@ -122,6 +130,8 @@ struct Hierarchy {
     bs = bs_;
     nrhs = nrhs_;
     nu = std::max(1, o.amg_nu);
+    smoother = o.amg_smoother;
+    degree = std::max(1, o.amg_degree);
     f32 = use_f32;
     lv.clear();
     arena.reset(new DeviceArena(s));
@@ -136,12 +146,16 @@ struct Hierarchy {
       const bool last = Al.nbr <= o.amg_coarse_size || (int)lv.size() + 1 >= o.amg_max_levels;
       if (!last) {
         DeviceArena tmp(s);
+        auto t0 = Clock::now();
         Aggregation ag = aggregate(Al, o.amg_theta, ar, tmp, s, &mis_rounds);
+        SCR_CUDA(cudaStreamSynchronize(s));
+        const double t_agg = ms_since(t0);
         if (ag.n_agg > 0 && ag.n_agg < (int)(0.9 * Al.nbr)) {
           L.agg = ag.agg;
           L.n_agg = ag.n_agg;
           DBsr<double> Pt, T, AP, Ac;
           DeviceArena tmp2(s);
+          t0 = Clock::now();
           tentative(ag.agg, Al.nbr, ag.n_agg, bs, Pt, tmp2, tmp, s);
           double* d = tmp.alloc<double>(L.n + 1);
           int* bad = tmp.alloc<int>(1);
@@ -152,11 +166,33 @@ struct Hierarchy {
           double* rs = tmp.alloc<double>(L.n + 1);
           prolong_rowscale(d, lam, rs, (int)L.n, s);
           spgemm(Al, Pt, T, tmp2, s);
-          spadd(Pt, 1.0, T, rs, L.P, ar, s);
+          if (o.amg_trunc > 0.0 || o.amg_pmax > 0) {
+            DBsr<double> Ps;
+            spadd(Pt, 1.0, T, rs, Ps, tmp2, s);
+            truncate_rows(Ps, o.amg_trunc, o.amg_pmax, L.P, ar, s);
+          } else {
+            spadd(Pt, 1.0, T, rs, L.P, ar, s);
+          }
+          SCR_CUDA(cudaStreamSynchronize(s));
+          const double t_p = ms_since(t0);
+          t0 = Clock::now();
           transpose(L.P, L.R, ar, s);
+          SCR_CUDA(cudaStreamSynchronize(s));
+          const double t_tr = ms_since(t0);
+          t0 = Clock::now();
           spgemm(Al, L.P, AP, tmp2, s);
+          SCR_CUDA(cudaStreamSynchronize(s));
+          const double t_ap = ms_since(t0);
+          t0 = Clock::now();
           spgemm(L.R, AP, Ac, ar, s);
           SCR_CUDA(cudaStreamSynchronize(s));
+          const double t_rap = ms_since(t0);
+          if (o.verbose)
+            fprintf(stderr,
+                    "[amg bs=%d] level %zu: %d block rows, %lld blocks -> %d aggregates (%d MIS rounds); P %lld blocks,"
+                    " AP %lld, Ac %lld | ms: agg %.2f P %.2f R %.2f AP %.2f RAP %.2f\n",
+                    bs, lv.size(), Al.nbr, Al.nnzb, ag.n_agg, mis_rounds, L.P.nnzb, AP.nnzb, Ac.nnzb, t_agg, t_p,
+                    t_tr, t_ap, t_rap);
           lv.push_back(L);
           Al = Ac;
           continue;
@@ -168,6 +204,7 @@ struct Hierarchy {
     // coarsest level: dense inverse
     Level& C = lv.back();
     nc = (int)C.n;
+    auto tc0 = Clock::now();
     if (nc > 4096) throw CudaError{cudaErrorInvalidValue, "coarsest AMG level too large for a dense inverse"};
     {
       DeviceArena tmp(s);
@@ -182,10 +219,27 @@ struct Hierarchy {
       SCR_CUDA(cudaStreamSynchronize(s));
       if (hs) throw CudaError{cudaErrorInvalidValue, "singular coarsest AMG operator"};
     }
+    if (o.verbose)
+      fprintf(stderr, "[amg bs=%d] coarsest level %zu: %d scalar rows, dense inverse %.2f ms\n", bs, lv.size() - 1,
+              nc, ms_since(tc0));
     // work vectors and FP32 copies
     for (size_t l = 0; l < lv.size(); ++l) {
       Level& L = lv[l];
       const long long m = L.n * nrhs + 1;
+      if (smoother == SCR_SMOOTH_CHEB && l + 1 < lv.size()) {
+        L.dd = ar.alloc<double>(L.n + 1);
+        inv_diag(L.A, L.dd, s);
+        L.lam = power_lambda(L.A, L.dd, 20, s);
+        if (f32) {
+          L.ddf = ar.alloc<float>(L.n + 1);
+          cast_d2f(L.dd, L.ddf, L.n, s);
+          L.d0f = ar.alloc<float>(m);
+          L.d1f = ar.alloc<float>(m);
+        } else {
+          L.d0 = ar.alloc<double>(m);
+          L.d1 = ar.alloc<double>(m);
+        }
+      }
       if (!f32) {
         L.b = ar.alloc<double>(m);
         L.x = ar.alloc<double>(m);
@@ -208,6 +262,26 @@ struct Hierarchy {
     if (f32) {
       cinvf = ar.alloc<float>((size_t)nc * nc + 1);
       cast_d2f(cinv, cinvf, (long long)nc * nc, s);
+    }
+    // lane-group widths of the products on the two finest levels
+    if (o.autotune) {
+      for (size_t l = 0; l < lv.size() && l < 2; ++l) {
+        Level& L = lv[l];
+        if (L.n < 4096) continue;
+        if (f32) {
+          if (!(l == 0 && A0f)) autotune_spmv<float>(L.Af, nrhs, s);
+          if (L.P.nbr) {
+            autotune_spmv<float>(L.Pf, nrhs, s);
+            autotune_spmv<float>(L.Rf, nrhs, s);
+          }
+        } else {
+          if (l > 0 || A0.g == 0) autotune_spmv<double>(L.A, nrhs, s);
+          if (L.P.nbr) {
+            autotune_spmv<double>(L.P, nrhs, s);
+            autotune_spmv<double>(L.R, nrhs, s);
+          }
+        }
+      }
     }
     SCR_CUDA(cudaStreamSynchronize(s));
   }
@@ -233,6 +307,93 @@ struct Hierarchy {
     if constexpr (sizeof(T) == 8) return L.dinv; else return L.dinvf;
   }
 
+  // Chebyshev coefficients on [lam/30, lam]: 1/theta and (alpha_j, beta_j)
+  static void cheb_coeffs(double lam, int degree, double* inv_theta, std::vector<std::pair<double, double>>& st) {
+    const double lo = lam / 30.0, hi = lam;
+    const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+    const double sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    st.clear();
+    for (int j = 1; j < degree; ++j) {
+      const double rn = 1.0 / (2.0 * sigma - rho);
+      st.emplace_back(rn * rho, 2.0 * rn / delta);
+      rho = rn;
+    }
+    *inv_theta = 1.0 / theta;
+  }
+
+  template <typename T>
+  void cycle_cheb(int l, const T* b, T* out, cudaStream_t s) {
+    Level& L = lv[l];
+    const DBsr<T>& A = pick<T>(L.A, L.Af);
+    const DBsr<T>& P = pick<T>(L.P, L.Pf);
+    const DBsr<T>& R = pick<T>(L.R, L.Rf);
+    const T* dd;
+    T *d0, *d1;
+    if constexpr (sizeof(T) == 8) {
+      dd = L.dd;
+      d0 = L.d0;
+      d1 = L.d1;
+    } else {
+      dd = L.ddf;
+      d0 = L.d0f;
+      d1 = L.d1f;
+    }
+    double inv_theta;
+    std::vector<std::pair<double, double>> st;
+    cheb_coeffs(L.lam, degree, &inv_theta, st);
+    T* r = vr<T>(L);
+    T* cur = vt<T>(L);
+    // pre-smoothing from zero
+    cheb_zero<T>(b, dd, r, d0, cur, inv_theta, L.n, nrhs, s);
+    EpiArgs e;
+    e.kind = Epi::ChebStep;
+    e.dinv = dd;
+    e.r = r;
+    for (auto& ab : st) {
+      e.alpha = ab.first;
+      e.beta = ab.second;
+      e.dout = d1;
+      e.xsol = cur;
+      spmv<T, T>(A, d0, d1, nrhs, e, s);
+      std::swap(d0, d1);
+    }
+    // coarse-grid correction
+    EpiArgs res;
+    res.kind = Epi::Resid;
+    res.z = b;
+    spmv<T, T>(A, cur, r, nrhs, res, s);
+    Level& Lc = lv[l + 1];
+    T* bc = vb<T>(Lc);
+    spmv<T, T>(R, r, bc, nrhs, EpiArgs(), s);
+    T* xc = vx<T>(Lc);
+    cycle<T>(l + 1, bc, xc, s);
+    EpiArgs pro;
+    pro.kind = Epi::Axpby;
+    pro.alpha = 1.0;
+    pro.beta = 1.0;
+    pro.z = cur;
+    spmv<T, T>(P, xc, cur, nrhs, pro, s);
+    // post-smoothing from cur, result in out
+    EpiArgs f;
+    f.kind = Epi::ChebFirst;
+    f.alpha = inv_theta;
+    f.z = b;
+    f.xs = cur;
+    f.dinv = dd;
+    f.r = r;
+    f.dout = d0;
+    spmv<T, T>(A, cur, out, nrhs, f, s);
+    for (auto& ab : st) {
+      e.alpha = ab.first;
+      e.beta = ab.second;
+      e.dout = d1;
+      e.xsol = out;
+      spmv<T, T>(A, d0, d1, nrhs, e, s);
+      std::swap(d0, d1);
+    }
+  }
+
   // out = V-cycle(b) at level l, starting from a zero iterate
   template <typename T>
   void cycle(int l, const T* b, T* out, cudaStream_t s) {
@@ -240,6 +401,10 @@ struct Hierarchy {
     if (l == n_levels() - 1) {
       if constexpr (sizeof(T) == 8) dense_apply(cinv, b, out, nc, nrhs, s);
       else dense_apply_f(cinvf, b, out, nc, nrhs, s);
+      return;
+    }
+    if (smoother == SCR_SMOOTH_CHEB) {
+      cycle_cheb<T>(l, b, out, s);
       return;
     }
     const DBsr<T>& A = pick<T>(L.A, L.Af);
@@ -640,6 +805,11 @@ int scr_default_opts(scr_opts* o) {
   o->amg_max_levels = 10;
   o->amg_coarse_size = 64;
   o->amg_nu = 1;
+  o->amg_trunc = 0.3;
+  o->amg_pmax = 5;
+  o->autotune = 1;
+  o->amg_smoother = SCR_SMOOTH_CHEB;
+  o->amg_degree = 3;
   o->mm_rtol = 1e-8;
   o->mm_max_it = 500;
   o->verbose = 0;
@@ -660,6 +830,9 @@ int scr_create(scr_handle* out, const scr_opts* o, void* stream) {
       throw std::invalid_argument("restart lengths must lie in [1, 63]");
     if (op.precision != SCR_FP64 && op.precision != SCR_MIXED) throw std::invalid_argument("unknown precision");
     if (op.precond != 0) throw std::invalid_argument("only the SCR preconditioner (precond = 0) is built");
+    if (op.amg_smoother != SCR_SMOOTH_L1 && op.amg_smoother != SCR_SMOOTH_CHEB)
+      throw std::invalid_argument("unknown smoother");
+    if (op.amg_degree < 1 || op.amg_degree > 16) throw std::invalid_argument("Chebyshev degree must lie in [1, 16]");
     std::unique_ptr<scr_ctx> h(new scr_ctx());
     h->o = op;
     h->s = static_cast<cudaStream_t>(stream);
@@ -707,6 +880,8 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
     h->B = upload(B, dev, a, s);
     h->C = upload(C, dev, a, s);
     h->D = upload(D, dev, a, s);
+    if (h->o.verbose) fprintf(stderr, "[setup] upload %.2f ms\n", ms_since(t0));
+    auto t1 = Clock::now();
     // Shat = D - C diag(A)^{-1} B  (Sec. 5.2.1)
     {
       DeviceArena tmp(s);
@@ -724,12 +899,18 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
       spadd(h->D, 1.0, T, nullptr, h->Shat, a, s);
       SCR_CUDA(cudaStreamSynchronize(s));
     }
+    if (h->o.verbose) fprintf(stderr, "[setup] Shat %.2f ms (%lld entries)\n", ms_since(t1), h->Shat.nnzb);
     const bool f32 = h->o.precision == SCR_MIXED;
+    if (h->o.autotune) {
+      autotune_spmv<double>(h->A, 1, s);
+      autotune_spmv<double>(h->Shat, 1, s);
+    }
     if (f32) {
       h->Af = float_copy(h->A, a, s);
       h->Bf = float_copy(h->B, a, s);
       h->Cf = float_copy(h->C, a, s);
       h->Df = float_copy(h->D, a, s);
+      if (h->o.autotune) autotune_spmv<float>(h->Af, 1, s);
     }
     h->hA.build(h->A, 3, 1, h->o, f32, s, f32 ? &h->Af : nullptr);
     h->hS.build(h->Shat, 1, 1, h->o, f32, s);
@@ -877,6 +1058,7 @@ int mm_setup(scr_handle h, const scr_bsr* L, int dev) {
       if (hb) throw std::invalid_argument("L has a missing or zero diagonal entry");
     }
     scr_opts o = h->o;
+    if (o.autotune) autotune_spmv<double>(h->L, 3, s);
     h->hM.build(h->L, 1, 3, o, false, s);
     h->mwork.reset(new DeviceArena(s));
     DeviceArena& w = *h->mwork;

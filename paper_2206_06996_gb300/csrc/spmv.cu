@@ -128,6 +128,10 @@ struct Epilogue {
   const XT* z;
   const XT* xs;
   const XT* dinv;
+  const XT* xin;  // the product's source vector (ChebStep: the direction)
+  XT* r;
+  XT* dout;
+  XT* xsol;
   XT alpha, beta;
   template <typename AT>
   __device__ __forceinline__ void operator()(long long gi, long long o, AT acc) const {
@@ -139,36 +143,44 @@ struct Epilogue {
       y[gi] = v;
     } else if constexpr (E == Epi::Resid) {
       y[gi] = z[gi] - (XT)acc;
-    } else {
+    } else if constexpr (E == Epi::Jacobi) {
       y[gi] = xs[gi] + (z[gi] - (XT)acc) * dinv[o];
+    } else if constexpr (E == Epi::ChebFirst) {
+      const XT ri = (z[gi] - (XT)acc) * dinv[o];
+      const XT di = alpha * ri;
+      r[gi] = ri;
+      dout[gi] = di;
+      y[gi] = xs[gi] + di;
+    } else {
+      const XT ri = r[gi] - (XT)acc * dinv[o];
+      const XT di = alpha * xin[gi] + beta * ri;
+      r[gi] = ri;
+      dout[gi] = di;
+      xsol[gi] += di;
     }
   }
 };
 
-// accumulate one scalar row r of block row i of M into acc[h], lanes of a
-// G-group split the row's k*BC stored values
+// accumulate one scalar row r of block row i of M into acc[h]; the lanes of
+// a G-group take the row's blocks in turn (BC values each, contiguous in the
+// slab layout) so every stored value costs one multiply-add
 template <int BC, int NRHS, int G, typename VT, typename XT, typename AT>
 __device__ __forceinline__ void scalar_row_accum(const int* __restrict__ rp, const int* __restrict__ col,
                                                  const VT* __restrict__ val, const XT* __restrict__ x, int BR,
                                                  int i, int r, int lane, AT (&acc)[NRHS]) {
   const int s = __ldg(rp + i), k = __ldg(rp + i + 1) - s;
-  const int L = k * BC;
-  const VT* vr = val + (long long)s * BR * BC + (long long)r * L;
+  const VT* vr = val + (long long)s * BR * BC + (long long)r * k * BC;
   const int* cr = col + s;
-#pragma unroll 4
-  for (int q = lane; q < L; q += G) {
-    int t, c;
-    if constexpr (BC == 1) {
-      t = q;
-      c = 0;
-    } else {
-      t = q / BC;
-      c = q - t * BC;
-    }
-    const long long xb = ((long long)__ldg(cr + t) * BC + c) * NRHS;
-    const AT a = (AT)__ldg(vr + q);
+#pragma unroll 2
+  for (int t = lane; t < k; t += G) {
+    const long long xb = (long long)__ldg(cr + t) * BC * NRHS;
+    const VT* vt = vr + t * BC;
 #pragma unroll
-    for (int h = 0; h < NRHS; ++h) acc[h] = fma(a, (AT)__ldg(x + xb + h), acc[h]);
+    for (int c = 0; c < BC; ++c) {
+      const AT a = (AT)__ldg(vt + c);
+#pragma unroll
+      for (int h = 0; h < NRHS; ++h) acc[h] = fma(a, (AT)__ldg(x + xb + c * NRHS + h), acc[h]);
+    }
   }
 }
 
@@ -187,10 +199,12 @@ __global__ void __launch_bounds__(256) k_spmv(int nbr, const int* __restrict__ r
     const int i = (int)(o / BR), r = (int)(o - (long long)i * BR);
     scalar_row_accum<BC, NRHS, G>(rp, col, val, x, BR, i, r, lane, acc);
   }
+  if constexpr (G > 1) {
 #pragma unroll
-  for (int h = 0; h < NRHS; ++h) {
+    for (int h = 0; h < NRHS; ++h) {
 #pragma unroll
-    for (int off = G / 2; off > 0; off >>= 1) acc[h] += __shfl_xor_sync(0xffffffffu, acc[h], off, G);
+      for (int off = G / 2; off > 0; off >>= 1) acc[h] += __shfl_xor_sync(0xffffffffu, acc[h], off, G);
+    }
   }
   if (active && lane == 0) {
 #pragma unroll
@@ -205,6 +219,10 @@ static void launch_spmv_g(const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& 
   epi.z = static_cast<const XT*>(e.z);
   epi.xs = static_cast<const XT*>(e.xs);
   epi.dinv = static_cast<const XT*>(e.dinv);
+  epi.xin = x;
+  epi.r = static_cast<XT*>(e.r);
+  epi.dout = static_cast<XT*>(e.dout);
+  epi.xsol = static_cast<XT*>(e.xsol);
   epi.alpha = (XT)e.alpha;
   epi.beta = (XT)e.beta;
   const long long threads = (long long)M.nbr * BR * G;
@@ -221,6 +239,15 @@ static void launch_spmv_e(const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& 
     case Epi::Axpby: launch_spmv_g<BR, BC, NRHS, G, VT, XT, AT, Epi::Axpby>(M, x, y, e, s); break;
     case Epi::Resid: launch_spmv_g<BR, BC, NRHS, G, VT, XT, AT, Epi::Resid>(M, x, y, e, s); break;
     case Epi::Jacobi: launch_spmv_g<BR, BC, NRHS, G, VT, XT, AT, Epi::Jacobi>(M, x, y, e, s); break;
+    case Epi::ChebFirst:
+    case Epi::ChebStep:
+      if constexpr (BR == BC) {
+        if (e.kind == Epi::ChebFirst) launch_spmv_g<BR, BC, NRHS, G, VT, XT, AT, Epi::ChebFirst>(M, x, y, e, s);
+        else launch_spmv_g<BR, BC, NRHS, G, VT, XT, AT, Epi::ChebStep>(M, x, y, e, s);
+      } else {
+        throw CudaError{cudaErrorInvalidValue, "Chebyshev epilogue on a non-square block shape"};
+      }
+      break;
   }
 }
 
@@ -228,32 +255,40 @@ static void launch_spmv_e(const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& 
 // reduction compete with the products), FP32 widens them for coalescing
 template <typename VT>
 static int pick_group(const DBsr<VT>& M) {
-  const double per_row = M.nbr ? (double)M.nnzb * M.bc / M.nbr : 0.0;
-  if (sizeof(VT) == 8) return per_row >= 24 ? 4 : 2;
-  return per_row >= 48 ? 8 : 4;
+  if (M.g > 0) return M.g;
+  const double blocks_per_row = M.nbr ? (double)M.nnzb / M.nbr : 0.0;
+  if (sizeof(VT) == 8) return blocks_per_row >= 12 ? 4 : 2;
+  return blocks_per_row >= 24 ? 8 : 4;
+}
+
+template <int BR, int BC, int NR, typename VT, typename XT>
+static void dispatch_g(int G, const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& e, cudaStream_t s) {
+  switch (G) {
+    case 1: launch_spmv_e<BR, BC, NR, 1, VT, XT>(M, x, y, e, s); break;
+    case 2: launch_spmv_e<BR, BC, NR, 2, VT, XT>(M, x, y, e, s); break;
+    case 4: launch_spmv_e<BR, BC, NR, 4, VT, XT>(M, x, y, e, s); break;
+    case 8: launch_spmv_e<BR, BC, NR, 8, VT, XT>(M, x, y, e, s); break;
+    default: launch_spmv_e<BR, BC, NR, 16, VT, XT>(M, x, y, e, s); break;
+  }
+}
+
+template <typename VT, typename XT>
+static void spmv_launch(int G, const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const EpiArgs& e, cudaStream_t s) {
+  const int br = M.br, bc = M.bc;
+  if (br == 3 && bc == 3 && nrhs == 1) dispatch_g<3, 3, 1, VT, XT>(G, M, x, y, e, s);
+  else if (br == 3 && bc == 1 && nrhs == 1) dispatch_g<3, 1, 1, VT, XT>(G, M, x, y, e, s);
+  else if (br == 1 && bc == 3 && nrhs == 1) dispatch_g<1, 3, 1, VT, XT>(G, M, x, y, e, s);
+  else if (br == 1 && bc == 1 && nrhs == 1) dispatch_g<1, 1, 1, VT, XT>(G, M, x, y, e, s);
+  else if (br == 1 && bc == 1 && nrhs == 3) dispatch_g<1, 1, 3, VT, XT>(G, M, x, y, e, s);
+  else throw CudaError{cudaErrorInvalidValue, "spmv: unsupported block shape"};
 }
 
 template <typename VT, typename XT>
 void spmv(const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const EpiArgs& e, cudaStream_t s) {
   if (M.nbr == 0) return;
   const int G = pick_group(M);
-  const int br = M.br, bc = M.bc;
   const int pidx = prof_start(0, M.val, s);
-#define SCR_SPMV_CASE(BR_, BC_, NR_)                                            \
-  if (br == BR_ && bc == BC_ && nrhs == NR_) {                                  \
-    if (G == 2) launch_spmv_e<BR_, BC_, NR_, 2, VT, XT>(M, x, y, e, s);         \
-    else if (G == 4) launch_spmv_e<BR_, BC_, NR_, 4, VT, XT>(M, x, y, e, s);    \
-    else launch_spmv_e<BR_, BC_, NR_, 8, VT, XT>(M, x, y, e, s);                \
-    goto done;                                                                  \
-  }
-  SCR_SPMV_CASE(3, 3, 1)
-  SCR_SPMV_CASE(3, 1, 1)
-  SCR_SPMV_CASE(1, 3, 1)
-  SCR_SPMV_CASE(1, 1, 1)
-  SCR_SPMV_CASE(1, 1, 3)
-#undef SCR_SPMV_CASE
-  throw CudaError{cudaErrorInvalidValue, "spmv: unsupported block shape"};
-done:
+  spmv_launch<VT, XT>(G, M, x, y, nrhs, e, s);
   counters().launches++;
   {
     // algorithmic bytes: stored values + column indices + row pointers once,
@@ -264,10 +299,51 @@ done:
                (double)M.nbc * M.bc * nrhs * sizeof(XT) + nrow * nrhs * sizeof(XT);
     if (e.kind == Epi::Resid || (e.kind == Epi::Axpby && e.z)) b += nrow * nrhs * sizeof(XT);
     if (e.kind == Epi::Jacobi) b += 2.0 * nrow * nrhs * sizeof(XT) + nrow * sizeof(XT);
+    if (e.kind == Epi::ChebFirst) b += 4.0 * nrow * nrhs * sizeof(XT) + nrow * sizeof(XT);
+    if (e.kind == Epi::ChebStep) b += 5.0 * nrow * nrhs * sizeof(XT) + nrow * sizeof(XT);
     counters().spmv_bytes += (long long)b;
     prof_stop(pidx, b, 2.0 * (double)M.nnzb * M.br * M.bc * nrhs, s);
   }
 }
+
+template <typename VT>
+int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s) {
+  if (M.nbr == 0) return M.g;
+  using XT = VT;
+  const long long nx = (long long)M.nbc * M.bc * nrhs + 1, ny = (long long)M.nbr * M.br * nrhs + 1;
+  XT *x = nullptr, *y = nullptr;
+  SCR_CUDA(cudaMallocAsync(&x, nx * sizeof(XT), s));
+  SCR_CUDA(cudaMallocAsync(&y, ny * sizeof(XT), s));
+  SCR_CUDA(cudaMemsetAsync(x, 0, nx * sizeof(XT), s));
+  cudaEvent_t e0, e1;
+  SCR_CUDA(cudaEventCreate(&e0));
+  SCR_CUDA(cudaEventCreate(&e1));
+  const int cands[] = {1, 2, 4, 8, 16};
+  float best = 1e30f;
+  int bestg = pick_group(M);
+  for (int G : cands) {
+    spmv_launch<VT, XT>(G, M, x, y, nrhs, EpiArgs(), s);  // warm-up
+    SCR_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 3; ++r) spmv_launch<VT, XT>(G, M, x, y, nrhs, EpiArgs(), s);
+    SCR_CUDA(cudaEventRecord(e1, s));
+    SCR_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    SCR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      bestg = G;
+    }
+  }
+  counters().launches += 20;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  SCR_CUDA(cudaFreeAsync(x, s));
+  SCR_CUDA(cudaFreeAsync(y, s));
+  M.g = bestg;
+  return bestg;
+}
+template int autotune_spmv<double>(DBsr<double>&, int, cudaStream_t);
+template int autotune_spmv<float>(DBsr<float>&, int, cudaStream_t);
 
 template void spmv<double, double>(const DBsr<double>&, const double*, double*, int, const EpiArgs&, cudaStream_t);
 template void spmv<float, float>(const DBsr<float>&, const float*, float*, int, const EpiArgs&, cudaStream_t);

@@ -239,6 +239,84 @@ def test_galerkin_operator(mini_system):
     assert np.allclose(l0.P.toarray(), P.toarray(), rtol=1e-12, atol=1e-15)
 
 
+@pytest.mark.parametrize("bs", [1, 3])
+def test_prolongator_truncation_definition(bs):
+    """Vectorised truncation = the per-row definition (keep blocks with
+    norm >= 0.3 of the row maximum, at most 4, largest first with ties to
+    the smaller column; rescale each scalar row to its old sum)."""
+    rng = np.random.default_rng(bs)
+    nbr, nbc = 150, 50
+    P = sp.random(nbr * bs, nbc * bs, density=0.15, random_state=bs, format="csr")
+    P.data = np.abs(rng.standard_normal(P.data.size)) + 0.1
+    T = amg.truncate_prolongator(P, bs, 0.3, 4).toarray()
+    Pd = P.toarray()
+    R = np.zeros_like(Pd)
+    for i in range(nbr):
+        rows = slice(i * bs, (i + 1) * bs)
+        blocks = [(j, Pd[rows, j * bs:(j + 1) * bs]) for j in range(nbc)]
+        blocks = [(j, b) for j, b in blocks if np.any(b != 0)]
+        if not blocks:
+            continue
+        m = max(np.linalg.norm(b) for _, b in blocks)
+        cand = sorted(((np.linalg.norm(b), j, b) for j, b in blocks if np.linalg.norm(b) >= 0.3 * m),
+                      key=lambda t: (-t[0], t[1]))[:4]
+        skept = sum(b.sum(axis=1) for _, _, b in cand)
+        # a scalar row whose kept part sums to zero keeps its values
+        sc = np.ones(bs)
+        nzk = skept != 0
+        sc[nzk] = Pd[rows].sum(axis=1)[nzk] / skept[nzk]
+        for _, j, b in cand:
+            R[rows, j * bs:(j + 1) * bs] = b * sc[:, None]
+    assert np.allclose(T, R, rtol=1e-13, atol=1e-15)
+    # row sums are preserved wherever a kept entry carries them
+    keep_rows = np.abs(T).sum(axis=1) > 0
+    assert np.allclose(T.sum(axis=1)[keep_rows], Pd.sum(axis=1)[keep_rows])
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3, 5])
+def test_chebyshev_smoother_is_the_chebyshev_polynomial(degree):
+    """With b = 0 the smoother maps an eigenvector of D^{-1}A with eigenvalue
+    mu to p(mu) times itself, p(mu) = T_k((theta - mu)/delta) / T_k(theta/delta)
+    on [lam/30, lam] (closed form of Chebyshev acceleration)."""
+    n = 40
+    L = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]).tocsr()
+    dinv = 1.0 / L.diagonal()
+    lam = 2.2
+    j = np.arange(1, n + 1)
+    for k in (1, 7, 23, 40):
+        v = np.sin(np.pi * k * j / (n + 1))
+        mu = 1.0 - np.cos(np.pi * k / (n + 1))
+        x = amg.cheb_smooth(L, dinv, lam, degree, v.copy(), np.zeros(n), False)
+        lo, hi = lam / 30, lam
+        theta, delta = (hi + lo) / 2, (hi - lo) / 2
+        Tk = lambda t: np.polynomial.chebyshev.chebval(t, [0] * degree + [1])
+        p = Tk((theta - mu) / delta) / Tk(theta / delta)
+        assert np.allclose(x, p * v, rtol=1e-10, atol=1e-12)
+
+
+def test_power_lambda_converges_to_spectral_radius():
+    n = 20
+    L = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]).tocsr()
+    rho = 1.0 - np.cos(np.pi * n / (n + 1))   # largest eigenvalue of D^{-1} L
+    est = amg.power_lambda(L, 1.0 / L.diagonal(), iters=400) / 1.1
+    assert abs(est - rho) < 1e-3
+    assert amg.power_lambda(L, 1.0 / L.diagonal()) / 1.1 <= rho + 1e-12
+
+
+def test_vcycle_chebyshev_contracts_on_spd(mini_system):
+    L = to_csr(mini_system.L)
+    H = amg.setup(L, 1, 0.08, 10, 16, 1, 1, 0.3, 5, "cheb", 3)
+    n = L.shape[0]
+    Ld = L.toarray()
+    M = np.column_stack([amg.vcycle(H, np.eye(n)[:, j]) for j in range(n)])
+    E = np.eye(n) - M @ Ld
+    w, V = np.linalg.eigh(Ld)
+    Lh = V @ np.diag(np.sqrt(w)) @ V.T
+    Lhi = V @ np.diag(1 / np.sqrt(w)) @ V.T
+    assert np.linalg.norm(Lh @ E @ Lhi, 2) < 0.5
+    assert np.allclose(M, M.T, atol=1e-10 * np.abs(M).max())
+
+
 def test_two_level_exact_on_constant_near_nullspace():
     # 1-D Laplacian: the V-cycle reduces a smooth error far better than one
     # Jacobi sweep (checks the coarse-grid correction is wired in)
