@@ -94,6 +94,11 @@ typedef struct {
   int autotune;       /* 1: time the SpMV lane-group widths at set-up and keep the fastest */
   int amg_smoother;   /* 0: l1-Jacobi (amg_nu sweeps); 1: Chebyshev on D^{-1}A (default) */
   int amg_degree;     /* Chebyshev degree, 3 */
+  int spmv_group;     /* 0: autotune/heuristic; 1..16: lanes per block row; 101..116: 100 + lanes per
+                         scalar row (forces the product kernel of every matrix) */
+  int sell;           /* 0: slab products; W > 0: products with A, Shat and L use a sliced block-ELL
+                         copy with rows sorted by length inside windows of W block rows
+                         (W a multiple of 32, at most 1024); default 0 */
   double mm_rtol;     /* mesh CG relative residual, 1e-8 */
   int mm_max_it;      /* mesh CG iteration cap, 500 */
   int verbose;        /* 0 quiet */

@@ -40,7 +40,22 @@ struct DBsr {
   int* rp = nullptr;
   int* col = nullptr;
   T* val = nullptr;
-  int g = 0;  // lanes per scalar row in products with this matrix (0: heuristic)
+  int g = 0;                  // lanes per scalar row in products with this matrix (0: heuristic)
+  const void* sell = nullptr; // host pointer to a DSell<T> copy used for products (optional)
+};
+
+// Sliced block-ELL copy of a block matrix (see sell.cu): chunks of 32 block
+// rows, rows ordered by length inside windows of 512.
+constexpr int kChunk = 32;
+constexpr int kWindow = 512;
+template <typename T>
+struct DSell {
+  int nbr = 0, nbc = 0, br = 1, bc = 1, nchunk = 0;
+  long long slots = 0;   // padded block slots per lane, summed over chunks
+  int* perm = nullptr;   // lane slot -> block row
+  int* cptr = nullptr;   // chunk -> first slot (units of 32 block slots)
+  int* col = nullptr;
+  T* val = nullptr;
 };
 
 __host__ __device__ inline long long slab_index(int s, int k, int t, int r, int c, int BR, int BC) {

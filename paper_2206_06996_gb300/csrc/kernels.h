@@ -68,6 +68,12 @@ struct EpiArgs {
 template <typename VT, typename XT>
 void spmv(const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const EpiArgs& e, cudaStream_t s);
 
+// build the sliced block-ELL copy of M (values converted to VT)
+template <typename VT>
+void build_sell(const DBsr<double>& M, DSell<VT>& S, DeviceArena& a, cudaStream_t s, int window);
+
+// forced kernel code for every product (0: per-matrix choice)
+void set_forced_group(int code);
 // time the lane-group widths for products of M with nrhs right-hand sides
 // and store the fastest in M.g; returns the chosen width
 template <typename VT>

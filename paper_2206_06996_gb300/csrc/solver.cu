@@ -561,6 +561,8 @@ struct scr_ctx {
   std::unique_ptr<DeviceArena> mmats;
   DBsr<double> A, B, C, D, Shat, L;
   DBsr<float> Af, Bf, Cf, Df;
+  DSell<double> A_sell, Shat_sell, L_sell;
+  DSell<float> Af_sell, Shatf_sell;
   Hierarchy hA, hS, hM;
   Reducer red, mred;
   int nv = 0, np = 0, nm = 0;
@@ -810,6 +812,7 @@ int scr_default_opts(scr_opts* o) {
   o->autotune = 1;
   o->amg_smoother = SCR_SMOOTH_CHEB;
   o->amg_degree = 3;
+  o->sell = 0;
   o->mm_rtol = 1e-8;
   o->mm_max_it = 500;
   o->verbose = 0;
@@ -835,6 +838,7 @@ int scr_create(scr_handle* out, const scr_opts* o, void* stream) {
     if (op.amg_degree < 1 || op.amg_degree > 16) throw std::invalid_argument("Chebyshev degree must lie in [1, 16]");
     std::unique_ptr<scr_ctx> h(new scr_ctx());
     h->o = op;
+    set_forced_group(op.spmv_group);
     h->s = static_cast<cudaStream_t>(stream);
     SCR_CUDA(cudaGetDevice(&h->device));
     configure_pool(h->device);
@@ -901,6 +905,12 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
     }
     if (h->o.verbose) fprintf(stderr, "[setup] Shat %.2f ms (%lld entries)\n", ms_since(t1), h->Shat.nnzb);
     const bool f32 = h->o.precision == SCR_MIXED;
+    if (h->o.sell) {
+      build_sell<double>(h->A, h->A_sell, a, s, h->o.sell);
+      h->A.sell = &h->A_sell;
+      build_sell<double>(h->Shat, h->Shat_sell, a, s, h->o.sell);
+      h->Shat.sell = &h->Shat_sell;
+    }
     if (h->o.autotune) {
       autotune_spmv<double>(h->A, 1, s);
       autotune_spmv<double>(h->Shat, 1, s);
@@ -910,10 +920,20 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
       h->Bf = float_copy(h->B, a, s);
       h->Cf = float_copy(h->C, a, s);
       h->Df = float_copy(h->D, a, s);
+      if (h->o.sell) {
+        build_sell<float>(h->A, h->Af_sell, a, s, h->o.sell);
+        h->Af.sell = &h->Af_sell;
+      }
       if (h->o.autotune) autotune_spmv<float>(h->Af, 1, s);
     }
+    if (h->o.verbose)
+      fprintf(stderr, "[setup] lane groups: A %d, Shat %d, A(fp32) %d\n", h->A.g, h->Shat.g, h->Af.g);
     h->hA.build(h->A, 3, 1, h->o, f32, s, f32 ? &h->Af : nullptr);
     h->hS.build(h->Shat, 1, 1, h->o, f32, s);
+    if (f32 && h->o.sell && h->hS.n_levels() > 0) {
+      build_sell<float>(h->Shat, h->Shatf_sell, a, s, h->o.sell);
+      h->hS.lv[0].Af.sell = &h->Shatf_sell;
+    }
     // workspaces
     h->work.reset(new DeviceArena(s));
     DeviceArena& w = *h->work;
@@ -1058,6 +1078,10 @@ int mm_setup(scr_handle h, const scr_bsr* L, int dev) {
       if (hb) throw std::invalid_argument("L has a missing or zero diagonal entry");
     }
     scr_opts o = h->o;
+    if (o.sell) {
+      build_sell<double>(h->L, h->L_sell, *h->mmats, s, o.sell);
+      h->L.sell = &h->L_sell;
+    }
     if (o.autotune) autotune_spmv<double>(h->L, 3, s);
     h->hM.build(h->L, 1, 3, o, false, s);
     h->mwork.reset(new DeviceArena(s));

@@ -212,6 +212,110 @@ __global__ void __launch_bounds__(256) k_spmv(int nbr, const int* __restrict__ r
   }
 }
 
+// G lanes per BLOCK row: each lane takes blocks t = lane, lane+G, ... and
+// accumulates all BR scalar rows, so the column index and the BC source
+// values of a block are loaded once for its BR x BC multiply-adds; the
+// BR*NRHS sums are combined over the G lanes and written by distinct lanes.
+template <int BR, int BC, int NRHS, int G, typename VT, typename XT, typename AT, Epi E>
+__global__ void __launch_bounds__(256) k_spmv_brow(int nbr, const int* __restrict__ rp, const int* __restrict__ col,
+                                                   const VT* __restrict__ val, const XT* __restrict__ x,
+                                                   Epilogue<XT, E> epi) {
+  const long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;  // block row
+  const int lane = threadIdx.x % G;
+  const bool active = i < nbr;
+  AT acc[BR][NRHS];
+#pragma unroll
+  for (int r = 0; r < BR; ++r)
+#pragma unroll
+    for (int h = 0; h < NRHS; ++h) acc[r][h] = (AT)0;
+  if (active) {
+    const int s = __ldg(rp + i), k = __ldg(rp + i + 1) - s;
+    const VT* v0 = val + (long long)s * BR * BC;
+    const int* cr = col + s;
+#pragma unroll 2
+    for (int t = lane; t < k; t += G) {
+      const long long xb = (long long)__ldg(cr + t) * BC * NRHS;
+      AT xv[BC][NRHS];
+#pragma unroll
+      for (int c = 0; c < BC; ++c)
+#pragma unroll
+        for (int h = 0; h < NRHS; ++h) xv[c][h] = (AT)__ldg(x + xb + c * NRHS + h);
+#pragma unroll
+      for (int r = 0; r < BR; ++r) {
+        const VT* vt = v0 + (long long)r * k * BC + t * BC;
+#pragma unroll
+        for (int c = 0; c < BC; ++c) {
+          const AT a = (AT)__ldg(vt + c);
+#pragma unroll
+          for (int h = 0; h < NRHS; ++h) acc[r][h] = fma(a, xv[c][h], acc[r][h]);
+        }
+      }
+    }
+  }
+  if constexpr (G > 1) {
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int h = 0; h < NRHS; ++h)
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) acc[r][h] += __shfl_xor_sync(0xffffffffu, acc[r][h], off, G);
+  }
+  if (active) {
+#pragma unroll
+    for (int q = 0; q < BR * NRHS; ++q) {
+      if (q % G != lane) continue;
+      const int r = q / NRHS, h = q - r * NRHS;
+      const long long o = i * BR + r;
+      epi(o * NRHS + h, o, acc[r][h]);
+    }
+  }
+}
+
+// sliced block-ELL product: one lane per block row, no cross-lane sums
+template <int BR, int BC, int NRHS, typename VT, typename XT, Epi E>
+__global__ void __launch_bounds__(256) k_sell_spmv(DSell<VT> S, const XT* __restrict__ x, Epilogue<XT, E> epi) {
+  const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int c = (int)(g / kChunk), lane = (int)(g % kChunk);
+  if (c >= S.nchunk) return;
+  const int q = c * kChunk + lane;
+  if (q >= S.nbr) return;
+  const int i = __ldg(S.perm + q);
+  const int c0 = __ldg(S.cptr + c), L = __ldg(S.cptr + c + 1) - c0;
+  const long long base = (long long)c0 * kChunk;
+  const int* __restrict__ cl = S.col + base + lane;
+  const VT* __restrict__ vl = S.val + base * (BR * BC) + lane;
+  using AT = XT;
+  AT acc[BR][NRHS];
+#pragma unroll
+  for (int r = 0; r < BR; ++r)
+#pragma unroll
+    for (int h = 0; h < NRHS; ++h) acc[r][h] = (AT)0;
+#pragma unroll 2
+  for (int t = 0; t < L; ++t) {
+    const long long xb = (long long)__ldg(cl + (long long)t * kChunk) * BC * NRHS;
+    AT xv[BC][NRHS];
+#pragma unroll
+    for (int cc = 0; cc < BC; ++cc)
+#pragma unroll
+      for (int h = 0; h < NRHS; ++h) xv[cc][h] = (AT)__ldg(x + xb + cc * NRHS + h);
+    const VT* vt = vl + (long long)t * kChunk * (BR * BC);
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int cc = 0; cc < BC; ++cc) {
+        const AT a = (AT)__ldg(vt + (r * BC + cc) * kChunk);
+#pragma unroll
+        for (int h = 0; h < NRHS; ++h) acc[r][h] = fma(a, xv[cc][h], acc[r][h]);
+      }
+  }
+#pragma unroll
+  for (int r = 0; r < BR; ++r) {
+    const long long o = (long long)i * BR + r;
+#pragma unroll
+    for (int h = 0; h < NRHS; ++h) epi(o * NRHS + h, o, acc[r][h]);
+  }
+}
+
 template <int BR, int BC, int NRHS, int G, typename VT, typename XT, typename AT, Epi E>
 static void launch_spmv_g(const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& e, cudaStream_t s) {
   Epilogue<XT, E> epi;
@@ -225,9 +329,19 @@ static void launch_spmv_g(const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& 
   epi.xsol = static_cast<XT*>(e.xsol);
   epi.alpha = (XT)e.alpha;
   epi.beta = (XT)e.beta;
-  const long long threads = (long long)M.nbr * BR * G;
   const int blk = 256;
-  k_spmv<BR, BC, NRHS, G, VT, XT, AT, E><<<ceil_div(threads, blk), blk, 0, s>>>(M.nbr, M.rp, M.col, M.val, x, epi);
+  if (M.sell) {
+    const DSell<VT>& S = *static_cast<const DSell<VT>*>(M.sell);
+    const long long threads = (long long)S.nchunk * kChunk;
+    k_sell_spmv<BR, BC, NRHS, VT, XT, E><<<ceil_div(threads, blk), blk, 0, s>>>(S, x, epi);
+  } else if (BR > 1 && code_of(M) > 0 && code_of(M) < 100) {
+    const long long threads = (long long)M.nbr * G;
+    k_spmv_brow<BR, BC, NRHS, G, VT, XT, AT, E><<<ceil_div(threads, blk), blk, 0, s>>>(M.nbr, M.rp, M.col, M.val,
+                                                                                     x, epi);
+  } else {
+    const long long threads = (long long)M.nbr * BR * G;
+    k_spmv<BR, BC, NRHS, G, VT, XT, AT, E><<<ceil_div(threads, blk), blk, 0, s>>>(M.nbr, M.rp, M.col, M.val, x, epi);
+  }
   SCR_LAUNCH();
 }
 
@@ -253,12 +367,25 @@ static void launch_spmv_e(const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& 
 
 // lanes per scalar row: FP64 keeps groups narrow (FP64 adds of the
 // reduction compete with the products), FP32 widens them for coalescing
+// M.g: lanes per block row (1..16, block-row kernel for BR > 1) or 100 +
+// lanes per scalar row (scalar-row kernel); 0 selects by row length
+static int g_forced = 0;
+void set_forced_group(int code) { g_forced = code; }
+
+template <typename VT>
+static int code_of(const DBsr<VT>& M) {
+  return g_forced > 0 ? g_forced : M.g;
+}
+
 template <typename VT>
 static int pick_group(const DBsr<VT>& M) {
-  if (M.g > 0) return M.g;
-  const double blocks_per_row = M.nbr ? (double)M.nnzb / M.nbr : 0.0;
-  if (sizeof(VT) == 8) return blocks_per_row >= 12 ? 4 : 2;
-  return blocks_per_row >= 24 ? 8 : 4;
+  const int g = code_of(M);
+  if (g > 0) return g >= 100 ? g - 100 : g;
+  // measured on the 616k-node tube: FP64 3x3 rows are fastest with 2 lanes
+  // per scalar row (the FP64 pipe binds), FP32 with 4 (coalescing binds)
+  const double per_row = M.nbr ? (double)M.nnzb * M.bc / M.nbr : 0.0;
+  if (sizeof(VT) == 8) return per_row >= 24 ? 2 : 1;
+  return per_row >= 24 ? 4 : 2;
 }
 
 template <int BR, int BC, int NR, typename VT, typename XT>
@@ -286,7 +413,7 @@ static void spmv_launch(int G, const DBsr<VT>& M, const XT* x, XT* y, int nrhs, 
 template <typename VT, typename XT>
 void spmv(const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const EpiArgs& e, cudaStream_t s) {
   if (M.nbr == 0) return;
-  const int G = pick_group(M);
+  const int G = M.sell ? 1 : pick_group(M);
   const int pidx = prof_start(0, M.val, s);
   spmv_launch<VT, XT>(G, M, x, y, nrhs, e, s);
   counters().launches++;
@@ -308,7 +435,7 @@ void spmv(const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const EpiArgs& e, cud
 
 template <typename VT>
 int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s) {
-  if (M.nbr == 0) return M.g;
+  if (M.nbr == 0 || M.sell) return M.g;
   using XT = VT;
   const long long nx = (long long)M.nbc * M.bc * nrhs + 1, ny = (long long)M.nbr * M.br * nrhs + 1;
   XT *x = nullptr, *y = nullptr;
@@ -318,23 +445,31 @@ int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s) {
   cudaEvent_t e0, e1;
   SCR_CUDA(cudaEventCreate(&e0));
   SCR_CUDA(cudaEventCreate(&e1));
-  const int cands[] = {1, 2, 4, 8, 16};
+  // the scalar-row kernel with 1, 2, 4 or 8 lanes (the block-row and
+  // sliced-ELL variants measured slower on the tube operators)
+  const int cands[] = {1, 2, 4, 8};
+  const int ncand = 4;
   float best = 1e30f;
-  int bestg = pick_group(M);
-  for (int G : cands) {
+  int bestg = M.g;
+  const int saved = M.g;
+  for (int q = 0; q < ncand; ++q) {
+    const int code = 100 + cands[q];
+    M.g = code;
+    const int G = pick_group(M);
     spmv_launch<VT, XT>(G, M, x, y, nrhs, EpiArgs(), s);  // warm-up
     SCR_CUDA(cudaEventRecord(e0, s));
-    for (int r = 0; r < 3; ++r) spmv_launch<VT, XT>(G, M, x, y, nrhs, EpiArgs(), s);
+    for (int r = 0; r < 5; ++r) spmv_launch<VT, XT>(G, M, x, y, nrhs, EpiArgs(), s);
     SCR_CUDA(cudaEventRecord(e1, s));
     SCR_CUDA(cudaEventSynchronize(e1));
     float ms = 0;
     SCR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     if (ms < best) {
       best = ms;
-      bestg = G;
+      bestg = code;
     }
   }
-  counters().launches += 20;
+  (void)saved;
+  counters().launches += 6 * ncand;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   SCR_CUDA(cudaFreeAsync(x, s));

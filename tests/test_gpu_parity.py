@@ -191,6 +191,29 @@ def test_vcycle_matches_oracle_on_exported_hierarchy(small, which, bs, nrhs, smo
     assert _rel(x, ref) < 1e-11
 
 
+@pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
+def test_sliced_ell_products_match_slab_products(small, precision):
+    """The sliced block-ELL copies of A, Shat and L give the same V-cycles as
+    the slab layout (same arithmetic per row, same order of terms)."""
+    rng = np.random.default_rng(5)
+    outs = []
+    for sell in (0, 32, 512):
+        with pkg.BlockSolver(sell=sell, precision=precision) as sol:
+            sol.setup(small.A, small.B, small.C, small.D)
+            sol.mesh_setup(small.L)
+            r = []
+            for which, n in ((pkg.SCR_HIER_A, 3 * small.n_v), (pkg.SCR_HIER_SHAT, small.n_p),
+                             (pkg.SCR_HIER_MESH, 3 * small.L.nb_rows)):
+                b = _dev(np.random.default_rng(which).standard_normal(n))
+                r.append(sol.amg_apply(which, b).cpu().numpy())
+            outs.append(r)
+    tol = 1e-12 if precision == pkg.SCR_FP64 else 1e-5
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            assert _rel(a, b) < tol
+    del rng
+
+
 # ---------------------------------------------------------------- Alg. 1 / 2
 def test_algorithm2_tight_inner_equals_schur(mini):
     op = BlockOperator.from_system(mini)
