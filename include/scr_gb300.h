@@ -240,6 +240,24 @@ int scr_export(scr_handle h, int which, int level, int kind, scr_bsr_out* out);
    x has nb_cols*bc entries, y nb_rows*br. */
 int scr_bsr_spmv(const scr_bsr* M, const double* x, double* y, void* cuda_stream);
 
+/* y = M x like scr_bsr_spmv, but without allocating any device memory.
+   The paper has no counterpart: this entry point exists for callers that
+   cannot let a library call cudaMalloc/cudaFree, such as code recorded into
+   a CUDA graph (allocation calls cannot be captured, and cudaFree waits for
+   the whole device), hosts whose device memory is owned by another
+   allocator or fixed at start-up, and tight loops that must not pay an
+   allocation per call.  Its scratch (the matrix values in the kernel's row
+   layout and a validation flag) is one static device array that every GPU
+   loading the library keeps until the process exits; matrices with more
+   than 2,097,152 stored scalars (nnzb * br * bc, 16 MiB) are rejected with
+   SCR_INVALID_ARG.  The first call on each device looks up the array's
+   device address (cudaGetSymbolAddress) with that device current; make
+   that first call before any stream capture.  All calls share the array:
+   calls whose work overlaps on the GPU (different streams, or different
+   host threads) race and give wrong results; serialise them.  Arguments,
+   layout and errors are those of scr_bsr_spmv. */
+int scr_bsr_spmv_noalloc(const scr_bsr* M, const double* x, double* y, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,7 +70,7 @@ EXPORTED = [
     "scr_default_opts", "scr_create", "scr_destroy", "scr_setup", "scr_solve", "scr_iters",
     "scr_residual", "scr_get_stats", "mm_setup", "mm_solve", "mm_iters", "scr_last_error",
     "scr_apply_op", "scr_apply_pc", "scr_apply_schur", "scr_amg_apply", "scr_amg_levels",
-    "scr_export", "scr_bsr_spmv", "scr_profile_begin", "scr_profile_end",
+    "scr_export", "scr_bsr_spmv", "scr_profile_begin", "scr_profile_end", "scr_bsr_spmv_noalloc",
 ]
 
 _lib = None
@@ -110,6 +110,7 @@ def load_library(build_if_missing: bool = False):
     L.scr_amg_levels.argtypes = [V, C.c_int, P(C.c_int)]
     L.scr_export.argtypes = [V, C.c_int, C.c_int, C.c_int, P(BsrOut)]
     L.scr_bsr_spmv.argtypes = [P(Bsr), V, V, V]
+    L.scr_bsr_spmv_noalloc.argtypes = [P(Bsr), V, V, V]
     L.scr_profile_begin.argtypes = [V, C.c_int, C.c_int]
     L.scr_profile_end.argtypes = [V, P(KProf)]
     for name in EXPORTED:

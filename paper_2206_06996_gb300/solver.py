@@ -259,3 +259,16 @@ def bsr_spmv(M: DeviceBSR, x, y=None, stream=None):
     s = Bsr(M.nb_rows, M.nb_cols, M.br, M.bc, M.nnzb, M.row_ptr.data_ptr(), M.col.data_ptr(), M.val.data_ptr())
     check(lib.scr_bsr_spmv(C.byref(s), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), C.c_void_p(stream)))
     return y
+
+
+def bsr_spmv_noalloc(M: DeviceBSR, x, y, stream=None):
+    """y = M x through scr_bsr_spmv_noalloc (no device allocation inside the
+    call; y must be preallocated)."""
+    torch = _torch()
+    lib = load_library()
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    s = Bsr(M.nb_rows, M.nb_cols, M.br, M.bc, M.nnzb, M.row_ptr.data_ptr(), M.col.data_ptr(), M.val.data_ptr())
+    check(lib.scr_bsr_spmv_noalloc(C.byref(s), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                   C.c_void_p(stream)))
+    return y
