@@ -168,19 +168,40 @@ template <int BC, int NRHS, int G, typename VT, typename XT, typename AT>
 __device__ __forceinline__ void scalar_row_accum(const int* __restrict__ rp, const int* __restrict__ col,
                                                  const VT* __restrict__ val, const XT* __restrict__ x, int BR,
                                                  int i, int r, int lane, AT (&acc)[NRHS]) {
+  // U blocks per lane in flight: the column indices are loaded first, then
+  // every gather and value of the batch, then the multiply-adds, so a lane
+  // keeps U independent load chains outstanding instead of one
+  constexpr int U = 4;
   const int s = __ldg(rp + i), k = __ldg(rp + i + 1) - s;
   const VT* vr = val + (long long)s * BR * BC + (long long)r * k * BC;
   const int* cr = col + s;
-#pragma unroll 2
-  for (int t = lane; t < k; t += G) {
-    const long long xb = (long long)__ldg(cr + t) * BC * NRHS;
-    const VT* vt = vr + t * BC;
+  for (int t0 = lane; t0 < k; t0 += G * U) {
+    int cidx[U];
 #pragma unroll
-    for (int c = 0; c < BC; ++c) {
-      const AT a = (AT)__ldg(vt + c);
-#pragma unroll
-      for (int h = 0; h < NRHS; ++h) acc[h] = fma(a, (AT)__ldg(x + xb + c * NRHS + h), acc[h]);
+    for (int u = 0; u < U; ++u) {
+      const int t = t0 + u * G;
+      cidx[u] = t < k ? __ldg(cr + t) : -1;
     }
+    AT a[U][BC], xv[U][BC][NRHS];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int t = t0 + u * G;
+      const bool ok = cidx[u] >= 0;
+      const long long xb = (long long)(ok ? cidx[u] : 0) * BC * NRHS;
+#pragma unroll
+      for (int c = 0; c < BC; ++c) {
+        a[u][c] = ok ? (AT)__ldg(vr + t * BC + c) : (AT)0;
+#pragma unroll
+        for (int h = 0; h < NRHS; ++h) xv[u][c][h] = ok ? (AT)__ldg(x + xb + c * NRHS + h) : (AT)0;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int c = 0; c < BC; ++c)
+#pragma unroll
+        for (int h = 0; h < NRHS; ++h)
+          if (cidx[u] >= 0) acc[h] = fma(a[u][c], xv[u][c][h], acc[h]);
   }
 }
 
