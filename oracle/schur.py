@@ -73,3 +73,14 @@ def simple_factored_dense(op: BlockOperator) -> np.ndarray:
     Df = np.block([[A, np.zeros((nv, np_))], [np.zeros((np_, nv)), Sh]])
     Uf = np.block([[np.eye(nv), dinv @ B], [np.zeros((np_, nv)), np.eye(np_)]])
     return Lf @ Df @ Uf
+
+
+def simple_inverse_apply_dense(op: BlockOperator, r: np.ndarray) -> np.ndarray:
+    """P_SIMPLE^{-1} r with exact solves (dense): U_SIMPLE^{-1} diag(A, Shat)^{-1} L^{-1} r."""
+    A = op.A.toarray()
+    Sh = schur_hat(op).toarray()
+    rv, rp = op.split(np.asarray(r, dtype=np.float64))
+    yv_hat = np.linalg.solve(A, rv)
+    yp = np.linalg.solve(Sh, rp - op.C @ yv_hat)
+    yv = yv_hat - (op.B @ yp) / np.diag(A)
+    return np.concatenate([yv, yp])

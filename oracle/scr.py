@@ -13,6 +13,13 @@ infrastructure only; the CPU reference of the whole solver path).
   inner GMRES + P_I solve to delta_I.
 * Outer level (Sec. 5.2.1): FGMRES on calA x = b preconditioned by P_SCR,
   tolerance delta, n^max.  P_A = P_I = AMG(A), P_S = AMG(Shat).
+* SIMPLE (Sec. 5.2.1): P_SIMPLE = L diag(A, Shat) U_SIMPLE with
+  L = [[I, 0], [C A^{-1}, I]] and U_SIMPLE = [[I, diag(A)^{-1} B], [0, I]];
+  its inverse applies L^{-1} (one A solve), diag(A^{-1}, Shat^{-1}) (the
+  same A solve and one GMRES + P_S solve with the explicit Shat, no inner
+  level) and U_SIMPLE^{-1}:
+      yhat_v = A^{-1} r_v, y_p = Shat^{-1} (r_p - C yhat_v),
+      y_v = yhat_v - diag(A)^{-1} B y_p.
 * Mesh motion (Sec. 5.2.2): CG + AMG(L) on the harmonic extension.
 """
 from __future__ import annotations
@@ -49,6 +56,7 @@ class SolverOptions:
     amg_pmax: int = 5
     smoother: str = "cheb"
     cheb_degree: int = 3
+    precond: str = "scr"       # "scr" (Algorithm 1) or "simple"
     mm_rtol: float = 1e-8
     mm_max_it: int = 500
 
@@ -106,10 +114,23 @@ class SCRSolver:
         yv = self.solve_A(rv2)
         return np.concatenate([yv, yp])
 
+    # SIMPLE --------------------------------------------------------------
+    def apply_simple(self, r: np.ndarray) -> np.ndarray:
+        o, op = self.opts, self.op
+        rv, rp = op.split(np.asarray(r, dtype=np.float64))
+        yv_hat = self.solve_A(rv)
+        rp2 = rp - op.C @ yv_hat
+        yp, info = gmres(lambda v: self.Shat @ v, rp2, lambda v: amg.vcycle(self.amg_S, v),
+                         tol=o.rtol_S, maxit=o.max_S, restart=o.restart_inner)
+        self.cnt.s_iters += info.iters
+        yv = yv_hat - (op.B @ yp) / op.A.diagonal()
+        return np.concatenate([yv, yp])
+
     # outer level --------------------------------------------------------
     def solve(self, b: np.ndarray, max_outer: int | None = None):
         o = self.opts
-        x, info = fgmres(self.op.matvec, b, self.apply_pc, tol=o.rtol,
+        pc = self.apply_simple if o.precond == "simple" else self.apply_pc
+        x, info = fgmres(self.op.matvec, b, pc, tol=o.rtol,
                          maxit=o.max_it if max_outer is None else max_outer, restart=o.restart)
         self.cnt.outer += info.iters
         return x, info

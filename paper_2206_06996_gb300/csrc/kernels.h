@@ -51,6 +51,7 @@ enum class Epi : int {
   Jacobi = 3,     // y = xs + (z - acc) * dinv[o]
   ChebFirst = 4,  // r = (z - acc) dinv[o]; dout = alpha r; y = xs + dout   (x = xs)
   ChebStep = 5,   // r -= acc dinv[o]; dout = alpha x + beta r; xsol += dout (x = d)
+  ScaledSub = 6,  // y = z - acc * dinv[o]
 };
 struct EpiArgs {
   Epi kind = Epi::Set;

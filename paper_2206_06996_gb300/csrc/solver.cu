@@ -573,6 +573,8 @@ struct scr_ctx {
   Gmres<float> gAf, gSf, gIf;
   double *bvec = nullptr, *xvec = nullptr, *rvec = nullptr;
   double *yhat = nullptr, *rp2 = nullptr, *rv2 = nullptr, *xbar = nullptr, *xt = nullptr;
+  double* dAinv = nullptr;  // 1 / diag(A) (SIMPLE upper factor)
+  float* dAinvf = nullptr;
   float *pr = nullptr, *py = nullptr, *yhatf = nullptr, *rp2f = nullptr, *rv2f = nullptr, *xbarf = nullptr,
         *xtf = nullptr;
   // mesh CG
@@ -686,19 +688,20 @@ int guarded(F&& f) {
 // ---- the operators of the path, in precision T ----
 template <typename T>
 struct PcView {
-  const DBsr<T>*A, *B, *C, *D;
+  const DBsr<T>*A, *B, *C, *D, *Shat;
   Hierarchy *hA, *hS;
   Gmres<T>*gA, *gS, *gI;
   T *yhat, *rp2, *rv2, *xbar, *xt;
+  const T* dAinv;
 };
 
 PcView<double> view64(scr_ctx* h) {
-  return PcView<double>{&h->A, &h->B, &h->C, &h->D, &h->hA, &h->hS, &h->gA, &h->gS, &h->gI,
-                        h->yhat, h->rp2, h->rv2, h->xbar, h->xt};
+  return PcView<double>{&h->A, &h->B, &h->C, &h->D, &h->Shat, &h->hA, &h->hS, &h->gA, &h->gS, &h->gI,
+                        h->yhat, h->rp2, h->rv2, h->xbar, h->xt, h->dAinv};
 }
 PcView<float> view32(scr_ctx* h) {
-  return PcView<float>{&h->Af, &h->Bf, &h->Cf, &h->Df, &h->hA, &h->hS, &h->gAf, &h->gSf, &h->gIf,
-                       h->yhatf, h->rp2f, h->rv2f, h->xbarf, h->xtf};
+  return PcView<float>{&h->Af, &h->Bf, &h->Cf, &h->Df, &h->hS.lv[0].Af, &h->hA, &h->hS, &h->gAf, &h->gSf, &h->gIf,
+                       h->yhatf, h->rp2f, h->rv2f, h->xbarf, h->xtf, h->dAinvf};
 }
 
 // Algorithm 2: y_p = D x_p - C A^{-1} (B x_p), A^{-1} by inner GMRES + P_I
@@ -759,16 +762,55 @@ void apply_pc(scr_ctx* h, PcView<T>& v, const T* r, T* y) {
   h->stats.a_iters += it;
 }
 
+// P_SIMPLE^{-1} r = U_SIMPLE^{-1} diag(A, Shat)^{-1} L^{-1} r (Sec. 5.2.1):
+//   yhat_v = A^{-1} r_v (GMRES + P_A), y_p = Shat^{-1} (r_p - C yhat_v)
+//   (GMRES + P_S on the explicit Shat, no inner level),
+//   y_v = yhat_v - diag(A)^{-1} B y_p
+template <typename T>
+void apply_simple(scr_ctx* h, PcView<T>& v, const T* r, T* y) {
+  cudaStream_t s = h->s;
+  const long long nv3 = 3LL * h->nv;
+  const T* rv = r;
+  const T* rp = r + nv3;
+  T* yv = y;
+  T* yp = y + nv3;
+  typename Gmres<T>::Op opA = [&](const T* x, T* o) { spmv<T, T>(*v.A, x, o, 1, EpiArgs(), s); };
+  typename Gmres<T>::Op pcA = [&](const T* b, T* x) { v.hA->template apply<T>(b, x, s); };
+  typename Gmres<T>::Op opS = [&](const T* x, T* o) { spmv<T, T>(*v.Shat, x, o, 1, EpiArgs(), s); };
+  typename Gmres<T>::Op pcS = [&](const T* b, T* x) { v.hS->template apply<T>(b, x, s); };
+  int it = 0;
+  double rel = 0;
+  v.gA->solve(opA, &pcA, rv, v.yhat, h->o.rtol_A, h->o.max_A, h->red, s, &it, &rel);
+  h->stats.a_solves++;
+  h->stats.a_iters += it;
+  EpiArgs e;
+  e.kind = Epi::Axpby;
+  e.alpha = -1.0;
+  e.beta = 1.0;
+  e.z = rp;
+  spmv<T, T>(*v.C, v.yhat, v.rp2, 1, e, s);
+  v.gS->solve(opS, &pcS, v.rp2, yp, h->o.rtol_S, h->o.max_S, h->red, s, &it, &rel);
+  h->stats.s_iters += it;
+  EpiArgs u;
+  u.kind = Epi::ScaledSub;
+  u.z = v.yhat;
+  u.dinv = v.dAinv;
+  spmv<T, T>(*v.B, yp, yv, 1, u, s);
+}
+
 void apply_pc_any(scr_ctx* h, const double* r, double* y) {
+  const bool simple = h->o.precond == SCR_PC_SIMPLE;
   if (h->o.precision == SCR_MIXED) {
     const long long n = 3LL * h->nv + h->np;
     cast_d2f(r, h->pr, n, h->s);
     PcView<float> v = view32(h);
-    apply_pc<float>(h, v, h->pr, h->py);
+    if (simple) apply_simple<float>(h, v, h->pr, h->py);
+    else apply_pc<float>(h, v, h->pr, h->py);
     cast_f2d(h->py, y, n, h->s);
   } else {
     PcView<double> v = view64(h);
-    apply_pc<double>(h, v, r, y);
+    if (simple) apply_simple<double>(h, v, r, y);
+    else apply_pc<double>(h, v, r, y);
   }
 }
 
@@ -832,7 +874,7 @@ int scr_create(scr_handle* out, const scr_opts* o, void* stream) {
     if (op.restart < 1 || op.restart >= kMaxBasis || op.restart_inner < 1 || op.restart_inner >= kMaxBasis)
       throw std::invalid_argument("restart lengths must lie in [1, 63]");
     if (op.precision != SCR_FP64 && op.precision != SCR_MIXED) throw std::invalid_argument("unknown precision");
-    if (op.precond != 0) throw std::invalid_argument("only the SCR preconditioner (precond = 0) is built");
+    if (op.precond != SCR_PC_SCR && op.precond != SCR_PC_SIMPLE) throw std::invalid_argument("unknown preconditioner");
     if (op.amg_smoother != SCR_SMOOTH_L1 && op.amg_smoother != SCR_SMOOTH_CHEB)
       throw std::invalid_argument("unknown smoother");
     if (op.amg_degree < 1 || op.amg_degree > 16) throw std::invalid_argument("Chebyshev degree must lie in [1, 16]");
@@ -904,6 +946,8 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
       SCR_CUDA(cudaStreamSynchronize(s));
     }
     if (h->o.verbose) fprintf(stderr, "[setup] Shat %.2f ms (%lld entries)\n", ms_since(t1), h->Shat.nnzb);
+    h->dAinv = a.alloc<double>(3LL * nv + 1);
+    inv_diag(h->A, h->dAinv, s);
     const bool f32 = h->o.precision == SCR_MIXED;
     if (h->o.sell) {
       build_sell<double>(h->A, h->A_sell, a, s, h->o.sell);
@@ -944,6 +988,8 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
     h->xvec = w.alloc<double>(n + 1);
     h->rvec = w.alloc<double>(n + 1);
     if (f32) {
+      h->dAinvf = w.alloc<float>(nv3 + 1);
+      cast_d2f(h->dAinv, h->dAinvf, nv3, s);
       h->gAf.init(w, nv3, h->o.restart_inner);
       h->gSf.init(w, np, h->o.restart_inner);
       h->gIf.init(w, nv3, h->o.restart_inner);

@@ -118,6 +118,34 @@ def test_simple_identity(tiny_system):
     assert np.allclose(P1, P2, rtol=1e-9, atol=1e-12 * np.abs(P1).max())
 
 
+def test_simple_inverse_is_inverse_of_simple_matrix(tiny_system):
+    op = BlockOperator.from_system(tiny_system)
+    rng = np.random.default_rng(8)
+    r = rng.standard_normal(op.n)
+    y = schur.simple_inverse_apply_dense(op, r)
+    P = schur.simple_matrix_dense(op)
+    assert np.linalg.norm(P @ y - r) <= 1e-9 * np.linalg.norm(r)
+
+
+def test_simple_apply_with_tight_solves(tiny_system):
+    opts = scr.SolverOptions(rtol_A=1e-13, rtol_S=1e-13, max_A=400, max_S=400, restart_inner=80,
+                             precond="simple")
+    s = scr.SCRSolver(tiny_system, opts)
+    rng = np.random.default_rng(9)
+    r = rng.standard_normal(s.op.n)
+    y = s.apply_simple(r)
+    yd = schur.simple_inverse_apply_dense(s.op, r)
+    assert np.linalg.norm(y - yd) <= 1e-8 * np.linalg.norm(yd)
+
+
+def test_simple_full_solve_matches_direct(mini_system, mini_direct):
+    s = scr.SCRSolver(mini_system, scr.SolverOptions(precond="simple"))
+    x, info = s.solve(mini_system.b)
+    assert info.converged
+    assert s.rel_residual(x, mini_system.b) <= 1e-8
+    assert np.linalg.norm(x - mini_direct) <= 1e-6 * np.linalg.norm(mini_direct)
+
+
 # ------------------------------------------------------------- krylov
 def _nonsym(rng, n):
     return np.eye(n) * 4 + rng.standard_normal((n, n)) / np.sqrt(n)
