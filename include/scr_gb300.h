@@ -170,6 +170,22 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
    FP64 with calA (scr_residual). */
 int scr_solve(scr_handle h, const double* b, double* x, int ptr_is_device);
 
+/* ---------------- batched form: many independent systems at once --------
+   nb independent block systems (each as in scr_setup, arrays A[i] ...
+   D[i]) are set up and solved together as one block-diagonal system, so
+   every kernel launch of the solve covers all members; the AMG aggregates
+   never cross members (they have no connections), so each level of the
+   hierarchies stays block-diagonal.  The outer tolerance is tightened to
+   rtol * min_i ||b_i|| / ||b||, which guarantees ||b_i - calA_i x_i|| <=
+   rtol ||b_i|| for every member; the per-member FP64 relative residuals
+   are available from scr_batch_residuals.  Member i's vectors have length
+   3 n_v(i) + n_p(i) in the usual order.  Errors as in scr_setup /
+   scr_solve; SCR_NOT_CONVERGED if a member with b_i != 0 misses rtol. */
+int scr_setup_batch(scr_handle h, int nb, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C,
+                    const scr_bsr* D, int ptr_is_device);
+int scr_solve_batch(scr_handle h, const double* const* b, double* const* x, int ptr_is_device);
+int scr_batch_residuals(scr_handle h, double* rel_res /* nb entries */);
+
 /* Iteration counts of the last scr_solve: outer FGMRES and the sum of all
    intermediate and inner GMRES iterations. */
 int scr_iters(scr_handle h, int* outer, int* inner_total);

@@ -72,6 +72,7 @@ EXPORTED = [
     "scr_residual", "scr_get_stats", "mm_setup", "mm_solve", "mm_iters", "scr_last_error",
     "scr_apply_op", "scr_apply_pc", "scr_apply_schur", "scr_amg_apply", "scr_amg_levels",
     "scr_export", "scr_bsr_spmv", "scr_profile_begin", "scr_profile_end", "scr_bsr_spmv_noalloc",
+    "scr_setup_batch", "scr_solve_batch", "scr_batch_residuals",
 ]
 
 _lib = None
@@ -112,6 +113,9 @@ def load_library(build_if_missing: bool = False):
     L.scr_export.argtypes = [V, C.c_int, C.c_int, C.c_int, P(BsrOut)]
     L.scr_bsr_spmv.argtypes = [P(Bsr), V, V, V]
     L.scr_bsr_spmv_noalloc.argtypes = [P(Bsr), V, V, V]
+    L.scr_setup_batch.argtypes = [V, C.c_int, P(Bsr), P(Bsr), P(Bsr), P(Bsr), C.c_int]
+    L.scr_solve_batch.argtypes = [V, P(V), P(V), C.c_int]
+    L.scr_batch_residuals.argtypes = [V, P(C.c_double)]
     L.scr_profile_begin.argtypes = [V, C.c_int, C.c_int]
     L.scr_profile_end.argtypes = [V, P(KProf)]
     for name in EXPORTED:

@@ -583,6 +583,11 @@ struct scr_ctx {
   HostScalars mhs;
   scr_stats stats;
   int counters_outer = 0;
+  // batched form: member sizes and offsets inside the union system
+  int nbatch = 0;
+  std::vector<int> b_nv, b_np, b_vo, b_po;
+  std::vector<double> b_rel;
+  double* b_norms = nullptr;  // device, 2 per member
 };
 
 namespace {
@@ -915,6 +920,7 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
     cudaStream_t s = h->s;
     SCR_CUDA(cudaStreamSynchronize(s));
     h->have_block = false;
+    h->nbatch = 0;
     h->hA = Hierarchy();
     h->hS = Hierarchy();
     h->work.reset();
@@ -1025,7 +1031,7 @@ static void reset_solve_stats(scr_ctx* h) {
   h->gAf.syncs = h->gSf.syncs = h->gIf.syncs = 0;
 }
 
-static int solve_impl(scr_ctx* h, const double* b, double* x) {
+static int solve_impl(scr_ctx* h, const double* b, double* x, double rtol) {
   const long long n = 3LL * h->nv + h->np;
   reset_solve_stats(h);
   Gmres<double>::Op op = [&](const double* xi, double* y) {
@@ -1035,7 +1041,7 @@ static int solve_impl(scr_ctx* h, const double* b, double* x) {
   std::function<double(const double*)> tr = [&](const double* xi) { return true_rel_block(h, b, xi); };
   int it = 0;
   double rel = 0;
-  const bool ok = h->gOuter.solve(op, &pc, b, x, h->o.rtol, h->o.max_it, h->red, h->s, &it, &rel, &tr);
+  const bool ok = h->gOuter.solve(op, &pc, b, x, rtol, h->o.max_it, h->red, h->s, &it, &rel, &tr);
   h->stats.outer_iters = it;
   h->stats.rel_res = true_rel_block(h, b, x);
   h->stats.vcycles_A = h->hA.vcycles;
@@ -1044,7 +1050,7 @@ static int solve_impl(scr_ctx* h, const double* b, double* x) {
                    h->gIf.syncs;
   (void)n;
   if (!std::isfinite(h->stats.rel_res)) return SCR_NOT_CONVERGED;
-  return (ok && h->stats.rel_res <= h->o.rtol) ? SCR_OK : SCR_NOT_CONVERGED;
+  return (ok && h->stats.rel_res <= rtol) ? SCR_OK : SCR_NOT_CONVERGED;
 }
 
 int scr_solve(scr_handle h, const double* b, double* x, int dev) {
@@ -1064,7 +1070,7 @@ int scr_solve(scr_handle h, const double* b, double* x, int dev) {
       bd = h->bvec;
       xd = h->xvec;
     }
-    status = solve_impl(h, bd, xd);
+    status = solve_impl(h, bd, xd, h->o.rtol);
     if (!dev) SCR_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
     SCR_CUDA(cudaStreamSynchronize(h->s));
     h->stats.solve_ms = ms_since(t0);
@@ -1074,6 +1080,204 @@ int scr_solve(scr_handle h, const double* b, double* x, int dev) {
     set_last_error("FGMRES stopped at %d iterations with relative residual %.3e", h->stats.outer_iters,
                    h->stats.rel_res);
   return status;
+}
+
+// ------------------------------------------------------------ batched form
+namespace {
+
+__global__ void k_add_offset(int* __restrict__ a, long long n, int off) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) a[i] += off;
+}
+
+// Concatenate nb block matrices into one block-diagonal device matrix
+// (standard value layout); row and column offsets in blocks.
+struct UnionMatrix {
+  int* rp = nullptr;
+  int* col = nullptr;
+  double* val = nullptr;
+  scr_bsr desc{};
+};
+
+UnionMatrix build_union(int nb, const scr_bsr* M, int br, int bc, const std::vector<int>& roff,
+                        const std::vector<int>& coff, int nrows, int ncols, int dev, DeviceArena& a,
+                        cudaStream_t s, const char* name) {
+  UnionMatrix U;
+  long long nnz = 0;
+  for (int i = 0; i < nb; ++i) {
+    check_bsr(&M[i], br, bc, M[i].nb_rows, M[i].nb_cols, name);
+    nnz += M[i].nnzb;
+  }
+  if (nnz > 2147483647LL) throw std::invalid_argument("batched matrix exceeds int32 block indices");
+  const int bs = br * bc;
+  U.rp = a.alloc<int>(nrows + 1);
+  U.col = a.alloc<int>(nnz + 1);
+  U.val = a.alloc<double>(nnz * bs + 1);
+  const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  long long off = 0;
+  for (int i = 0; i < nb; ++i) {
+    const scr_bsr& m = M[i];
+    int first = 0, last = 0;
+    SCR_CUDA(cudaMemcpyAsync(&first, m.row_ptr, sizeof(int), dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+    SCR_CUDA(cudaMemcpyAsync(&last, m.row_ptr + m.nb_rows, sizeof(int),
+                             dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s));
+    SCR_CUDA(cudaStreamSynchronize(s));
+    if (first != 0 || last != m.nnzb) throw std::invalid_argument(std::string(name) + ": row_ptr inconsistent");
+    if (m.nb_rows > 0) {
+      SCR_CUDA(cudaMemcpyAsync(U.rp + roff[i], m.row_ptr, sizeof(int) * m.nb_rows, k, s));
+      k_add_offset<<<ceil_div(m.nb_rows, 256), 256, 0, s>>>(U.rp + roff[i], m.nb_rows, (int)off);
+      SCR_LAUNCH();
+    }
+    if (m.nnzb > 0) {
+      SCR_CUDA(cudaMemcpyAsync(U.col + off, m.col_idx, sizeof(int) * m.nnzb, k, s));
+      k_add_offset<<<ceil_div(m.nnzb, 256), 256, 0, s>>>(U.col + off, m.nnzb, coff[i]);
+      SCR_LAUNCH();
+      SCR_CUDA(cudaMemcpyAsync(U.val + off * bs, m.val, sizeof(double) * m.nnzb * bs, k, s));
+    }
+    off += m.nnzb;
+  }
+  const int total = (int)nnz;
+  SCR_CUDA(cudaMemcpyAsync(U.rp + nrows, &total, sizeof(int), cudaMemcpyHostToDevice, s));
+  SCR_CUDA(cudaStreamSynchronize(s));
+  U.desc.nb_rows = nrows;
+  U.desc.nb_cols = ncols;
+  U.desc.br = br;
+  U.desc.bc = bc;
+  U.desc.nnzb = total;
+  U.desc.row_ptr = U.rp;
+  U.desc.col_idx = U.col;
+  U.desc.val = U.val;
+  return U;
+}
+
+}  // namespace
+
+int scr_setup_batch(scr_handle h, int nb, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C, const scr_bsr* D,
+                    int dev) {
+  if (!h || nb < 1 || !A || !B || !C || !D) {
+    set_last_error("scr_setup_batch: NULL argument or nb < 1");
+    return SCR_INVALID_ARG;
+  }
+  std::vector<int> nv(nb), np(nb), vo(nb), po(nb);
+  int NV = 0, NP = 0;
+  for (int i = 0; i < nb; ++i) {
+    nv[i] = A[i].nb_rows;
+    np[i] = D[i].nb_rows;
+    if (nv[i] < 0 || np[i] < 0) {
+      set_last_error("scr_setup_batch: negative size");
+      return SCR_INVALID_ARG;
+    }
+    vo[i] = NV;
+    po[i] = NP;
+    NV += nv[i];
+    NP += np[i];
+  }
+  int rc = SCR_OK;
+  DeviceArena tmp(h->s);
+  UnionMatrix UA, UB, UC, UD;
+  rc = guarded([&] {
+    for (int i = 0; i < nb; ++i) {
+      check_bsr(&A[i], 3, 3, nv[i], nv[i], "A");
+      check_bsr(&B[i], 3, 1, nv[i], np[i], "B");
+      check_bsr(&C[i], 1, 3, np[i], nv[i], "C");
+      check_bsr(&D[i], 1, 1, np[i], np[i], "D");
+    }
+    UA = build_union(nb, A, 3, 3, vo, vo, NV, NV, dev, tmp, h->s, "A");
+    UB = build_union(nb, B, 3, 1, vo, po, NV, NP, dev, tmp, h->s, "B");
+    UC = build_union(nb, C, 1, 3, po, vo, NP, NV, dev, tmp, h->s, "C");
+    UD = build_union(nb, D, 1, 1, po, po, NP, NP, dev, tmp, h->s, "D");
+  });
+  if (rc != SCR_OK) return rc;
+  rc = scr_setup(h, &UA.desc, &UB.desc, &UC.desc, &UD.desc, 1);
+  if (rc != SCR_OK) return rc;
+  return guarded([&] {
+    h->nbatch = nb;
+    h->b_nv = nv;
+    h->b_np = np;
+    h->b_vo = vo;
+    h->b_po = po;
+    h->b_rel.assign(nb, 0.0);
+    h->b_norms = h->work->alloc<double>(2LL * nb + 2);
+    SCR_CUDA(cudaStreamSynchronize(h->s));
+  });
+}
+
+namespace {
+
+// out[2i] = ||v_i||^2, out[2i+1] = ||p_i||^2 of the union vector u, copied to host
+std::vector<double> member_norms(scr_ctx* h, const double* u) {
+  const int nb = h->nbatch;
+  const long long NV3 = 3LL * h->nv;
+  for (int i = 0; i < nb; ++i) {
+    norm2<double>(u + 3LL * h->b_vo[i], 3LL * h->b_nv[i], h->b_norms + 2 * i, h->red, h->s);
+    norm2<double>(u + NV3 + h->b_po[i], h->b_np[i], h->b_norms + 2 * i + 1, h->red, h->s);
+  }
+  std::vector<double> out(2 * nb);
+  SCR_CUDA(cudaMemcpyAsync(out.data(), h->b_norms, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, h->s));
+  SCR_CUDA(cudaStreamSynchronize(h->s));
+  return out;
+}
+
+}  // namespace
+
+int scr_solve_batch(scr_handle h, const double* const* b, double* const* x, int dev) {
+  if (!h || !b || !x) return SCR_INVALID_ARG;
+  if (!h->have_block || h->nbatch == 0) {
+    set_last_error("scr_solve_batch before scr_setup_batch");
+    return SCR_INVALID_ARG;
+  }
+  int status = SCR_OK;
+  int rc = guarded([&] {
+    auto t0 = Clock::now();
+    const int nb = h->nbatch;
+    const long long NV3 = 3LL * h->nv;
+    const cudaMemcpyKind kin = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind kout = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    for (int i = 0; i < nb; ++i) {
+      if (!b[i] || !x[i]) throw std::invalid_argument("scr_solve_batch: NULL member vector");
+      const long long v3 = 3LL * h->b_nv[i];
+      if (v3) SCR_CUDA(cudaMemcpyAsync(h->bvec + 3LL * h->b_vo[i], b[i], sizeof(double) * v3, kin, h->s));
+      if (h->b_np[i])
+        SCR_CUDA(cudaMemcpyAsync(h->bvec + NV3 + h->b_po[i], b[i] + v3, sizeof(double) * h->b_np[i], kin, h->s));
+    }
+    // every member's relative residual stays below rtol when the union's
+    // does below rtol * min_i ||b_i|| / ||b||
+    std::vector<double> bn = member_norms(h, h->bvec);
+    double btot = 0.0, bmin = INFINITY;
+    for (int i = 0; i < nb; ++i) {
+      const double bi = bn[2 * i] + bn[2 * i + 1];
+      btot += bi;
+      if (bi > 0.0) bmin = std::min(bmin, std::sqrt(bi));
+    }
+    btot = std::sqrt(btot);
+    const double rtol = (btot > 0.0 && std::isfinite(bmin)) ? h->o.rtol * bmin / btot : h->o.rtol;
+    status = solve_impl(h, h->bvec, h->xvec, rtol);
+    block_op(h->A, h->B, h->C, h->D, h->xvec, h->rvec, h->bvec, true, h->s);
+    std::vector<double> rn = member_norms(h, h->rvec);
+    for (int i = 0; i < nb; ++i) {
+      const double bi = std::sqrt(bn[2 * i] + bn[2 * i + 1]);
+      const double ri = std::sqrt(rn[2 * i] + rn[2 * i + 1]);
+      h->b_rel[i] = bi > 0.0 ? ri / bi : ri;
+      if (!(h->b_rel[i] <= h->o.rtol) && bi > 0.0) status = SCR_NOT_CONVERGED;
+    }
+    for (int i = 0; i < nb; ++i) {
+      const long long v3 = 3LL * h->b_nv[i];
+      if (v3) SCR_CUDA(cudaMemcpyAsync(x[i], h->xvec + 3LL * h->b_vo[i], sizeof(double) * v3, kout, h->s));
+      if (h->b_np[i])
+        SCR_CUDA(cudaMemcpyAsync(x[i] + v3, h->xvec + NV3 + h->b_po[i], sizeof(double) * h->b_np[i], kout, h->s));
+    }
+    SCR_CUDA(cudaStreamSynchronize(h->s));
+    h->stats.solve_ms = ms_since(t0);
+  });
+  if (rc != SCR_OK) return rc;
+  if (status == SCR_NOT_CONVERGED) set_last_error("batched solve: a member did not reach the tolerance");
+  return status;
+}
+
+int scr_batch_residuals(scr_handle h, double* rel_res) {
+  if (!h || !rel_res || h->nbatch == 0) return SCR_INVALID_ARG;
+  for (int i = 0; i < h->nbatch; ++i) rel_res[i] = h->b_rel[i];
+  return SCR_OK;
 }
 
 int scr_iters(scr_handle h, int* outer, int* inner_total) {

@@ -166,6 +166,50 @@ class BlockSolver:
         check(self.lib.scr_get_stats(self.h, C.byref(s)))
         return s.as_dict()
 
+    # -------------------------------------------------------------- batched form
+    def setup_batch(self, systems):
+        """systems: list of (A, B, C, D), all host (numpy) or all device."""
+        keep: list = []
+        nb = len(systems)
+        arrs = [(Bsr * nb)() for _ in range(4)]
+        devs = set()
+        for i, sysm in enumerate(systems):
+            for j in range(4):
+                st, d = _as_bsr(sysm[j], keep)
+                arrs[j][i] = st
+                devs.add(d)
+        if len(devs) != 1:
+            raise ValueError("all members must be on the host or all on the device")
+        check(self.lib.scr_setup_batch(self.h, nb, arrs[0], arrs[1], arrs[2], arrs[3], devs.pop()))
+        self.batch_sizes = [(sysm[0].nb_rows, sysm[3].nb_rows) for sysm in systems]
+        return self
+
+    def solve_batch(self, bs, xs=None, raise_on_nonconvergence: bool = True):
+        nb = len(bs)
+        keep: list = []
+        if xs is None:
+            xs = [np.empty_like(np.asarray(b, dtype=np.float64)) if isinstance(b, np.ndarray)
+                  else _torch().empty_like(b) for b in bs]
+        pb = (C.c_void_p * nb)()
+        px = (C.c_void_p * nb)()
+        devs = set()
+        for i in range(nb):
+            a, d = _ptr(bs[i], keep)
+            c, e = _ptr(xs[i], keep)
+            pb[i], px[i] = a, c
+            devs.update((d, e))
+        if len(devs) != 1:
+            raise ValueError("vectors must all be host or all device")
+        st = self.lib.scr_solve_batch(self.h, pb, px, devs.pop())
+        check(st, (SCR_OK,) if raise_on_nonconvergence else (SCR_OK, SCR_NOT_CONVERGED))
+        return xs
+
+    def batch_residuals(self):
+        n = len(self.batch_sizes)
+        r = (C.c_double * n)()
+        check(self.lib.scr_batch_residuals(self.h, r))
+        return np.array(r[:])
+
     # -------------------------------------------------------------- mesh
     def mesh_setup(self, L):
         keep: list = []
