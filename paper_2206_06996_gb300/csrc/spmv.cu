@@ -10,6 +10,9 @@
 // reduction than on the product itself.
 #include <cstdarg>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "kernels.h"
 
@@ -468,9 +471,37 @@ void spmv(const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const EpiArgs& e, cud
   }
 }
 
+// Decisions are cached by (shape, size, precision, right-hand sides): a
+// Newton step's new Jacobian has the pattern of the previous one, so the
+// timing runs once per pattern.
+struct TuneKey {
+  long long nnzb;
+  int nbr, nbc, br, bc, vt, nrhs, dev;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(nnzb, nbr, nbc, br, bc, vt, nrhs, dev) <
+           std::tie(o.nnzb, o.nbr, o.nbc, o.br, o.bc, o.vt, o.nrhs, o.dev);
+  }
+};
+static std::map<TuneKey, int>& tune_cache() {
+  static std::map<TuneKey, int> m;
+  return m;
+}
+static std::mutex g_tune_mutex;
+
 template <typename VT>
 int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s) {
   if (M.nbr == 0 || M.sell) return M.g;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const TuneKey key{M.nnzb, M.nbr, M.nbc, M.br, M.bc, (int)sizeof(VT), nrhs, dev};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = tune_cache().find(key);
+    if (it != tune_cache().end()) {
+      M.g = it->second;
+      return M.g;
+    }
+  }
   using XT = VT;
   const long long nx = (long long)M.nbc * M.bc * nrhs + 1, ny = (long long)M.nbr * M.br * nrhs + 1;
   XT *x = nullptr, *y = nullptr;
@@ -510,6 +541,10 @@ int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s) {
   SCR_CUDA(cudaFreeAsync(x, s));
   SCR_CUDA(cudaFreeAsync(y, s));
   M.g = bestg;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    tune_cache()[key] = bestg;
+  }
   return bestg;
 }
 template int autotune_spmv<double>(DBsr<double>&, int, cudaStream_t);

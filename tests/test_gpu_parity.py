@@ -460,3 +460,19 @@ def test_batched_64_tubes_mixed():
         assert rel_residual(BlockOperator.from_system(m), x, m.b) <= 1e-8
     smallest = int(np.argmin([m.n for m in members]))
     assert _rel(xs[smallest], direct.solve_block(members[smallest])) <= 1e-6
+
+
+def test_outer_iterations_grow_with_the_time_step():
+    """Robustness trend (paper, AAA model: SCR outer iterations 2.1 / 3.1 /
+    5.1 for dt = 1e-5 / 1e-4 / 1e-3): on the small tube the outer count does
+    not decrease as dt grows, and every solve meets the tolerance."""
+    counts = []
+    for dt in (1e-5, 1e-4, 1e-3):
+        s = F.tube_system("tube_small", dt=dt)
+        with pkg.BlockSolver() as sol:
+            sol.setup(s.A, s.B, s.C, s.D)
+            x = sol.solve(s.b.copy())
+            counts.append(sol.iters()[0])
+        assert rel_residual(BlockOperator.from_system(s), x, s.b) <= 1e-8
+    assert counts[0] <= counts[1] <= counts[2], counts
+    assert counts[2] <= 20, counts
