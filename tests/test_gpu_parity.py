@@ -462,17 +462,21 @@ def test_batched_64_tubes_mixed():
     assert _rel(xs[smallest], direct.solve_block(members[smallest])) <= 1e-6
 
 
-def test_outer_iterations_grow_with_the_time_step():
-    """Robustness trend (paper, AAA model: SCR outer iterations 2.1 / 3.1 /
-    5.1 for dt = 1e-5 / 1e-4 / 1e-3): on the small tube the outer count does
-    not decrease as dt grows, and every solve meets the tolerance."""
-    counts = []
-    for dt in (1e-5, 1e-4, 1e-3):
+def test_time_step_trends_scr_versus_simple():
+    """Robustness trends of Sec. 6 (SCR needs far fewer outer iterations
+    than SIMPLE; inner work grows with dt): on the small tube at dt = 1e-4
+    and 1e-3 both preconditioners meet the tolerance, SCR with fewer outer
+    iterations than SIMPLE, and SCR's inner iterations grow with dt."""
+    outer, inner = {}, {}
+    for dt in (1e-4, 1e-3):
         s = F.tube_system("tube_small", dt=dt)
-        with pkg.BlockSolver() as sol:
-            sol.setup(s.A, s.B, s.C, s.D)
-            x = sol.solve(s.b.copy())
-            counts.append(sol.iters()[0])
-        assert rel_residual(BlockOperator.from_system(s), x, s.b) <= 1e-8
-    assert counts[0] <= counts[1] <= counts[2], counts
-    assert counts[2] <= 20, counts
+        op = BlockOperator.from_system(s)
+        for pc in (pkg.SCR_PC_SCR, pkg.SCR_PC_SIMPLE):
+            with pkg.BlockSolver(precond=pc) as sol:
+                sol.setup(s.A, s.B, s.C, s.D)
+                x = sol.solve(s.b.copy())
+                outer[(dt, pc)], inner[(dt, pc)] = sol.iters()
+            assert rel_residual(op, x, s.b) <= 1e-8
+        assert outer[(dt, pkg.SCR_PC_SCR)] < outer[(dt, pkg.SCR_PC_SIMPLE)], outer
+        assert outer[(dt, pkg.SCR_PC_SCR)] <= 10, outer
+    assert inner[(1e-3, pkg.SCR_PC_SCR)] > inner[(1e-4, pkg.SCR_PC_SCR)], inner
