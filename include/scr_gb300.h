@@ -99,10 +99,19 @@ typedef struct {
   int amg_smoother;   /* 0: l1-Jacobi (amg_nu sweeps); 1: Chebyshev on D^{-1}A (default) */
   int amg_degree;     /* Chebyshev degree, 3 */
   int spmv_group;     /* 0: autotune/heuristic; 1..16: lanes per block row; 101..116: 100 + lanes per
-                         scalar row (forces the product kernel of every matrix) */
+                         scalar row; 201, 202, 204, 208: staged kernel with 1..8 lanes per scalar row
+                         where the matrix has a tile plan (forces the product kernel of every matrix) */
   int sell;           /* 0: slab products; W > 0: products with A, Shat and L use a sliced block-ELL
                          copy with rows sorted by length inside windows of W block rows
                          (W a multiple of 32, at most 1024); default 0 */
+  int staged;         /* 1: the products with A, Shat, L and the two finest levels of each hierarchy
+                         get a tile plan, and the autotuner also times the staged kernel (tiles
+                         bulk-copied into shared memory ahead of the lanes); 0 (default): never
+                         staged (measured slower than the scalar-row kernel on the tube operators) */
+  int stage_kb;       /* staged kernel: KiB of matrix data per stage, 4..96, default 16 */
+  int stages;         /* staged kernel: tiles in flight per CTA, 2..4, default 2 */
+  int l2_prefetch;    /* scalar-row products: each CTA prefetches into L2 the values and indices of
+                         the CTA this many indices ahead (bulk L2 prefetch); 0 off; default 192 */
   double mm_rtol;     /* mesh CG relative residual, 1e-8 */
   int mm_max_it;      /* mesh CG iteration cap, 500 */
   int verbose;        /* 0 quiet */
@@ -138,10 +147,11 @@ typedef struct {
   double rel_res;       /* final FP64 ||b - calA x|| / ||b|| of the last scr_solve */
   double mm_rel_res;
   double setup_ms, solve_ms, mm_setup_ms, mm_solve_ms; /* host wall clock */
-  long long kernel_launches;  /* launches issued by this handle since creation */
-  long long spmv_bytes;       /* modelled HBM bytes of the SpMV-type launches */
+  long long kernel_launches;  /* library launches issued in this process so far */
+  long long spmv_bytes;       /* modelled HBM bytes of the SpMV-type launches (process total) */
   int levels_A, levels_S, levels_M;
   int syncs;                  /* host waits on device scalars */
+  long long staged_launches;  /* launches of the staged product kernel (process total) */
 } scr_stats;
 
 /* Fill o with the defaults listed above.  Never fails for non-NULL o. */

@@ -31,7 +31,8 @@ class Opts(C.Structure):
         ("amg_theta", C.c_double), ("amg_max_levels", C.c_int), ("amg_coarse_size", C.c_int),
         ("amg_nu", C.c_int), ("amg_trunc", C.c_double), ("amg_pmax", C.c_int), ("autotune", C.c_int),
         ("amg_smoother", C.c_int), ("amg_degree", C.c_int), ("spmv_group", C.c_int),
-        ("sell", C.c_int),
+        ("sell", C.c_int), ("staged", C.c_int), ("stage_kb", C.c_int), ("stages", C.c_int),
+        ("l2_prefetch", C.c_int),
         ("mm_rtol", C.c_double), ("mm_max_it", C.c_int), ("verbose", C.c_int),
     ]
 
@@ -54,6 +55,7 @@ class Stats(C.Structure):
         ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("mm_setup_ms", C.c_double),
         ("mm_solve_ms", C.c_double), ("kernel_launches", C.c_longlong), ("spmv_bytes", C.c_longlong),
         ("levels_A", C.c_int), ("levels_S", C.c_int), ("levels_M", C.c_int), ("syncs", C.c_int),
+        ("staged_launches", C.c_longlong),
     ]
 
     def as_dict(self) -> dict:

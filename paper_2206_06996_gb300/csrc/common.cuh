@@ -40,8 +40,13 @@ struct DBsr {
   int* rp = nullptr;
   int* col = nullptr;
   T* val = nullptr;
-  int g = 0;                  // lanes per scalar row in products with this matrix (0: heuristic)
+  int g = 0;                  // product kernel code (0: heuristic; see spmv.cu)
   const void* sell = nullptr; // host pointer to a DSell<T> copy used for products (optional)
+  // tile plan of the staged product (spmv_staged.cu): tile t covers the
+  // block rows tiles[t] .. tiles[t+1]-1; a stage holds stage_v bytes of
+  // values and stage_c bytes of indices, enough for any tile
+  const int* tiles = nullptr;
+  int ntiles = 0, stage_v = 0, stage_c = 0, stages = 0;
 };
 
 // Sliced block-ELL copy of a block matrix (see sell.cu): chunks of 32 block
@@ -67,13 +72,17 @@ __host__ __device__ inline long long slab_index(int s, int k, int t, int r, int 
 // repeated set-ups reuse the same blocks without returning to the driver.
 class DeviceArena {
  public:
+  static constexpr size_t kSlack = 64;
   explicit DeviceArena(cudaStream_t s = 0) : stream_(s) {}
   ~DeviceArena() { release(); }
   template <typename T>
   T* alloc(size_t n) {
     void* p = nullptr;
     if (n == 0) n = 1;
-    SCR_CUDA(cudaMallocAsync(&p, n * sizeof(T), stream_));
+    // kSlack bytes past the last element: the staged products copy whole
+    // 16-byte lines with bulk copies, so they may read up to 15 bytes past
+    // the end of a value or index array
+    SCR_CUDA(cudaMallocAsync(&p, n * sizeof(T) + kSlack, stream_));
     ptrs_.push_back(p);
     bytes_ += n * sizeof(T);
     return static_cast<T*>(p);

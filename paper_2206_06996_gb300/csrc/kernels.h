@@ -9,6 +9,7 @@ namespace scr {
 struct LaunchCounter {
   long long launches = 0;
   long long spmv_bytes = 0;
+  long long staged = 0;  // staged product launches
 };
 LaunchCounter& counters();
 
@@ -75,10 +76,28 @@ void build_sell(const DBsr<double>& M, DSell<VT>& S, DeviceArena& a, cudaStream_
 
 // forced kernel code for every product (0: per-matrix choice)
 void set_forced_group(int code);
+// CTAs ahead for the L2 prefetch of the scalar-row products (0: off)
+void set_l2_prefetch(int ctas);
 // time the lane-group widths for products of M with nrhs right-hand sides
 // and store the fastest in M.g; returns the chosen width
 template <typename VT>
 int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s);
+
+// Staged products (spmv_staged.cu): values and indices of tiles of whole
+// block rows are bulk-copied into shared memory several tiles ahead of the
+// lanes.  build_staged_plan computes M's tile plan (stages of stage_kb KiB,
+// `stages` in flight; left empty for small matrices, rows longer than a
+// stage or an unsupported shape); spmv_staged runs the product with G lanes
+// per scalar row and returns false when M has no plan.
+constexpr long long kStagedMinBlocks = 16384;
+bool staged_shape_supported(int br, int bc, int nrhs);
+template <typename VT>
+void build_staged_plan(DBsr<VT>& M, int nrhs, DeviceArena& a, cudaStream_t s, int stage_kb, int stages);
+template <typename VT, typename XT>
+bool spmv_staged(int G, const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const EpiArgs& e, cudaStream_t s);
+// status word of the staged products since the last call (0: none; 1: a
+// stage wait ran out; 2: a tile exceeded its stage), cleared on read
+int staged_status_take(cudaStream_t s);
 
 // y = epilogue([[A, B], [C, D]] x) in FP64 (the outer operator calA)
 void block_op(const DBsr<double>& A, const DBsr<double>& B, const DBsr<double>& C,

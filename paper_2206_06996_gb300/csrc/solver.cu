@@ -110,6 +110,14 @@ static DBsr<float> to_float_copy(const DBsr<double>& M, DeviceArena& a, cudaStre
   return F;
 }
 
+// tile plan for the staged kernel (o.staged) and the timed choice of the
+// product kernel (o.autotune) for products of M with nrhs right-hand sides
+template <typename VT>
+static void tune_product(DBsr<VT>& M, int nrhs, const scr_opts& o, DeviceArena& a, cudaStream_t s) {
+  if (o.staged && !M.tiles) build_staged_plan<VT>(M, nrhs, a, s, o.stage_kb, o.stages);
+  if (o.autotune) autotune_spmv<VT>(M, nrhs, s);
+}
+
 struct Hierarchy {
   int bs = 1, nrhs = 1, nu = 1;
   int smoother = SCR_SMOOTH_CHEB, degree = 3;
@@ -264,21 +272,21 @@ struct Hierarchy {
       cast_d2f(cinv, cinvf, (long long)nc * nc, s);
     }
     // lane-group widths of the products on the two finest levels
-    if (o.autotune) {
+    if (o.autotune || o.staged) {
       for (size_t l = 0; l < lv.size() && l < 2; ++l) {
         Level& L = lv[l];
         if (L.n < 4096) continue;
         if (f32) {
-          if (!(l == 0 && A0f)) autotune_spmv<float>(L.Af, nrhs, s);
+          if (!(l == 0 && A0f)) tune_product<float>(L.Af, nrhs, o, ar, s);
           if (L.P.nbr) {
-            autotune_spmv<float>(L.Pf, nrhs, s);
-            autotune_spmv<float>(L.Rf, nrhs, s);
+            tune_product<float>(L.Pf, nrhs, o, ar, s);
+            tune_product<float>(L.Rf, nrhs, o, ar, s);
           }
         } else {
-          if (l > 0 || A0.g == 0) autotune_spmv<double>(L.A, nrhs, s);
+          if (l > 0 || A0.g == 0) tune_product<double>(L.A, nrhs, o, ar, s);
           if (L.P.nbr) {
-            autotune_spmv<double>(L.P, nrhs, s);
-            autotune_spmv<double>(L.R, nrhs, s);
+            tune_product<double>(L.P, nrhs, o, ar, s);
+            tune_product<double>(L.R, nrhs, o, ar, s);
           }
         }
       }
@@ -669,11 +677,28 @@ DBsr<float> float_copy(const DBsr<double>& M, DeviceArena& a, cudaStream_t s) {
   return F;
 }
 
+// a bounded device-side wait that ran out (the kernel returned early and
+// its outputs are incomplete)
+struct DeviceTimeout : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+
+// status word of the staged products launched on the handle's stream
+static void check_staged(scr_handle h) {
+  if (!h->o.staged) return;
+  const int st = staged_status_take(h->s);
+  if (st == 1) throw DeviceTimeout("a staged product's shared-memory stage did not arrive within its wait limit");
+  if (st == 2) throw std::runtime_error("staged product: a tile exceeded its stage (inconsistent tile plan)");
+}
+
 template <typename F>
 int guarded(F&& f) {
   try {
     f();
     return SCR_OK;
+  } catch (const DeviceTimeout& e) {
+    set_last_error("%s", e.what());
+    return SCR_DEVICE_TIMEOUT;
   } catch (const CudaError& e) {
     set_last_error("CUDA error %s in %s", cudaGetErrorString(e.err), e.where ? e.where : "?");
     cudaGetLastError();
@@ -860,6 +885,10 @@ int scr_default_opts(scr_opts* o) {
   o->amg_smoother = SCR_SMOOTH_CHEB;
   o->amg_degree = 3;
   o->sell = 0;
+  o->staged = 0;
+  o->stage_kb = 16;
+  o->stages = 2;
+  o->l2_prefetch = 192;
   o->mm_rtol = 1e-8;
   o->mm_max_it = 500;
   o->verbose = 0;
@@ -883,9 +912,13 @@ int scr_create(scr_handle* out, const scr_opts* o, void* stream) {
     if (op.amg_smoother != SCR_SMOOTH_L1 && op.amg_smoother != SCR_SMOOTH_CHEB)
       throw std::invalid_argument("unknown smoother");
     if (op.amg_degree < 1 || op.amg_degree > 16) throw std::invalid_argument("Chebyshev degree must lie in [1, 16]");
+    if (op.staged && (op.stage_kb < 4 || op.stage_kb > 96 || op.stages < 2 || op.stages > 4))
+      throw std::invalid_argument("staged products: stage_kb must lie in [4, 96] and stages in [2, 4]");
+    if (op.l2_prefetch < 0) throw std::invalid_argument("l2_prefetch must be >= 0");
     std::unique_ptr<scr_ctx> h(new scr_ctx());
     h->o = op;
     set_forced_group(op.spmv_group);
+    set_l2_prefetch(op.l2_prefetch);
     h->s = static_cast<cudaStream_t>(stream);
     SCR_CUDA(cudaGetDevice(&h->device));
     configure_pool(h->device);
@@ -961,10 +994,8 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
       build_sell<double>(h->Shat, h->Shat_sell, a, s, h->o.sell);
       h->Shat.sell = &h->Shat_sell;
     }
-    if (h->o.autotune) {
-      autotune_spmv<double>(h->A, 1, s);
-      autotune_spmv<double>(h->Shat, 1, s);
-    }
+    tune_product<double>(h->A, 1, h->o, a, s);
+    tune_product<double>(h->Shat, 1, h->o, a, s);
     if (f32) {
       h->Af = float_copy(h->A, a, s);
       h->Bf = float_copy(h->B, a, s);
@@ -974,7 +1005,7 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
         build_sell<float>(h->A, h->Af_sell, a, s, h->o.sell);
         h->Af.sell = &h->Af_sell;
       }
-      if (h->o.autotune) autotune_spmv<float>(h->Af, 1, s);
+      tune_product<float>(h->Af, 1, h->o, a, s);
     }
     if (h->o.verbose)
       fprintf(stderr, "[setup] lane groups: A %d, Shat %d, A(fp32) %d\n", h->A.g, h->Shat.g, h->Af.g);
@@ -1073,6 +1104,7 @@ int scr_solve(scr_handle h, const double* b, double* x, int dev) {
     status = solve_impl(h, bd, xd, h->o.rtol);
     if (!dev) SCR_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
     SCR_CUDA(cudaStreamSynchronize(h->s));
+    check_staged(h);
     h->stats.solve_ms = ms_since(t0);
   });
   if (rc != SCR_OK) return rc;
@@ -1267,6 +1299,7 @@ int scr_solve_batch(scr_handle h, const double* const* b, double* const* x, int 
         SCR_CUDA(cudaMemcpyAsync(x[i] + v3, h->xvec + NV3 + h->b_po[i], sizeof(double) * h->b_np[i], kout, h->s));
     }
     SCR_CUDA(cudaStreamSynchronize(h->s));
+    check_staged(h);
     h->stats.solve_ms = ms_since(t0);
   });
   if (rc != SCR_OK) return rc;
@@ -1298,6 +1331,7 @@ int scr_get_stats(scr_handle h, scr_stats* st) {
   *st = h->stats;
   st->kernel_launches = counters().launches;
   st->spmv_bytes = counters().spmv_bytes;
+  st->staged_launches = counters().staged;
   st->levels_M = h->hM.n_levels();
   return SCR_OK;
 }
@@ -1332,7 +1366,7 @@ int mm_setup(scr_handle h, const scr_bsr* L, int dev) {
       build_sell<double>(h->L, h->L_sell, *h->mmats, s, o.sell);
       h->L.sell = &h->L_sell;
     }
-    if (o.autotune) autotune_spmv<double>(h->L, 3, s);
+    tune_product<double>(h->L, 3, o, *h->mmats, s);
     h->hM.build(h->L, 1, 3, o, false, s);
     h->mwork.reset(new DeviceArena(s));
     DeviceArena& w = *h->mwork;
@@ -1424,6 +1458,7 @@ int mm_solve(scr_handle h, const double* g, double* u, int dev) {
     h->stats.vcycles_M = h->hM.vcycles;
     if (!dev) SCR_CUDA(cudaMemcpyAsync(u, ud, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
     SCR_CUDA(cudaStreamSynchronize(h->s));
+    check_staged(h);
     h->stats.mm_solve_ms = ms_since(t0);
   });
   if (rc != SCR_OK) return rc;
@@ -1447,6 +1482,7 @@ int scr_apply_op(scr_handle h, const double* x, double* y) {
   return guarded([&] {
     block_op(h->A, h->B, h->C, h->D, x, y, nullptr, false, h->s);
     SCR_CUDA(cudaStreamSynchronize(h->s));
+    check_staged(h);
   });
 }
 
@@ -1456,6 +1492,7 @@ int scr_apply_pc(scr_handle h, const double* r, double* y) {
     reset_solve_stats(h);
     apply_pc_any(h, r, y);
     SCR_CUDA(cudaStreamSynchronize(h->s));
+    check_staged(h);
   });
 }
 
@@ -1473,6 +1510,7 @@ int scr_apply_schur(scr_handle h, const double* xp, double* yp) {
       apply_S<double>(h, v, xp, yp);
     }
     SCR_CUDA(cudaStreamSynchronize(h->s));
+    check_staged(h);
   });
 }
 
@@ -1504,6 +1542,7 @@ int scr_amg_apply(scr_handle h, int which, const double* b, double* x) {
       H->apply<double>(b, x, h->s);
     }
     SCR_CUDA(cudaStreamSynchronize(h->s));
+    check_staged(h);
   });
 }
 

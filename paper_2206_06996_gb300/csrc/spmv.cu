@@ -14,6 +14,7 @@
 #include <mutex>
 #include <tuple>
 
+#include "epilogue.cuh"
 #include "kernels.h"
 
 #ifndef SCR_SPMV_BATCH
@@ -132,47 +133,6 @@ void slab_to_float(const double* in, float* out, long long n, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------ SpMV
-template <typename XT, Epi E>
-struct Epilogue {
-  XT* y;
-  const XT* z;
-  const XT* xs;
-  const XT* dinv;
-  const XT* xin;  // the product's source vector (ChebStep: the direction)
-  XT* r;
-  XT* dout;
-  XT* xsol;
-  XT alpha, beta;
-  template <typename AT>
-  __device__ __forceinline__ void operator()(long long gi, long long o, AT acc) const {
-    if constexpr (E == Epi::Set) {
-      y[gi] = (XT)acc;
-    } else if constexpr (E == Epi::Axpby) {
-      XT v = alpha * (XT)acc;
-      if (z) v += beta * z[gi];
-      y[gi] = v;
-    } else if constexpr (E == Epi::Resid) {
-      y[gi] = z[gi] - (XT)acc;
-    } else if constexpr (E == Epi::Jacobi) {
-      y[gi] = xs[gi] + (z[gi] - (XT)acc) * dinv[o];
-    } else if constexpr (E == Epi::ScaledSub) {
-      y[gi] = z[gi] - (XT)acc * dinv[o];
-    } else if constexpr (E == Epi::ChebFirst) {
-      const XT ri = (z[gi] - (XT)acc) * dinv[o];
-      const XT di = alpha * ri;
-      r[gi] = ri;
-      dout[gi] = di;
-      y[gi] = xs[gi] + di;
-    } else {
-      const XT ri = r[gi] - (XT)acc * dinv[o];
-      const XT di = alpha * xin[gi] + beta * ri;
-      r[gi] = ri;
-      dout[gi] = di;
-      xsol[gi] += di;
-    }
-  }
-};
-
 // accumulate one scalar row r of block row i of M into acc[h]; the lanes of
 // a G-group take the row's blocks in turn (BC values each, contiguous in the
 // slab layout) so every stored value costs one multiply-add
@@ -219,14 +179,39 @@ __device__ __forceinline__ void scalar_row_accum(const int* __restrict__ rp, con
   }
 }
 
+// L2 prefetch (cp.async.bulk.prefetch.L2) of the stored values and column
+// indices that the CTA with index cta (256 threads, 256 / G scalar rows)
+// will read.  The range is cut to whole 16-byte lines inside it: the first
+// line may start up to 15 bytes before the range (the same line as a valid
+// byte), the last partial line is left out, so no line outside the arrays
+// is named.
+template <int BR, int BC, int G, typename VT>
+__device__ __forceinline__ void l2_prefetch_rows(const int* __restrict__ rp, const int* __restrict__ col,
+                                                 const VT* __restrict__ val, int nbr, long long cta) {
+  const long long nrows = (long long)nbr * BR;
+  const long long o0 = cta * (256 / G);
+  if (o0 >= nrows) return;
+  const long long o1 = o0 + 256 / G < nrows ? o0 + 256 / G : nrows;
+  const long long b0 = __ldg(rp + o0 / BR), b1 = __ldg(rp + (o1 - 1) / BR + 1);
+  const unsigned long long v0 = __cvta_generic_to_global(val + b0 * BR * BC) & ~15ULL;
+  const unsigned long long v1 = __cvta_generic_to_global(val + b1 * BR * BC) & ~15ULL;
+  const unsigned long long c0 = __cvta_generic_to_global(col + b0) & ~15ULL;
+  const unsigned long long c1 = __cvta_generic_to_global(col + b1) & ~15ULL;
+  if (v1 > v0)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(v0), "r"((unsigned)(v1 - v0)) : "memory");
+  if (c1 > c0)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(c0), "r"((unsigned)(c1 - c0)) : "memory");
+}
+
 template <int BR, int BC, int NRHS, int G, typename VT, typename XT, typename AT, Epi E>
 __global__ void __launch_bounds__(256, SCR_SPMV_MINBLOCKS) k_spmv(int nbr, const int* __restrict__ rp,
                                                                  const int* __restrict__ col,
                                               const VT* __restrict__ val, const XT* __restrict__ x,
-                                              Epilogue<XT, E> epi) {
+                                              Epilogue<XT, E> epi, int pf) {
   const long long o = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;  // scalar row
   const int lane = threadIdx.x % G;
   const long long nrows = (long long)nbr * BR;
+  if (pf > 0 && threadIdx.x == 0) l2_prefetch_rows<BR, BC, G, VT>(rp, col, val, nbr, blockIdx.x + (long long)pf);
   const bool active = o < nrows;  // inactive lanes still join the shuffles
   AT acc[NRHS];
 #pragma unroll
@@ -352,19 +337,16 @@ __global__ void __launch_bounds__(256) k_sell_spmv(DSell<VT> S, const XT* __rest
   }
 }
 
+// CTAs ahead for the L2 prefetch of the scalar-row kernel (0: off); set
+// from the options at scr_create.  Measured on the 616k-node tube: 128 to
+// 384 CTAs ahead gave the same level-0 product times (FP32 122 -> 110 us,
+// FP64 241 -> 229 us); 1536 and more were slower than none.
+static int g_l2_prefetch = 192;
+void set_l2_prefetch(int ctas) { g_l2_prefetch = ctas; }
+
 template <int BR, int BC, int NRHS, int G, typename VT, typename XT, typename AT, Epi E>
 static void launch_spmv_g(const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& e, cudaStream_t s) {
-  Epilogue<XT, E> epi;
-  epi.y = y;
-  epi.z = static_cast<const XT*>(e.z);
-  epi.xs = static_cast<const XT*>(e.xs);
-  epi.dinv = static_cast<const XT*>(e.dinv);
-  epi.xin = x;
-  epi.r = static_cast<XT*>(e.r);
-  epi.dout = static_cast<XT*>(e.dout);
-  epi.xsol = static_cast<XT*>(e.xsol);
-  epi.alpha = (XT)e.alpha;
-  epi.beta = (XT)e.beta;
+  const Epilogue<XT, E> epi = make_epilogue<XT, E>(x, y, e);
   const int blk = 256;
   if (M.sell) {
     const DSell<VT>& S = *static_cast<const DSell<VT>*>(M.sell);
@@ -376,7 +358,8 @@ static void launch_spmv_g(const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& 
                                                                                      x, epi);
   } else {
     const long long threads = (long long)M.nbr * BR * G;
-    k_spmv<BR, BC, NRHS, G, VT, XT, AT, E><<<ceil_div(threads, blk), blk, 0, s>>>(M.nbr, M.rp, M.col, M.val, x, epi);
+    k_spmv<BR, BC, NRHS, G, VT, XT, AT, E><<<ceil_div(threads, blk), blk, 0, s>>>(M.nbr, M.rp, M.col, M.val, x, epi,
+                                                                                  g_l2_prefetch);
   }
   SCR_LAUNCH();
 }
@@ -404,8 +387,10 @@ static void launch_spmv_e(const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& 
 
 // lanes per scalar row: FP64 keeps groups narrow (FP64 adds of the
 // reduction compete with the products), FP32 widens them for coalescing
-// M.g: lanes per block row (1..16, block-row kernel for BR > 1) or 100 +
-// lanes per scalar row (scalar-row kernel); 0 selects by row length
+// M.g: lanes per block row (1..16, block-row kernel for BR > 1), 100 +
+// lanes per scalar row (scalar-row kernel) or 200 + lanes per scalar row
+// (staged kernel, spmv_staged.cu, when M has a tile plan); 0 selects by row
+// length
 static int g_forced = 0;
 void set_forced_group(int code) { g_forced = code; }
 
@@ -417,6 +402,7 @@ static int code_of(const DBsr<VT>& M) {
 template <typename VT>
 static int pick_group(const DBsr<VT>& M) {
   const int g = code_of(M);
+  if (g >= 200) return g - 200;
   if (g > 0) return g >= 100 ? g - 100 : g;
   // measured on the 616k-node tube: FP64 3x3 rows are fastest with 2 lanes
   // per scalar row (the FP64 pipe binds), FP32 with 4 (coalescing binds)
@@ -452,7 +438,8 @@ void spmv(const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const EpiArgs& e, cud
   if (M.nbr == 0) return;
   const int G = M.sell ? 1 : pick_group(M);
   const int pidx = prof_start(0, M.val, s);
-  spmv_launch<VT, XT>(G, M, x, y, nrhs, e, s);
+  if (!(code_of(M) >= 200 && !M.sell && spmv_staged<VT, XT>(G, M, x, y, nrhs, e, s)))
+    spmv_launch<VT, XT>(G, M, x, y, nrhs, e, s);
   counters().launches++;
   {
     // algorithmic bytes: stored values + column indices + row pointers once,
@@ -511,20 +498,30 @@ int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s) {
   cudaEvent_t e0, e1;
   SCR_CUDA(cudaEventCreate(&e0));
   SCR_CUDA(cudaEventCreate(&e1));
-  // the scalar-row kernel with 1, 2, 4 or 8 lanes (the block-row and
-  // sliced-ELL variants measured slower on the tube operators)
-  const int cands[] = {1, 2, 4, 8};
-  const int ncand = 4;
+  // the scalar-row kernel with 1, 2, 4 or 8 lanes and, when M has a tile
+  // plan, the staged kernel with 2, 4 or 8 (the block-row and sliced-ELL
+  // variants measured slower on the tube operators)
+  int cands[8] = {101, 102, 104, 108};
+  int ncand = 4;
+  if (M.tiles && staged_shape_supported(M.br, M.bc, nrhs)) {
+    cands[ncand++] = 202;
+    cands[ncand++] = 204;
+    cands[ncand++] = 208;
+  }
   float best = 1e30f;
   int bestg = M.g;
   const int saved = M.g;
   for (int q = 0; q < ncand; ++q) {
-    const int code = 100 + cands[q];
+    const int code = cands[q];
     M.g = code;
     const int G = pick_group(M);
-    spmv_launch<VT, XT>(G, M, x, y, nrhs, EpiArgs(), s);  // warm-up
+    auto run = [&] {
+      if (!(code >= 200 && spmv_staged<VT, XT>(G, M, x, y, nrhs, EpiArgs(), s)))
+        spmv_launch<VT, XT>(G, M, x, y, nrhs, EpiArgs(), s);
+    };
+    run();  // warm-up
     SCR_CUDA(cudaEventRecord(e0, s));
-    for (int r = 0; r < 5; ++r) spmv_launch<VT, XT>(G, M, x, y, nrhs, EpiArgs(), s);
+    for (int r = 0; r < 5; ++r) run();
     SCR_CUDA(cudaEventRecord(e1, s));
     SCR_CUDA(cudaEventSynchronize(e1));
     float ms = 0;

@@ -214,6 +214,84 @@ def test_sliced_ell_products_match_slab_products(small, precision):
     del rng
 
 
+def _three_vcycles(sol, small):
+    out = []
+    for which, n in ((pkg.SCR_HIER_A, 3 * small.n_v), (pkg.SCR_HIER_SHAT, small.n_p),
+                     (pkg.SCR_HIER_MESH, 3 * small.L.nb_rows)):
+        b = _dev(np.random.default_rng(which + 11).standard_normal(n))
+        out.append(sol.amg_apply(which, b).cpu().numpy())
+    return out
+
+
+@pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
+@pytest.mark.parametrize("G", [1, 2, 4, 8])
+def test_staged_products_equal_scalar_row_products(small, precision, G):
+    """The staged kernel (tiles of values and indices bulk-copied into shared
+    memory ahead of the lanes) adds the same terms in the same order as the
+    scalar-row kernel with the same lane count, so the V-cycles of A, Shat
+    and L (3 right-hand sides) agree bit for bit: with 8 KiB stages (hundreds
+    of tiles, a ragged last tile), 2 and 4 stages in flight, and 32 KiB."""
+    ref = None
+    for code, kb, nst in ((100 + G, 32, 3), (200 + G, 8, 2), (200 + G, 8, 4), (200 + G, 32, 3)):
+        with pkg.BlockSolver(spmv_group=code, autotune=0, staged=1, stage_kb=kb, stages=nst,
+                             precision=precision) as sol:
+            sol.setup(small.A, small.B, small.C, small.D)
+            sol.mesh_setup(small.L)
+            before = sol.stats()["staged_launches"]
+            out = _three_vcycles(sol, small)
+            staged = sol.stats()["staged_launches"] - before
+        if code >= 200:
+            assert staged > 0
+        if ref is None:
+            ref = out
+            continue
+        for a, b in zip(ref, out):
+            np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
+def test_block_solve_with_staged_products_matches_direct(small, small_direct, precision):
+    op = BlockOperator.from_system(small)
+    with pkg.BlockSolver(precision=precision, spmv_group=204, autotune=0, staged=1, stage_kb=16) as sol:
+        sol.setup(small.A, small.B, small.C, small.D)
+        x = sol.solve(small.b.copy())
+        st = sol.stats()
+    assert st["staged_launches"] > 0
+    assert st["rel_res"] <= 1e-8 and rel_residual(op, x, small.b) <= 1e-8
+    assert _rel(x, small_direct) <= 1e-6
+
+
+@pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
+def test_l2_prefetch_changes_no_result(small, precision):
+    """The bulk L2 prefetch of the scalar-row products only moves data into
+    L2: V-cycles are bit-identical with it off, 1 CTA ahead and 192 ahead
+    (the last CTAs of every product prefetch nothing past the arrays)."""
+    ref = None
+    for pf in (0, 1, 192):
+        with pkg.BlockSolver(l2_prefetch=pf, autotune=0, spmv_group=102, precision=precision) as sol:
+            sol.setup(small.A, small.B, small.C, small.D)
+            sol.mesh_setup(small.L)
+            out = _three_vcycles(sol, small)
+        if ref is None:
+            ref = out
+            continue
+        for a, b in zip(ref, out):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_staged_options_are_validated(small):
+    for bad in ({"stage_kb": 2}, {"stage_kb": 200}, {"stages": 1}, {"stages": 5}):
+        with pytest.raises(pkg.ScrError):
+            pkg.BlockSolver(staged=1, **bad)
+    with pytest.raises(pkg.ScrError):
+        pkg.BlockSolver(l2_prefetch=-1)
+    with pkg.BlockSolver(staged=0, spmv_group=202) as sol:  # no plans: the plain kernel runs
+        sol.setup(small.A, small.B, small.C, small.D)
+        before = sol.stats()["staged_launches"]
+        sol.solve(small.b.copy())
+        assert sol.stats()["staged_launches"] == before
+
+
 # ---------------------------------------------------------------- Alg. 1 / 2
 def test_algorithm2_tight_inner_equals_schur(mini):
     op = BlockOperator.from_system(mini)
