@@ -112,6 +112,10 @@ typedef struct {
   int stages;         /* staged kernel: tiles in flight per CTA, 2..4, default 2 */
   int l2_prefetch;    /* scalar-row products: each CTA prefetches into L2 the values and indices of
                          the CTA this many indices ahead (bulk L2 prefetch); 0 off; default 192 */
+  int amg_coarse_bf16;/* mixed form only: 1 (default) stores the values of the coarse AMG levels
+                         (operators and transfers of levels >= 1) in BF16, rounded to nearest even
+                         from the FP32 copy; products still use FP32 vectors and FP32 sums;
+                         0 keeps them in FP32 */
   double mm_rtol;     /* mesh CG relative residual, 1e-8 */
   int mm_max_it;      /* mesh CG iteration cap, 500 */
   int verbose;        /* 0 quiet */

@@ -18,6 +18,8 @@ Contents (each function cites the passage of the paper it restates):
 * ``amg``     - a plain smoothed-aggregation AMG (strength graph,
                 greedy aggregation, tentative and smoothed prolongators,
                 Galerkin products) and the V-cycle with l1-Jacobi smoothing.
+* ``precision`` - the value an FP64 number takes when stored in binary32 or
+                bfloat16 (the storage formats of the mixed-precision form).
 * ``scr``     - Algorithm 1 (SCR preconditioner action) and Algorithm 2
                 (matrix-free Schur complement action) of App. B, the outer
                 FGMRES solve of Sec. 5.2.1 and the mesh-motion AMG-CG of

@@ -47,6 +47,9 @@ struct DBsr {
   // values and stage_c bytes of indices, enough for any tile
   const int* tiles = nullptr;
   int ntiles = 0, stage_v = 0, stage_c = 0, stages = 0;
+  // BF16 copy of val (same slab layout): when set, FP32 products read these
+  // values instead (coarse AMG levels of the mixed-precision form)
+  const void* hval = nullptr;
 };
 
 // Sliced block-ELL copy of a block matrix (see sell.cu): chunks of 32 block

@@ -41,6 +41,8 @@ void from_slab_f(const int* rp, const float* slab_val, double* std_val, int nbr,
                  long long nnzb, cudaStream_t s);
 // slab double -> slab float
 void slab_to_float(const double* in, float* out, long long n, cudaStream_t s);
+// slab float -> slab BF16 (round to nearest even); out holds n __nv_bfloat16
+void slab_to_bf16(const float* in, void* out, long long n, cudaStream_t s);
 
 // --------------------------------------------------------------- SpMV
 // Epilogues applied to the row sums acc of M x (scalar output index o,

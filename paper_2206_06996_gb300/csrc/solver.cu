@@ -110,6 +110,15 @@ static DBsr<float> to_float_copy(const DBsr<double>& M, DeviceArena& a, cudaStre
   return F;
 }
 
+// BF16 copy of an FP32 matrix's values, used by its products from now on
+static void add_bf16_copy(DBsr<float>& F, DeviceArena& a, cudaStream_t s) {
+  if (F.nnzb == 0) return;
+  const long long n = F.nnzb * F.br * F.bc;
+  uint16_t* h = a.alloc<uint16_t>(n + 1);
+  slab_to_bf16(F.val, h, n, s);
+  F.hval = h;
+}
+
 // tile plan for the staged kernel (o.staged) and the timed choice of the
 // product kernel (o.autotune) for products of M with nrhs right-hand sides
 template <typename VT>
@@ -258,6 +267,13 @@ struct Hierarchy {
         if (L.P.nbr) {
           L.Pf = to_float_copy(L.P, ar, s);
           L.Rf = to_float_copy(L.R, ar, s);
+        }
+        // coarse levels: products read BF16 values (FP32 vectors and sums);
+        // the coarsest operator is only used through its dense inverse
+        if (o.amg_coarse_bf16 && l >= 1 && l + 1 < lv.size()) {
+          add_bf16_copy(L.Af, ar, s);
+          add_bf16_copy(L.Pf, ar, s);
+          add_bf16_copy(L.Rf, ar, s);
         }
         L.dinvf = ar.alloc<float>(L.n + 1);
         cast_d2f(L.dinv, L.dinvf, L.n, s);
@@ -889,6 +905,7 @@ int scr_default_opts(scr_opts* o) {
   o->stage_kb = 16;
   o->stages = 2;
   o->l2_prefetch = 192;
+  o->amg_coarse_bf16 = 1;
   o->mm_rtol = 1e-8;
   o->mm_max_it = 500;
   o->verbose = 0;
@@ -915,6 +932,7 @@ int scr_create(scr_handle* out, const scr_opts* o, void* stream) {
     if (op.staged && (op.stage_kb < 4 || op.stage_kb > 96 || op.stages < 2 || op.stages > 4))
       throw std::invalid_argument("staged products: stage_kb must lie in [4, 96] and stages in [2, 4]");
     if (op.l2_prefetch < 0) throw std::invalid_argument("l2_prefetch must be >= 0");
+    if (op.amg_coarse_bf16 != 0 && op.amg_coarse_bf16 != 1) throw std::invalid_argument("amg_coarse_bf16 must be 0 or 1");
     std::unique_ptr<scr_ctx> h(new scr_ctx());
     h->o = op;
     set_forced_group(op.spmv_group);

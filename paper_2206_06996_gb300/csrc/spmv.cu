@@ -8,11 +8,14 @@
 // (about two FP64 FMAs per SM clock) is the binding resource of an FP64
 // SpMV, and a wider group would spend more FP64 adds on the cross-lane
 // reduction than on the product itself.
+#include <cuda_bf16.h>
+
 #include <cstdarg>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 
 #include "epilogue.cuh"
 #include "kernels.h"
@@ -125,6 +128,19 @@ __global__ void k_d2f(const double* __restrict__ x, float* __restrict__ y, long 
   long long st = (long long)gridDim.x * blockDim.x;
   for (; i < n; i += st) y[i] = (float)x[i];
 }
+// FP32 -> BF16, round to nearest even (__float2bfloat16_rn)
+__global__ void k_f2bf(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long st = (long long)gridDim.x * blockDim.x;
+  for (; i < n; i += st) y[i] = __float2bfloat16_rn(x[i]);
+}
+void slab_to_bf16(const float* in, void* out, long long n, cudaStream_t s) {
+  if (n == 0) return;
+  k_f2bf<<<std::min<long long>(ceil_div(n, 256), 4 * 1024), 256, 0, s>>>(in, static_cast<__nv_bfloat16*>(out), n);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
 void slab_to_float(const double* in, float* out, long long n, cudaStream_t s) {
   if (n == 0) return;
   k_d2f<<<std::min<long long>(ceil_div(n, 256), 4 * 1024), 256, 0, s>>>(in, out, n);
@@ -348,15 +364,21 @@ template <int BR, int BC, int NRHS, int G, typename VT, typename XT, typename AT
 static void launch_spmv_g(const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& e, cudaStream_t s) {
   const Epilogue<XT, E> epi = make_epilogue<XT, E>(x, y, e);
   const int blk = 256;
-  if (M.sell) {
-    const DSell<VT>& S = *static_cast<const DSell<VT>*>(M.sell);
-    const long long threads = (long long)S.nchunk * kChunk;
-    k_sell_spmv<BR, BC, NRHS, VT, XT, E><<<ceil_div(threads, blk), blk, 0, s>>>(S, x, epi);
-  } else if (BR > 1 && code_of(M) > 0 && code_of(M) < 100) {
-    const long long threads = (long long)M.nbr * G;
-    k_spmv_brow<BR, BC, NRHS, G, VT, XT, AT, E><<<ceil_div(threads, blk), blk, 0, s>>>(M.nbr, M.rp, M.col, M.val,
-                                                                                     x, epi);
-  } else {
+  bool done = false;
+  if constexpr (sizeof(VT) >= 4) {  // BF16 values: scalar-row kernel only
+    if (M.sell) {
+      const DSell<VT>& S = *static_cast<const DSell<VT>*>(M.sell);
+      const long long threads = (long long)S.nchunk * kChunk;
+      k_sell_spmv<BR, BC, NRHS, VT, XT, E><<<ceil_div(threads, blk), blk, 0, s>>>(S, x, epi);
+      done = true;
+    } else if (BR > 1 && code_of(M) > 0 && code_of(M) < 100) {
+      const long long threads = (long long)M.nbr * G;
+      k_spmv_brow<BR, BC, NRHS, G, VT, XT, AT, E><<<ceil_div(threads, blk), blk, 0, s>>>(M.nbr, M.rp, M.col,
+                                                                                       M.val, x, epi);
+      done = true;
+    }
+  }
+  if (!done) {
     const long long threads = (long long)M.nbr * BR * G;
     k_spmv<BR, BC, NRHS, G, VT, XT, AT, E><<<ceil_div(threads, blk), blk, 0, s>>>(M.nbr, M.rp, M.col, M.val, x, epi,
                                                                                   g_l2_prefetch);
@@ -433,20 +455,44 @@ static void spmv_launch(int G, const DBsr<VT>& M, const XT* x, XT* y, int nrhs, 
   else throw CudaError{cudaErrorInvalidValue, "spmv: unsupported block shape"};
 }
 
+// the product with the values M holds: its BF16 copy when it has one (FP32
+// vectors, FP32 sums), else val
+template <typename VT, typename XT>
+static void product(int G, const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const EpiArgs& e, cudaStream_t s) {
+  if constexpr (std::is_same<VT, float>::value) {
+    if (M.hval) {
+      DBsr<__nv_bfloat16> H;
+      H.nbr = M.nbr;
+      H.nbc = M.nbc;
+      H.br = M.br;
+      H.bc = M.bc;
+      H.nnzb = M.nnzb;
+      H.rp = M.rp;
+      H.col = M.col;
+      H.val = static_cast<__nv_bfloat16*>(const_cast<void*>(M.hval));
+      H.g = M.g;
+      spmv_launch<__nv_bfloat16, XT>(G, H, x, y, nrhs, e, s);
+      return;
+    }
+  }
+  if (!(code_of(M) >= 200 && !M.sell && spmv_staged<VT, XT>(G, M, x, y, nrhs, e, s)))
+    spmv_launch<VT, XT>(G, M, x, y, nrhs, e, s);
+}
+
 template <typename VT, typename XT>
 void spmv(const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const EpiArgs& e, cudaStream_t s) {
   if (M.nbr == 0) return;
   const int G = M.sell ? 1 : pick_group(M);
   const int pidx = prof_start(0, M.val, s);
-  if (!(code_of(M) >= 200 && !M.sell && spmv_staged<VT, XT>(G, M, x, y, nrhs, e, s)))
-    spmv_launch<VT, XT>(G, M, x, y, nrhs, e, s);
+  product<VT, XT>(G, M, x, y, nrhs, e, s);
   counters().launches++;
   {
     // algorithmic bytes: stored values + column indices + row pointers once,
     // the source vector once, the result written once, plus what the
     // epilogue reads (z, the current iterate, the inverse diagonal)
     const double nrow = (double)M.nbr * M.br;
-    double b = (double)M.nnzb * (M.br * M.bc * sizeof(VT) + sizeof(int)) + (M.nbr + 1.0) * sizeof(int) +
+    const double vsz = M.hval ? 2.0 : (double)sizeof(VT);
+    double b = (double)M.nnzb * (M.br * M.bc * vsz + sizeof(int)) + (M.nbr + 1.0) * sizeof(int) +
                (double)M.nbc * M.bc * nrhs * sizeof(XT) + nrow * nrhs * sizeof(XT);
     if (e.kind == Epi::Resid || (e.kind == Epi::Axpby && e.z)) b += nrow * nrhs * sizeof(XT);
     if (e.kind == Epi::Jacobi) b += 2.0 * nrow * nrhs * sizeof(XT) + nrow * sizeof(XT);
@@ -515,10 +561,7 @@ int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s) {
     const int code = cands[q];
     M.g = code;
     const int G = pick_group(M);
-    auto run = [&] {
-      if (!(code >= 200 && spmv_staged<VT, XT>(G, M, x, y, nrhs, EpiArgs(), s)))
-        spmv_launch<VT, XT>(G, M, x, y, nrhs, EpiArgs(), s);
-    };
+    auto run = [&] { product<VT, XT>(G, M, x, y, nrhs, EpiArgs(), s); };
     run();  // warm-up
     SCR_CUDA(cudaEventRecord(e0, s));
     for (int r = 0; r < 5; ++r) run();

@@ -191,6 +191,51 @@ def test_vcycle_matches_oracle_on_exported_hierarchy(small, which, bs, nrhs, smo
     assert _rel(x, ref) < 1e-11
 
 
+def _round_csr(M, rnd):
+    M = sp.csr_matrix(M, copy=True)
+    M.data = rnd(M.data)
+    return M
+
+
+@pytest.mark.parametrize("which,bs", [(pkg.SCR_HIER_A, 3), (pkg.SCR_HIER_SHAT, 1)])
+def test_mixed_vcycle_with_bf16_coarse_levels_matches_oracle(small, which, bs):
+    """Mixed form: level 0 stored in FP32, the operators and transfers of the
+    coarser levels in BF16 (FP32 vectors and sums).  The oracle V-cycle with
+    its matrices rounded the same way (oracle.precision) agrees to FP32
+    rounding of the vectors; the unrounded FP64 V-cycle is much farther off,
+    so the BF16 values are the ones the GPU used."""
+    from oracle import precision
+    with pkg.BlockSolver(precision=pkg.SCR_MIXED) as sol:
+        sol.setup(small.A, small.B, small.C, small.D)
+        nl = sol.amg_levels(which)
+        assert nl >= 3
+        As = [to_csr(sol.export(which, l, pkg.SCR_EXPORT_OPERATOR)) for l in range(nl)]
+        Ps = [to_csr(sol.export(which, l, pkg.SCR_EXPORT_PROLONGATOR)) for l in range(nl - 1)]
+        b = np.random.default_rng(12).standard_normal(As[0].shape[0])
+        x = sol.amg_apply(which, _dev(b)).cpu().numpy()
+    H = amg.hierarchy_from_matrices(As, Ps, bs, 1, 1, "cheb", 3)
+    exact = amg.vcycle(H, b)
+    for l, lev in enumerate(H.levels[:-1]):
+        rnd = precision.round_f32 if l == 0 else precision.round_bf16
+        lev.A = _round_csr(lev.A, rnd)
+        lev.P = _round_csr(lev.P, rnd)
+        lev.R = _round_csr(lev.R, rnd)
+    ref = amg.vcycle(H, b)
+    err = _rel(x, ref)
+    assert err < 1e-5
+    assert _rel(x, exact) > 10 * err
+
+
+def test_mixed_solve_with_fp32_coarse_levels(small, small_direct):
+    op = BlockOperator.from_system(small)
+    with pkg.BlockSolver(precision=pkg.SCR_MIXED, amg_coarse_bf16=0) as sol:
+        sol.setup(small.A, small.B, small.C, small.D)
+        x = sol.solve(small.b.copy())
+    assert rel_residual(op, x, small.b) <= 1e-8 and _rel(x, small_direct) <= 1e-6
+    with pytest.raises(pkg.ScrError):
+        pkg.BlockSolver(amg_coarse_bf16=2)
+
+
 @pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
 def test_sliced_ell_products_match_slab_products(small, precision):
     """The sliced block-ELL copies of A, Shat and L give the same V-cycles as

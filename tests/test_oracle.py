@@ -394,3 +394,26 @@ def test_mesh_cg_matches_direct(mini_system):
     assert info.converged
     ud = direct.solve_mesh(mini_system)
     assert np.linalg.norm(u - ud) <= 1e-9 * np.linalg.norm(ud)
+
+
+# ---------------------------------------------------------------- storage formats
+def test_bf16_rounding_special_values():
+    from oracle.precision import round_bf16
+    # 1 + 2^-8 lies halfway between 1 and 1 + 2^-7: ties go to the even mantissa (1)
+    # 1 + 3 * 2^-8 lies halfway between 1 + 2^-7 and 1 + 2^-6: even is 1 + 2^-6
+    x = np.array([1.0, 1.0 + 2.0**-8, 1.0 + 3 * 2.0**-8, -2.5, 0.0, 1.0 + 2.0**-9, 65280.0 + 128.0])
+    want = np.array([1.0, 1.0, 1.0 + 2.0**-6, -2.5, 0.0, 1.0, 65536.0])
+    np.testing.assert_array_equal(round_bf16(x), want)
+
+
+def test_bf16_rounding_matches_torch_and_error_bound():
+    """Against an independent implementation (PyTorch's binary32 -> bfloat16
+    cast, round to nearest even) and the format's error bound 2^-8."""
+    torch = pytest.importorskip("torch")
+    from oracle.precision import round_bf16, round_f32
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(20000) * np.exp(rng.uniform(-20, 20, 20000))
+    ref = torch.tensor(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(round_bf16(x), ref)
+    assert np.all(np.abs(round_bf16(x) - x) <= 2.0**-8 * np.abs(x) * (1 + 2.0**-20))
+    assert np.all(np.abs(round_f32(x) - x) <= 2.0**-24 * np.abs(x))
