@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--skip-mixed", action="store_true")
+    ap.add_argument("--tune-file", default=None,
+                    help="autotuner decisions: loaded before the first set-up when the file exists, "
+                         "written after the run otherwise (replays one run's kernel choices in another, "
+                         "e.g. under a profiler whose instrumentation distorts the autotuner's timings)")
     ap.add_argument("--batched", action="store_true",
                     help="also time the 64-tube batched form (mixed, one block-diagonal solve) against the "
                          "same 64 tubes solved one by one in FP64")
@@ -226,6 +230,9 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     pkg.load_library()
+    tune_loaded = bool(args.tune_file) and os.path.exists(args.tune_file)
+    if tune_loaded:
+        pkg.tune_load(args.tune_file)
     t_in = time.perf_counter()
     s = F.tube_system(args.workload)
     t_in = time.perf_counter() - t_in
@@ -415,7 +422,8 @@ def main():
         "config": {"workload": f"{args.workload}: straight tube 96x(11+5)x400, {s.n_v} nodes, {s.n} unknowns, "
                                f"{s.L.nb_rows} mesh nodes", "precision": args.precision,
                    "step": "scr_setup + scr_solve + mm_setup + mm_solve", "l2": "inputs > L2 (no flush)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "autotune": "decisions loaded from --tune-file" if tune_loaded else "timed at set-up"},
         "rel_res": rel_res, "outer_iters": st["outer_iters"], "inner_iters": st["a_iters"] + st["s_iters"] + st["i_iters"],
         "mesh_iters": st["mm_iters"], "setup_ms": st["setup_ms"], "solve_ms": st["solve_ms"],
         "mm_setup_ms": st["mm_setup_ms"], "mm_solve_ms": st["mm_solve_ms"],
@@ -423,6 +431,8 @@ def main():
         "batched": batched,
         "clocks": clocks, "inputs_build_s": t_in,
     }
+    if args.tune_file and not tune_loaded and rank == 0:
+        pkg.tune_save(args.tune_file)
     print(json.dumps(line))
 
 

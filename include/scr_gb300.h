@@ -265,6 +265,19 @@ typedef struct {
 int scr_profile_begin(scr_handle h, int kernel_class, int capacity);
 int scr_profile_end(scr_handle h, scr_kprof* out);
 
+/* The autotuner's kernel choices (scr_opts.autotune) live in a process-wide
+   cache keyed by block shape, block rows and columns, stored blocks, value
+   precision and right-hand sides.  scr_tune_save writes every cached
+   decision to a text file, one per line; scr_tune_load adds the decisions of
+   such a file to the cache for the current device, so later set-ups of
+   matrices with those keys skip the timing and use the stored kernels.  Use:
+   reproduce one run's choices in another, e.g. under a profiler, whose
+   instrumentation distorts the timings the autotuner relies on.  The paper
+   has no counterpart.  Errors: SCR_INVALID_ARG for a NULL path, a file that
+   cannot be opened or a malformed line (nothing is added then). */
+int scr_tune_save(const char* path);
+int scr_tune_load(const char* path);
+
 /* Copy a level operator, prolongator or the aggregates of a hierarchy to
    host arrays in the block CSR layout above.  Call once with NULL arrays to
    receive the sizes, then again with arrays of those sizes. */

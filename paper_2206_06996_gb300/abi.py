@@ -74,7 +74,7 @@ EXPORTED = [
     "scr_residual", "scr_get_stats", "mm_setup", "mm_solve", "mm_iters", "scr_last_error",
     "scr_apply_op", "scr_apply_pc", "scr_apply_schur", "scr_amg_apply", "scr_amg_levels",
     "scr_export", "scr_bsr_spmv", "scr_profile_begin", "scr_profile_end", "scr_bsr_spmv_noalloc",
-    "scr_setup_batch", "scr_solve_batch", "scr_batch_residuals",
+    "scr_setup_batch", "scr_solve_batch", "scr_batch_residuals", "scr_tune_save", "scr_tune_load",
 ]
 
 _lib = None

@@ -80,6 +80,11 @@ void build_sell(const DBsr<double>& M, DSell<VT>& S, DeviceArena& a, cudaStream_
 void set_forced_group(int code);
 // CTAs ahead for the L2 prefetch of the scalar-row products (0: off)
 void set_l2_prefetch(int ctas);
+// print every autotune decision to stderr (0: quiet)
+void set_tune_verbose(int v);
+// write / read the autotune cache as text (throw std::invalid_argument)
+void tune_save(const char* path);
+void tune_load(const char* path);
 // time the lane-group widths for products of M with nrhs right-hand sides
 // and store the fastest in M.g; returns the chosen width
 template <typename VT>

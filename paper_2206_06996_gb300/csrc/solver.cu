@@ -937,6 +937,7 @@ int scr_create(scr_handle* out, const scr_opts* o, void* stream) {
     h->o = op;
     set_forced_group(op.spmv_group);
     set_l2_prefetch(op.l2_prefetch);
+    set_tune_verbose(op.verbose);
     h->s = static_cast<cudaStream_t>(stream);
     SCR_CUDA(cudaGetDevice(&h->device));
     configure_pool(h->device);
@@ -1610,6 +1611,22 @@ int scr_export(scr_handle h, int which, int level, int kind, scr_bsr_out* out) {
     SCR_CUDA(cudaMemcpyAsync(out->val, v, sizeof(double) * nv, cudaMemcpyDeviceToHost, h->s));
     SCR_CUDA(cudaStreamSynchronize(h->s));
   });
+}
+
+int scr_tune_save(const char* path) {
+  if (!path) {
+    set_last_error("scr_tune_save: NULL path");
+    return SCR_INVALID_ARG;
+  }
+  return guarded([&] { tune_save(path); });
+}
+
+int scr_tune_load(const char* path) {
+  if (!path) {
+    set_last_error("scr_tune_load: NULL path");
+    return SCR_INVALID_ARG;
+  }
+  return guarded([&] { tune_load(path); });
 }
 
 int scr_profile_begin(scr_handle h, int kclass, int capacity) {

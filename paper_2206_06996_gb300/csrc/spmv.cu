@@ -14,7 +14,9 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <stdexcept>
 #include <tuple>
+#include <vector>
 #include <type_traits>
 
 #include "epilogue.cuh"
@@ -359,6 +361,9 @@ __global__ void __launch_bounds__(256) k_sell_spmv(DSell<VT> S, const XT* __rest
 // FP64 241 -> 229 us); 1536 and more were slower than none.
 static int g_l2_prefetch = 192;
 void set_l2_prefetch(int ctas) { g_l2_prefetch = ctas; }
+// print every autotune decision with the candidates' times (options.verbose)
+static int g_tune_verbose = 0;
+void set_tune_verbose(int v) { g_tune_verbose = v; }
 
 template <int BR, int BC, int NRHS, int G, typename VT, typename XT, typename AT, Epi E>
 static void launch_spmv_g(const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& e, cudaStream_t s) {
@@ -557,6 +562,7 @@ int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s) {
   float best = 1e30f;
   int bestg = M.g;
   const int saved = M.g;
+  float times[8] = {};
   for (int q = 0; q < ncand; ++q) {
     const int code = cands[q];
     M.g = code;
@@ -569,6 +575,7 @@ int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s) {
     SCR_CUDA(cudaEventSynchronize(e1));
     float ms = 0;
     SCR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    times[q] = ms;
     if (ms < best) {
       best = ms;
       bestg = code;
@@ -585,8 +592,57 @@ int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s) {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     tune_cache()[key] = bestg;
   }
+  if (g_tune_verbose) {
+    fprintf(stderr, "[autotune] %dx%d blocks, %d x %d block rows/cols, %lld blocks, %s, nrhs %d -> code %d |",
+            M.br, M.bc, M.nbr, M.nbc, M.nnzb, sizeof(VT) == 8 ? "fp64" : "fp32", nrhs, bestg);
+    for (int q = 0; q < ncand; ++q) fprintf(stderr, " %d: %.1f us", cands[q], 200.0f * times[q]);
+    fprintf(stderr, "\n");
+  }
   return bestg;
 }
+// text form of the cache: "nnzb nbr nbc br bc value_bytes nrhs code" per line
+static bool valid_code(int c) {
+  return (c >= 1 && c <= 16) || (c >= 101 && c <= 116) || c == 201 || c == 202 || c == 204 || c == 208;
+}
+
+void tune_save(const char* path) {
+  FILE* f = fopen(path, "w");
+  if (!f) throw std::invalid_argument("scr_tune_save: cannot open the file for writing");
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  fprintf(f, "# scr_gb300 autotune decisions: nnzb nbr nbc br bc value_bytes nrhs code\n");
+  for (const auto& kv : tune_cache()) {
+    const TuneKey& k = kv.first;
+    fprintf(f, "%lld %d %d %d %d %d %d %d\n", k.nnzb, k.nbr, k.nbc, k.br, k.bc, k.vt, k.nrhs, kv.second);
+  }
+  fclose(f);
+}
+
+void tune_load(const char* path) {
+  FILE* f = fopen(path, "r");
+  if (!f) throw std::invalid_argument("scr_tune_load: cannot open the file");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<std::pair<TuneKey, int>> got;
+  char line[512];
+  bool bad = false;
+  while (fgets(line, sizeof line, f)) {
+    if (line[0] == '#' || line[0] == '\n') continue;
+    TuneKey k{};
+    int code = 0;
+    if (sscanf(line, "%lld %d %d %d %d %d %d %d", &k.nnzb, &k.nbr, &k.nbc, &k.br, &k.bc, &k.vt, &k.nrhs, &code) != 8 ||
+        !valid_code(code) || k.nnzb < 0 || k.nbr < 0 || k.nbc < 0) {
+      bad = true;
+      break;
+    }
+    k.dev = dev;
+    got.emplace_back(k, code);
+  }
+  fclose(f);
+  if (bad) throw std::invalid_argument("scr_tune_load: malformed line");
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  for (const auto& kv : got) tune_cache()[kv.first] = kv.second;
+}
+
 template int autotune_spmv<double>(DBsr<double>&, int, cudaStream_t);
 template int autotune_spmv<float>(DBsr<float>&, int, cudaStream_t);
 

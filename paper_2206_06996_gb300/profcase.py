@@ -4,7 +4,8 @@
 
 builds the 96 x (11 + 5) tube with `--n-ax` axial layers (100 layers:
 154,337 nodes, A about 170 MB in FP64, larger than L2), sets up the solver
-with the autotuner off (default lane groups) and applies `--reps` V-cycles of
+with the autotuner off (every product with the kernel `--group`, default
+the scalar-row kernel with 2 lanes per row) and applies `--reps` V-cycles of
 the A hierarchy; `--what solve` runs one full block solve instead.  A
 profiler capture of one kernel family (for example `k_spmv<3, 3, 1, 2,
 double`) then sees only launches of that family on this moderate case.
@@ -26,6 +27,8 @@ def main():
     ap.add_argument("--n-ax", type=int, default=100)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--what", choices=["vcycle", "solve"], default="vcycle")
+    ap.add_argument("--group", type=int, default=102,
+                    help="product kernel code for every matrix (102: scalar-row kernel, 2 lanes per row)")
     args = ap.parse_args()
     import torch
 
@@ -34,7 +37,7 @@ def main():
 
     s = F.tube_system("tube_large", n_ax=args.n_ax)
     prec = pkg.SCR_MIXED if args.precision == "mixed" else pkg.SCR_FP64
-    with pkg.BlockSolver(precision=prec, autotune=0) as sol:
+    with pkg.BlockSolver(precision=prec, autotune=0, spmv_group=args.group) as sol:
         sol.setup(s.A, s.B, s.C, s.D)
         if args.what == "solve":
             x = sol.solve(torch.as_tensor(s.b, device="cuda"))

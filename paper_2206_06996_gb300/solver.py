@@ -3,6 +3,7 @@ from __future__ import annotations
 
 import ctypes as C
 import dataclasses
+import os
 
 import numpy as np
 
@@ -316,3 +317,13 @@ def bsr_spmv_noalloc(M: DeviceBSR, x, y, stream=None):
     check(lib.scr_bsr_spmv_noalloc(C.byref(s), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
                                    C.c_void_p(stream)))
     return y
+
+
+def tune_save(path: str) -> None:
+    """Write the autotuner's cached kernel choices to a text file."""
+    check(load_library().scr_tune_save(os.fsencode(path)))
+
+
+def tune_load(path: str) -> None:
+    """Add the kernel choices of a file written by tune_save to the cache."""
+    check(load_library().scr_tune_load(os.fsencode(path)))

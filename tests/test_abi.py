@@ -62,3 +62,24 @@ def test_options_struct_layout_matches_header():
         if len(parts) == 2:
             decl.extend(v.strip() for v in parts[1].split(","))
     assert [f for f, _ in abi.Opts._fields_] == decl, (decl, fields)
+
+
+def test_tune_file_round_trip_without_gpu(tmp_path):
+    """scr_tune_load / scr_tune_save: decisions read from a file come back
+    out unchanged; malformed files and invalid kernel codes are rejected."""
+    import paper_2206_06996_gb300 as pkg
+    good = tmp_path / "tune.txt"
+    good.write_text("# comment\n9044975 616337 616337 3 3 8 1 102\n620434 616337 76959 3 3 4 1 101\n")
+    pkg.tune_load(str(good))
+    out = tmp_path / "out.txt"
+    pkg.tune_save(str(out))
+    lines = [l.split() for l in out.read_text().splitlines() if not l.startswith("#")]
+    assert ["9044975", "616337", "616337", "3", "3", "8", "1", "102"] in lines
+    assert ["620434", "616337", "76959", "3", "3", "4", "1", "101"] in lines
+    for bad in ("1 2 3\n", "10 10 10 3 3 8 1 150\n", "10 -1 10 3 3 8 1 101\n"):
+        f = tmp_path / "bad.txt"
+        f.write_text(bad)
+        with pytest.raises(pkg.ScrError):
+            pkg.tune_load(str(f))
+    with pytest.raises(pkg.ScrError):
+        pkg.tune_load(str(tmp_path / "missing.txt"))
