@@ -434,8 +434,17 @@ static int pick_group(const DBsr<VT>& M) {
   // measured on the 616k-node tube: FP64 3x3 rows are fastest with 2 lanes
   // per scalar row (the FP64 pipe binds), FP32 with 4 (coalescing binds)
   const double per_row = M.nbr ? (double)M.nnzb * M.bc / M.nbr : 0.0;
-  if (sizeof(VT) == 8) return per_row >= 24 ? 2 : 1;
-  return per_row >= 24 ? 4 : 2;
+  int G = sizeof(VT) == 8 ? (per_row >= 24 ? 2 : 1) : (per_row >= 24 ? 4 : 2);
+  // small operators (the coarse AMG levels) fill less than a wave of the GPU
+  // with one group per row, and their rows are long, so each lane would walk
+  // dozens of blocks one dependent L2 round trip at a time: widen the group
+  // (up to 16 lanes, at least 4 values per lane) while the grid stays below
+  // two waves.  Measured on the coarse tube levels: about 23 us per product
+  // with 2 lanes whatever the level's size.
+  const long long nrows = (long long)M.nbr * M.br;
+  const long long wave = (long long)sm_count() * 2048;
+  while (G < 16 && per_row >= 8.0 * G && nrows * G < wave) G *= 2;
+  return G;
 }
 
 template <int BR, int BC, int NR, typename VT, typename XT>
@@ -552,8 +561,9 @@ int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s) {
   // the scalar-row kernel with 1, 2, 4 or 8 lanes and, when M has a tile
   // plan, the staged kernel with 2, 4 or 8 (the block-row and sliced-ELL
   // variants measured slower on the tube operators)
-  int cands[8] = {101, 102, 104, 108};
+  int cands[9] = {101, 102, 104, 108};
   int ncand = 4;
+  if (M.nbr && (double)M.nnzb * M.bc / M.nbr >= 64) cands[ncand++] = 116;  // long rows
   if (M.tiles && staged_shape_supported(M.br, M.bc, nrhs)) {
     cands[ncand++] = 202;
     cands[ncand++] = 204;
@@ -562,7 +572,7 @@ int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s) {
   float best = 1e30f;
   int bestg = M.g;
   const int saved = M.g;
-  float times[8] = {};
+  float times[9] = {};
   for (int q = 0; q < ncand; ++q) {
     const int code = cands[q];
     M.g = code;
