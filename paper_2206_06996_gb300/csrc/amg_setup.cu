@@ -543,6 +543,7 @@ void tentative(const int* agg, int nbr, int n_agg, int bs, DBsr<double>& P, Devi
 constexpr int kHashSlots = 1024;          // per warp in shared memory
 constexpr int kGlobalSlots = 1 << 16;     // per warp in global scratch
 constexpr int kSpgemmWarps = 4;
+constexpr int kNumericCols = 512;         // output columns cached per warp in the numeric phase
 
 __device__ __forceinline__ unsigned hash_col(int c) { return (unsigned)c * 2654435761u; }
 
@@ -566,29 +567,47 @@ __device__ __forceinline__ int global_table_size(int ub) {
 }
 
 // insert the columns of row i of A*B into a warp's hash table; returns the
-// number of new keys this lane inserted; a table that fills up sets *err
-__device__ int spgemm_insert(const DBsr<double>& A, const DBsr<double>& B, int i, int* table, int hsize, int lane,
-                             int* err) {
-  int mine = 0;
-  for (int t = A.rp[i]; t < A.rp[i + 1]; ++t) {
-    const int j = A.col[t];
-    for (int u = B.rp[j] + lane; u < B.rp[j + 1]; u += 32) {
-      const int key = B.col[u];
-      unsigned h = hash_col(key) & (hsize - 1);
-      for (int probe = 0;; ++probe) {
-        if (probe >= hsize) {
-          atomicExch(err, 1);
-          return mine;
-        }
-        const int prev = atomicCAS(table + h, -1, key);
-        if (prev == -1) {
-          ++mine;
-          break;
-        }
-        if (prev == key) break;
-        h = (h + 1) & (hsize - 1);
-      }
+// number of new keys this lane inserted; a table that fills up sets *err.
+// When B's rows are short on average (ub < 8 entries per A entry: the
+// prolongators and the Galerkin factors), the lanes take the entries of A's
+// row in turn and each inserts the whole B row its entry selects, which
+// keeps them busy and overlaps the dependent loads of the A entries;
+// otherwise the lanes share each B row.  The resulting column set does not
+// depend on the order of the inserts.
+__device__ __forceinline__ bool spgemm_try_insert(int key, int* table, int hsize, int* err, int& mine) {
+  unsigned h = hash_col(key) & (hsize - 1);
+  for (int probe = 0;; ++probe) {
+    if (probe >= hsize) {
+      atomicExch(err, 1);
+      return false;
     }
+    const int prev = atomicCAS(table + h, -1, key);
+    if (prev == -1) {
+      ++mine;
+      return true;
+    }
+    if (prev == key) return true;
+    h = (h + 1) & (hsize - 1);
+  }
+}
+
+__device__ int spgemm_insert(const DBsr<double>& A, const DBsr<double>& B, int i, int ub, int* table, int hsize,
+                             int lane, int* err) {
+  int mine = 0;
+  const int as = A.rp[i], ae = A.rp[i + 1];
+  if (ub >= 8 * (ae - as)) {
+    // long B rows (e.g. C diag(A)^{-1} B): the lanes share each B row
+    for (int t = as; t < ae; ++t) {
+      const int j = A.col[t];
+      for (int u = B.rp[j] + lane; u < B.rp[j + 1]; u += 32)
+        if (!spgemm_try_insert(B.col[u], table, hsize, err, mine)) return mine;
+    }
+    return mine;
+  }
+  for (int t = as + lane; t < ae; t += 32) {
+    const int j = A.col[t];
+    for (int u = B.rp[j]; u < B.rp[j + 1]; ++u)
+      if (!spgemm_try_insert(B.col[u], table, hsize, err, mine)) return mine;
   }
   return mine;
 }
@@ -606,7 +625,7 @@ __global__ void __launch_bounds__(32 * kSpgemmWarps) k_spgemm_count(DBsr<double>
     const int hsize = gs ? gs : kHashSlots;
     for (int h = lane; h < hsize; h += 32) table[h] = -1;
     __syncwarp();
-    const int mine = spgemm_insert(A, B, i, table, hsize, lane, err);
+    const int mine = spgemm_insert(A, B, i, ub[i], table, hsize, lane, err);
     const int tot = warp_sum(mine);
     if (lane == 0) cnt[i] = tot;
     __syncwarp();
@@ -626,7 +645,7 @@ __global__ void __launch_bounds__(32 * kSpgemmWarps) k_spgemm_fill(DBsr<double> 
     const int hsize = gs ? gs : kHashSlots;
     for (int h = lane; h < hsize; h += 32) table[h] = -1;
     __syncwarp();
-    spgemm_insert(A, B, i, table, hsize, lane, err);
+    spgemm_insert(A, B, i, ub[i], table, hsize, lane, err);
     __syncwarp();
     // compact the keys into the front of C's row (unsorted) ...
     const int base = C.rp[i], cnt = C.rp[i + 1] - base;
@@ -658,12 +677,90 @@ __global__ void __launch_bounds__(32 * kSpgemmWarps) k_spgemm_numeric(DBsr<doubl
                                                                      DBsr<double> C) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int i = blockIdx.x * kSpgemmWarps + w;
-  if (i >= A.nbr) return;
+  if (i >= A.nbr) return;  // uniform over the warp
   const int cs = C.rp[i], ck = C.rp[i + 1] - cs;
   double* cv = C.val + (long long)cs * BR * BC;
+  const int as = A.rp[i], ak = A.rp[i + 1] - as;
+  if (ck <= 32) {
+    // Rows with at most 32 output entries (the prolongator and Galerkin
+    // products): A's row is taken in chunks of 32 entries; within a chunk
+    // the partial products (t, u) = (entry t of A's row, entry u of the B row
+    // it selects) are numbered p in t-major order, lane p % 32 forms product
+    // p, and lane e, owner of output entry e, adds the products that land on
+    // e in increasing t, i.e. in the order of the general path below.
+    constexpr unsigned kFull = 0xffffffffu;
+    double acc[BR * BC];
+#pragma unroll
+    for (int e = 0; e < BR * BC; ++e) acc[e] = 0.0;
+    for (int tc = 0; tc < ak; tc += 32) {
+      const int nt = min(32, ak - tc);
+      int bst = 0, lent = 0;
+      if (lane < nt) {
+        const int jt = A.col[as + tc + lane];
+        bst = B.rp[jt];
+        lent = B.rp[jt + 1] - bst;
+      }
+      int incl = lent;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const int off = incl - lent;
+      const int np = __shfl_sync(kFull, incl, 31);
+      for (int base = 0; base < np; base += 32) {
+        const int p = base + lane;
+        int tl = 0;  // the last entry of the chunk whose products start at or before p
+        for (int q = 1; q < nt; ++q)
+          if (__shfl_sync(kFull, off, q) <= p) tl = q;
+        const int j_b = __shfl_sync(kFull, bst, tl), j_len = __shfl_sync(kFull, lent, tl);
+        const int u = p - __shfl_sync(kFull, off, tl);
+        int pos = -1;
+        double prod[BR * BC];
+#pragma unroll
+        for (int e = 0; e < BR * BC; ++e) prod[e] = 0.0;
+        if (p < np) {
+          const int t = tc + tl;
+          pos = find_in_row(C.col, cs, cs + ck, B.col[j_b + u]) - cs;
+#pragma unroll
+          for (int r = 0; r < BR; ++r)
+#pragma unroll
+            for (int q = 0; q < BC; ++q) {
+              double v = 0.0;
+#pragma unroll
+              for (int m = 0; m < BK; ++m)
+                v = fma(A.val[slab_index(as, ak, t, r, m, BR, BK)], B.val[slab_index(j_b, j_len, u, m, q, BK, BC)],
+                        v);
+              prod[r * BC + q] = v;
+            }
+        }
+        const int cnt = min(32, np - base);
+        for (int q = 0; q < cnt; ++q) {
+          const int pq = __shfl_sync(kFull, pos, q);
+#pragma unroll
+          for (int e = 0; e < BR * BC; ++e) {
+            const double v = __shfl_sync(kFull, prod[e], q);
+            if (lane == pq) acc[e] += v;
+          }
+        }
+      }
+    }
+    if (lane < ck) {
+#pragma unroll
+      for (int r = 0; r < BR; ++r)
+#pragma unroll
+        for (int q = 0; q < BC; ++q) cv[(long long)r * ck * BC + (long long)lane * BC + q] = acc[r * BC + q];
+    }
+    return;
+  }
+  // general path: the output row's columns in shared memory when they fit,
+  // for the searches below
+  __shared__ int ccol[kSpgemmWarps][kNumericCols];
+  const bool cached = ck <= kNumericCols;
+  if (cached)
+    for (int e = lane; e < ck; e += 32) ccol[w][e] = C.col[cs + e];
   for (int e = lane; e < ck * BR * BC; e += 32) cv[e] = 0.0;
   __syncwarp();
-  const int as = A.rp[i], ak = A.rp[i + 1] - as;
   for (int t = 0; t < ak; ++t) {
     double a[BR][BK];
 #pragma unroll
@@ -674,7 +771,7 @@ __global__ void __launch_bounds__(32 * kSpgemmWarps) k_spgemm_numeric(DBsr<doubl
     const int bs = B.rp[j], bk = B.rp[j + 1] - bs;
     for (int u = lane; u < bk; u += 32) {
       const int c = B.col[bs + u];
-      const int pos = find_in_row(C.col, cs, cs + ck, c) - cs;
+      const int pos = cached ? find_in_row(ccol[w], 0, ck, c) : find_in_row(C.col, cs, cs + ck, c) - cs;
       if (pos >= ck) continue;  // cannot happen for a consistent symbolic phase
       double b[BK][BC];
 #pragma unroll

@@ -341,41 +341,58 @@ SCR_INST_BLAS(double)
 SCR_INST_BLAS(float)
 
 // ------------------------------------------------------------ Arnoldi scalars
+// One warp: the lanes load column j of H (the two Gram-Schmidt passes'
+// coefficients) and the previous rotations into shared memory in parallel,
+// lane 0 applies the rotations and the new one there (the same operations
+// in the same order as a single thread on the state), the lanes write the
+// column back.
 __global__ void k_arnoldi_finalize(ArnoldiState* st, int j, double* host_rel) {
   constexpr int ldh = kMaxBasis + 1;
+  __shared__ double h[kMaxBasis + 2], rc[kMaxBasis], rs[kMaxBasis];
+  const int t = threadIdx.x;
   double* Hj = st->H + (long long)j * ldh;
-  for (int i = 0; i <= j; ++i) Hj[i] = st->h1[i] + st->h2[i];
-  const double hn = sqrt(fmax(st->nrm2, 0.0));
-  Hj[j + 1] = hn;
-  // previous rotations
-  for (int i = 0; i < j; ++i) {
-    const double t = st->cs[i] * Hj[i] + st->sn[i] * Hj[i + 1];
-    Hj[i + 1] = -st->sn[i] * Hj[i] + st->cs[i] * Hj[i + 1];
-    Hj[i] = t;
+  for (int i = t; i <= j; i += 32) h[i] = st->h1[i] + st->h2[i];
+  for (int i = t; i < j; i += 32) {
+    rc[i] = st->cs[i];
+    rs[i] = st->sn[i];
   }
-  const double a = Hj[j], c = Hj[j + 1];
-  const double d = hypot(a, c);
-  double cs = 1.0, sn = 0.0;
-  if (d != 0.0) {
-    cs = a / d;
-    sn = c / d;
+  __syncwarp();
+  if (t == 0) {
+    const double hn = sqrt(fmax(st->nrm2, 0.0));
+    h[j + 1] = hn;
+    // previous rotations
+    for (int i = 0; i < j; ++i) {
+      const double v = rc[i] * h[i] + rs[i] * h[i + 1];
+      h[i + 1] = -rs[i] * h[i] + rc[i] * h[i + 1];
+      h[i] = v;
+    }
+    const double a = h[j], c = h[j + 1];
+    const double d = hypot(a, c);
+    double cs = 1.0, sn = 0.0;
+    if (d != 0.0) {
+      cs = a / d;
+      sn = c / d;
+    }
+    st->cs[j] = cs;
+    st->sn[j] = sn;
+    h[j] = d;
+    h[j + 1] = 0.0;
+    const double gj = st->g[j];
+    st->g[j + 1] = -sn * gj;
+    st->g[j] = cs * gj;
+    st->rel = fabs(st->g[j + 1]) / st->bnorm;
+    // happy breakdown: the new direction vanished relative to the column
+    st->breakdown = (hn <= 1e-300 || d == 0.0) ? 1 : 0;
+    st->inv_hnext = hn > 1e-300 ? 1.0 / hn : 0.0;
+    host_rel[0] = st->rel;
+    host_rel[1] = (double)st->breakdown;
   }
-  st->cs[j] = cs;
-  st->sn[j] = sn;
-  Hj[j] = d;
-  Hj[j + 1] = 0.0;
-  st->g[j + 1] = -sn * st->g[j];
-  st->g[j] = cs * st->g[j];
-  st->rel = fabs(st->g[j + 1]) / st->bnorm;
-  // happy breakdown: the new direction vanished relative to the column
-  st->breakdown = (hn <= 1e-300 || d == 0.0) ? 1 : 0;
-  st->inv_hnext = hn > 1e-300 ? 1.0 / hn : 0.0;
-  host_rel[0] = st->rel;
-  host_rel[1] = (double)st->breakdown;
+  __syncwarp();
+  for (int i = t; i <= j + 1; i += 32) Hj[i] = h[i];
 }
 
 void arnoldi_finalize(ArnoldiState* st, int j, double* host_rel, cudaStream_t s) {
-  k_arnoldi_finalize<<<1, 1, 0, s>>>(st, j, host_rel);
+  k_arnoldi_finalize<<<1, 32, 0, s>>>(st, j, host_rel);
   SCR_LAUNCH();
   counters().launches++;
 }
