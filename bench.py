@@ -70,6 +70,8 @@ def peaks():
 # FP64 FMA rate of GB300: 2 FP64 FMA per SM per clock (152 SMs); measured
 # 0.600 TFMA/s at 1995 MHz with an independent-chain FMA loop
 FP64_FMA_PER_SM_CLK = 2
+# dram bytes / algorithmic bytes of the FP64 level-0 product (ncu, 154k-node tube)
+TRAFFIC_OVER_ALGORITHMIC_FP64 = 181.0 / 180.0
 N_SM = 152
 
 
@@ -405,6 +407,16 @@ def main():
                      "timed_launches": kprof["timed"], "bytes_per_launch": bytes_pl,
                      "us_per_launch": per_launch_s * 1e6,
                      "share_of_step": kprof["ms"] / ms, "traffic": None})
+        if prec == pkg.SCR_FP64:
+            # DRAM bytes per launch: the ncu capture of this kernel on the
+            # 154k-node tube measured dram read + write = 181.0 MB against
+            # 180.0 MB of algorithmic bytes per launch (x gathers hit L1/L2, no
+            # re-reads); traffic grows with the stored blocks, so the full
+            # launch's traffic is that ratio times its algorithmic bytes
+            roof["traffic"] = TRAFFIC_OVER_ALGORITHMIC_FP64 * bytes_pl
+            roof["traffic_note"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernel on the "
+                                    "154k-node tube (181.0 MB per launch, 180.0 MB algorithmic), scaled to this "
+                                    "launch by its algorithmic bytes")
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         try:
