@@ -20,6 +20,9 @@ infrastructure only; the CPU reference of the whole solver path).
   level) and U_SIMPLE^{-1}:
       yhat_v = A^{-1} r_v, y_p = Shat^{-1} (r_p - C yhat_v),
       y_v = yhat_v - diag(A)^{-1} B y_p.
+* SIMPLEC (Sec. 5.2.1): SIMPLE with diag(A) replaced, in Shat and in
+  U_SIMPLE, by the diagonal lumped from the absolute values of A's entries,
+  d_i = sum_j |a_ij|.
 * Mesh motion (Sec. 5.2.2): CG + AMG(L) on the harmonic extension.
 """
 from __future__ import annotations
@@ -30,7 +33,7 @@ import numpy as np
 
 from . import amg
 from .krylov import KrylovInfo, fgmres, gmres, pcg
-from .schur import schur_hat
+from .schur import schur_hat, simple_diagonal
 from .sparse import BlockOperator, rel_residual, to_csr
 
 
@@ -56,7 +59,7 @@ class SolverOptions:
     amg_pmax: int = 5
     smoother: str = "cheb"
     cheb_degree: int = 3
-    precond: str = "scr"       # "scr" (Algorithm 1) or "simple"
+    precond: str = "scr"       # "scr" (Algorithm 1), "simple" or "simplec"
     mm_rtol: float = 1e-8
     mm_max_it: int = 500
 
@@ -75,7 +78,10 @@ class SCRSolver:
         self.opts = opts or SolverOptions()
         self.op = BlockOperator.from_system(system)
         o = self.opts
-        self.Shat = schur_hat(self.op)
+        # SIMPLEC (Sec. 5.2.1): the lumped diagonal in Shat and in the update
+        self.lumped = o.precond == "simplec"
+        self.dsimple = simple_diagonal(self.op, self.lumped)
+        self.Shat = schur_hat(self.op, self.lumped)
         self.amg_A = amg.setup(self.op.A, 3, o.amg_theta, o.amg_max_levels, o.amg_coarse, o.nu, o.nu,
                                o.amg_trunc, o.amg_pmax, o.smoother, o.cheb_degree)
         self.amg_S = amg.setup(self.Shat, 1, o.amg_theta, o.amg_max_levels, o.amg_coarse, o.nu, o.nu,
@@ -123,13 +129,13 @@ class SCRSolver:
         yp, info = gmres(lambda v: self.Shat @ v, rp2, lambda v: amg.vcycle(self.amg_S, v),
                          tol=o.rtol_S, maxit=o.max_S, restart=o.restart_inner)
         self.cnt.s_iters += info.iters
-        yv = yv_hat - (op.B @ yp) / op.A.diagonal()
+        yv = yv_hat - (op.B @ yp) / self.dsimple
         return np.concatenate([yv, yp])
 
     # outer level --------------------------------------------------------
     def solve(self, b: np.ndarray, max_outer: int | None = None):
         o = self.opts
-        pc = self.apply_simple if o.precond == "simple" else self.apply_pc
+        pc = self.apply_simple if o.precond in ("simple", "simplec") else self.apply_pc
         x, info = fgmres(self.op.matvec, b, pc, tol=o.rtol,
                          maxit=o.max_it if max_outer is None else max_outer, restart=o.restart)
         self.cnt.outer += info.iters

@@ -417,3 +417,48 @@ def test_bf16_rounding_matches_torch_and_error_bound():
     np.testing.assert_array_equal(round_bf16(x), ref)
     assert np.all(np.abs(round_bf16(x) - x) <= 2.0**-8 * np.abs(x) * (1 + 2.0**-20))
     assert np.all(np.abs(round_f32(x) - x) <= 2.0**-24 * np.abs(x))
+
+
+# ------------------------------------------------------------- SIMPLEC
+def test_simplec_identity(tiny_system):
+    """P_SIMPLEC in factored form equals its closed form [[A, A D_c^{-1} B], [C, D]]."""
+    op = BlockOperator.from_system(tiny_system)
+    P1 = schur.simple_matrix_dense(op, lumped=True)
+    P2 = schur.simple_factored_dense(op, lumped=True)
+    assert np.allclose(P1, P2, rtol=1e-9, atol=1e-12 * np.abs(P1).max())
+    # the lumped diagonal dominates |diag(A)| and differs from it on this system
+    d, dl = schur.simple_diagonal(op), schur.simple_diagonal(op, lumped=True)
+    assert np.all(dl >= np.abs(d)) and np.any(dl > np.abs(d) * (1 + 1e-6))
+
+
+def test_simplec_reduces_to_simple_for_a_diagonal_A(tiny_system):
+    """With a diagonal A (positive entries) the lumped diagonal is diag(A):
+    SIMPLEC and SIMPLE coincide, including P^{-1} r."""
+    op = BlockOperator.from_system(tiny_system)
+    opd = BlockOperator.from_system(tiny_system)
+    opd.A = sp.diags(np.abs(op.A.diagonal()) + 1.0).tocsr()
+    assert np.array_equal(schur.simple_diagonal(opd, lumped=True), schur.simple_diagonal(opd))
+    r = np.random.default_rng(3).standard_normal(opd.n)
+    y1 = schur.simple_inverse_apply_dense(opd, r)
+    y2 = schur.simple_inverse_apply_dense(opd, r, lumped=True)
+    assert np.allclose(y1, y2, rtol=1e-12, atol=1e-12 * np.abs(y1).max())
+
+
+def test_simplec_apply_with_tight_solves(tiny_system):
+    opts = scr.SolverOptions(rtol_A=1e-13, rtol_S=1e-13, max_A=400, max_S=400, restart_inner=80,
+                             precond="simplec")
+    s = scr.SCRSolver(tiny_system, opts)
+    r = np.random.default_rng(10).standard_normal(s.op.n)
+    y = s.apply_simple(r)
+    yd = schur.simple_inverse_apply_dense(s.op, r, lumped=True)
+    assert np.linalg.norm(y - yd) <= 1e-8 * np.linalg.norm(yd)
+    P = schur.simple_matrix_dense(s.op, lumped=True)
+    assert np.linalg.norm(P @ yd - r) <= 1e-9 * np.linalg.norm(r)
+
+
+def test_simplec_full_solve_matches_direct(mini_system, mini_direct):
+    s = scr.SCRSolver(mini_system, scr.SolverOptions(precond="simplec"))
+    x, info = s.solve(mini_system.b)
+    assert info.converged
+    assert s.rel_residual(x, mini_system.b) <= 1e-8
+    assert np.linalg.norm(x - mini_direct) <= 1e-6 * np.linalg.norm(mini_direct)
