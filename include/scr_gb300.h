@@ -63,6 +63,8 @@ extern "C" {
 /* preconditioners of the outer FGMRES (Sec. 5.2.1) */
 #define SCR_PC_SCR 0    /* Schur complement reduction, App. B Algorithm 1 (S applied by Algorithm 2) */
 #define SCR_PC_SIMPLE 1 /* SIMPLE: Shat for S and diag(A) in the upper factor, no inner level */
+#define SCR_PC_SIMPLEC 2 /* SIMPLEC (Sec. 5.2.1): SIMPLE with diag(A) replaced, in Shat and in the upper
+                            factor, by the diagonal lumped from |A|: d_i = sum_j |a_ij| */
 
 /* hierarchies for scr_amg_apply / scr_export */
 #define SCR_HIER_A 0
@@ -88,7 +90,7 @@ typedef struct {
   int max_A, max_S, max_I; /* 200 each */
   int restart_inner;  /* restart of the intermediate/inner GMRES, 30 */
   int precision;      /* SCR_FP64 or SCR_MIXED */
-  int precond;        /* SCR_PC_SCR (Algorithm 1, default) or SCR_PC_SIMPLE */
+  int precond;        /* SCR_PC_SCR (Algorithm 1, default), SCR_PC_SIMPLE or SCR_PC_SIMPLEC */
   double amg_theta;   /* strength threshold, 0.08 */
   int amg_max_levels; /* 10 */
   int amg_coarse_size;/* block rows at which coarsening stops, 64 */
@@ -232,7 +234,7 @@ const char* scr_last_error(void);
 int scr_apply_op(scr_handle h, const double* x, double* y);
 
 /* y = P^{-1} r for the handle's preconditioner: Algorithm 1 of App. B
-   (SCR_PC_SCR) or P_SIMPLE^{-1} (SCR_PC_SIMPLE, Sec. 5.2.1). */
+   (SCR_PC_SCR) or P_SIMPLE^{-1} (SCR_PC_SIMPLE, Sec. 5.2.1; SCR_PC_SIMPLEC: P_SIMPLEC^{-1}). */
 int scr_apply_pc(scr_handle h, const double* r, double* y);
 
 /* y_p = S x_p = D x_p - C A^{-1} B x_p, Algorithm 2 of App. B. */

@@ -8,7 +8,7 @@ from . import build as _build
 
 SCR_OK, SCR_INVALID_ARG, SCR_CUDA_ERROR, SCR_NOT_CONVERGED, SCR_DEVICE_TIMEOUT, SCR_SINGULAR = range(6)
 SCR_FP64, SCR_MIXED = 0, 1
-SCR_PC_SCR, SCR_PC_SIMPLE = 0, 1
+SCR_PC_SCR, SCR_PC_SIMPLE, SCR_PC_SIMPLEC = 0, 1, 2
 SCR_HIER_A, SCR_HIER_SHAT, SCR_HIER_MESH = 0, 1, 2
 SCR_EXPORT_OPERATOR, SCR_EXPORT_PROLONGATOR, SCR_EXPORT_AGGREGATES = 0, 1, 2
 

@@ -199,6 +199,27 @@ __global__ void k_l1_inv(DBsr<double> A, double* __restrict__ dinv) {
   dinv[o] = acc > 0.0 ? 1.0 / acc : 0.0;
 }
 
+// per scalar row: sum_j |a_ij| (the lumped diagonal of SIMPLEC)
+__global__ void k_abs_rowsum(DBsr<double> A, double* __restrict__ d) {
+  const long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n = (long long)A.nbr * A.br;
+  if (o >= n) return;
+  const int i = (int)(o / A.br), r = (int)(o - (long long)i * A.br);
+  const int s = A.rp[i], k = A.rp[i + 1] - s, L = k * A.bc;
+  const double* v = A.val + (long long)s * A.br * A.bc + (long long)r * L;
+  double acc = 0.0;
+  for (int q = 0; q < L; ++q) acc += fabs(v[q]);
+  d[o] = acc;
+}
+
+void abs_rowsum(const DBsr<double>& A, double* d, cudaStream_t s) {
+  const long long n = (long long)A.nbr * A.br;
+  if (n == 0) return;
+  k_abs_rowsum<<<ceil_div(n, 256), 256, 0, s>>>(A, d);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
 void l1_inv(const DBsr<double>& A, double* dinv, cudaStream_t s) {
   const long long n = (long long)A.nbr * A.br;
   if (n == 0) return;

@@ -217,6 +217,8 @@ void inv_diag(const DBsr<double>& A, double* dinv, cudaStream_t s);
 double power_lambda(const DBsr<double>& A, const double* dinv, int iters, cudaStream_t s);
 // 1/ sum_j |a_ij| per scalar row
 void l1_inv(const DBsr<double>& A, double* dinv, cudaStream_t s);
+// d_i = sum_j |a_ij| per scalar row (SIMPLEC's lumped diagonal)
+void abs_rowsum(const DBsr<double>& A, double* d, cudaStream_t s);
 // max_i sum_j |a_ij| / |a_ii| (device scalar)
 void gershgorin(const DBsr<double>& A, const double* diag, double* out, cudaStream_t s);
 // scale scalar rows of B by -omega(dev)/d_i : out rowscale[n]

@@ -597,7 +597,7 @@ struct scr_ctx {
   Gmres<float> gAf, gSf, gIf;
   double *bvec = nullptr, *xvec = nullptr, *rvec = nullptr;
   double *yhat = nullptr, *rp2 = nullptr, *rv2 = nullptr, *xbar = nullptr, *xt = nullptr;
-  double* dAinv = nullptr;  // 1 / diag(A) (SIMPLE upper factor)
+  double* dAinv = nullptr;  // 1 / diag(A) (SIMPLE upper factor; SIMPLEC: 1 / sum_j |a_ij|)
   float* dAinvf = nullptr;
   float *pr = nullptr, *py = nullptr, *yhatf = nullptr, *rp2f = nullptr, *rv2f = nullptr, *xbarf = nullptr,
         *xtf = nullptr;
@@ -845,7 +845,7 @@ void apply_simple(scr_ctx* h, PcView<T>& v, const T* r, T* y) {
 }
 
 void apply_pc_any(scr_ctx* h, const double* r, double* y) {
-  const bool simple = h->o.precond == SCR_PC_SIMPLE;
+  const bool simple = h->o.precond == SCR_PC_SIMPLE || h->o.precond == SCR_PC_SIMPLEC;
   if (h->o.precision == SCR_MIXED) {
     const long long n = 3LL * h->nv + h->np;
     cast_d2f(r, h->pr, n, h->s);
@@ -925,7 +925,8 @@ int scr_create(scr_handle* out, const scr_opts* o, void* stream) {
     if (op.restart < 1 || op.restart >= kMaxBasis || op.restart_inner < 1 || op.restart_inner >= kMaxBasis)
       throw std::invalid_argument("restart lengths must lie in [1, 63]");
     if (op.precision != SCR_FP64 && op.precision != SCR_MIXED) throw std::invalid_argument("unknown precision");
-    if (op.precond != SCR_PC_SCR && op.precond != SCR_PC_SIMPLE) throw std::invalid_argument("unknown preconditioner");
+    if (op.precond != SCR_PC_SCR && op.precond != SCR_PC_SIMPLE && op.precond != SCR_PC_SIMPLEC)
+      throw std::invalid_argument("unknown preconditioner");
     if (op.amg_smoother != SCR_SMOOTH_L1 && op.amg_smoother != SCR_SMOOTH_CHEB)
       throw std::invalid_argument("unknown smoother");
     if (op.amg_degree < 1 || op.amg_degree > 16) throw std::invalid_argument("Chebyshev degree must lie in [1, 16]");
@@ -997,6 +998,8 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
       SCR_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
       SCR_CUDA(cudaStreamSynchronize(s));
       if (hb) throw std::invalid_argument("A has a missing or zero diagonal entry");
+      // SIMPLEC: the diagonal lumped from the absolute values of A's entries
+      if (h->o.precond == SCR_PC_SIMPLEC) abs_rowsum(h->A, d, s);
       DBsr<double> Bs, T;
       scale_rows_inv(h->B, d, Bs, tmp, s);
       spgemm(h->C, Bs, T, tmp, s);
@@ -1005,7 +1008,8 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
     }
     if (h->o.verbose) fprintf(stderr, "[setup] Shat %.2f ms (%lld entries)\n", ms_since(t1), h->Shat.nnzb);
     h->dAinv = a.alloc<double>(3LL * nv + 1);
-    inv_diag(h->A, h->dAinv, s);
+    if (h->o.precond == SCR_PC_SIMPLEC) l1_inv(h->A, h->dAinv, s);  // 1 / sum_j |a_ij|
+    else inv_diag(h->A, h->dAinv, s);
     const bool f32 = h->o.precision == SCR_MIXED;
     if (h->o.sell) {
       build_sell<double>(h->A, h->A_sell, a, s, h->o.sell);

@@ -124,6 +124,17 @@ def test_schur_hat(small):
     del ref
 
 
+def test_schur_hat_simplec(small):
+    """SIMPLEC builds Shat with the lumped diagonal (oracle: schur_hat(lumped=True))."""
+    op = BlockOperator.from_system(small)
+    with pkg.BlockSolver(precond=pkg.SCR_PC_SIMPLEC) as sol:
+        sol.setup(small.A, small.B, small.C, small.D)
+        got = to_csr(sol.export(pkg.SCR_HIER_SHAT, 0, pkg.SCR_EXPORT_OPERATOR))
+    want = schur.schur_hat(op, lumped=True)
+    assert abs(got - want).max() <= 1e-12 * abs(want).max()
+    assert abs(got - schur.schur_hat(op)).max() > 1e-6 * abs(want).max()
+
+
 def _strength_pattern(A, bs, theta):
     return amg.strength_graph(A, bs, theta)
 
@@ -397,6 +408,33 @@ def test_simple_apply_with_tight_solves(mini):
     assert _rel(y, yd) < 1e-7
 
 
+@pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
+def test_simplec_preconditioned_solve_matches_direct(small, small_direct, precision):
+    op = BlockOperator.from_system(small)
+    with pkg.BlockSolver(precond=pkg.SCR_PC_SIMPLEC, precision=precision) as sol:
+        sol.setup(small.A, small.B, small.C, small.D)
+        x = sol.solve(small.b.copy())
+        st = sol.stats()
+    assert st["rel_res"] <= 1e-8 and rel_residual(op, x, small.b) <= 1e-8
+    assert _rel(x, small_direct) <= 1e-6
+    assert st["i_iters"] == 0
+
+
+def test_simplec_apply_with_tight_solves(mini):
+    """P_SIMPLEC^{-1} r with tight intermediate solves equals the oracle's
+    dense P_SIMPLEC^{-1} r, and differs from P_SIMPLE^{-1} r (the lumped
+    diagonal is in effect)."""
+    op = BlockOperator.from_system(mini)
+    r = np.random.default_rng(13).standard_normal(op.n)
+    with pkg.BlockSolver(precond=pkg.SCR_PC_SIMPLEC, rtol_A=1e-13, rtol_S=1e-13, max_A=2000, max_S=2000,
+                         restart_inner=60) as sol:
+        sol.setup(mini.A, mini.B, mini.C, mini.D)
+        y = sol.apply_pc(_dev(r)).cpu().numpy()
+    yd = schur.simple_inverse_apply_dense(op, r, lumped=True)
+    assert _rel(y, yd) < 1e-7
+    assert _rel(y, schur.simple_inverse_apply_dense(op, r)) > 1e-4
+
+
 def test_block_solve_device_pointers(mini, mini_x):
     with pkg.BlockSolver() as sol:
         sol.setup(pkg.DeviceBSR.from_host(mini.A), pkg.DeviceBSR.from_host(mini.B),
@@ -603,3 +641,24 @@ def test_time_step_trends_scr_versus_simple():
         assert outer[(dt, pkg.SCR_PC_SCR)] < outer[(dt, pkg.SCR_PC_SIMPLE)], outer
         assert outer[(dt, pkg.SCR_PC_SCR)] <= 10, outer
     assert inner[(1e-3, pkg.SCR_PC_SCR)] > inner[(1e-4, pkg.SCR_PC_SCR)], inner
+
+
+@pytest.mark.parametrize("rho_s,E_s", [(1e-2, 4e6), (1e2, 4e6), (1.0, 1e6), (1.0, 1e8)])
+def test_wall_parameter_robustness(rho_s, E_s):
+    """Robustness over the wall density and Young's modulus (Sec. 6, table of
+    rho_s in [1e-2, 1e2] and E in [1e6, 1e8]: SCR's outer iteration count
+    barely moves, SIMPLE needs several times more).  On the small tube every
+    solve meets the tolerance, SCR stays within 1 to 5 outer iterations
+    (the CPU oracle: 3 in every case) and below SIMPLE's count."""
+    s = F.tube_system("tube_small", rho_s=rho_s, E_s=E_s)
+    op = BlockOperator.from_system(s)
+    outer = {}
+    for pc in (pkg.SCR_PC_SCR, pkg.SCR_PC_SIMPLE, pkg.SCR_PC_SIMPLEC):
+        with pkg.BlockSolver(precond=pc) as sol:
+            sol.setup(s.A, s.B, s.C, s.D)
+            x = sol.solve(s.b.copy())
+            outer[pc] = sol.iters()[0]
+        assert rel_residual(op, x, s.b) <= 1e-8
+    assert 1 <= outer[pkg.SCR_PC_SCR] <= 5, outer
+    assert outer[pkg.SCR_PC_SCR] < outer[pkg.SCR_PC_SIMPLE], outer
+    assert outer[pkg.SCR_PC_SCR] < outer[pkg.SCR_PC_SIMPLEC], outer
