@@ -118,6 +118,11 @@ typedef struct {
                          (operators and transfers of levels >= 1) in BF16, rounded to nearest even
                          from the FP32 copy; products still use FP32 vectors and FP32 sums;
                          0 keeps them in FP32 */
+  int cuda_graphs;    /* 1 (default): each AMG hierarchy records one V-cycle as a CUDA graph at its
+                         first use after set-up and replays it (between copies to and from two
+                         staging vectors) for every later V-cycle; 0: every V-cycle launched
+                         kernel by kernel.  V-cycles run kernel by kernel while scr_profile_begin
+                         is active.  Results are the same either way. */
   double mm_rtol;     /* mesh CG relative residual, 1e-8 */
   int mm_max_it;      /* mesh CG iteration cap, 500 */
   int verbose;        /* 0 quiet */

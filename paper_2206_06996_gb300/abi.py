@@ -32,7 +32,7 @@ class Opts(C.Structure):
         ("amg_nu", C.c_int), ("amg_trunc", C.c_double), ("amg_pmax", C.c_int), ("autotune", C.c_int),
         ("amg_smoother", C.c_int), ("amg_degree", C.c_int), ("spmv_group", C.c_int),
         ("sell", C.c_int), ("staged", C.c_int), ("stage_kb", C.c_int), ("stages", C.c_int),
-        ("l2_prefetch", C.c_int), ("amg_coarse_bf16", C.c_int),
+        ("l2_prefetch", C.c_int), ("amg_coarse_bf16", C.c_int), ("cuda_graphs", C.c_int),
         ("mm_rtol", C.c_double), ("mm_max_it", C.c_int), ("verbose", C.c_int),
     ]
 

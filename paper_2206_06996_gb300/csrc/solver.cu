@@ -127,6 +127,13 @@ static void tune_product(DBsr<VT>& M, int nrhs, const scr_opts& o, DeviceArena& 
   if (o.autotune) autotune_spmv<VT>(M, nrhs, s);
 }
 
+struct GraphExecDeleter {
+  void operator()(CUgraphExec_st* g) const {
+    if (g) cudaGraphExecDestroy(g);
+  }
+};
+using GraphExecPtr = std::unique_ptr<CUgraphExec_st, GraphExecDeleter>;
+
 struct Hierarchy {
   int bs = 1, nrhs = 1, nu = 1;
   int smoother = SCR_SMOOTH_CHEB, degree = 3;
@@ -139,6 +146,14 @@ struct Hierarchy {
   int vcycles = 0;
   int mis_rounds = 0;
   std::unique_ptr<DeviceArena> arena;
+  // CUDA graph of one V-cycle from the staging vector gin to gout (captured
+  // at the first V-cycle after set-up, replayed by every later one); the
+  // library counters of one captured V-cycle are added at each replay
+  bool use_graph = false, graph_failed = false;
+  GraphExecPtr gexec;
+  void *gin = nullptr, *gout = nullptr;
+  size_t gsize = 0;  // element size the graph was captured for
+  long long glaunches = 0, gbytes = 0;
 
   int n_levels() const { return (int)lv.size(); }
 
@@ -146,6 +161,11 @@ struct Hierarchy {
              const DBsr<float>* A0f = nullptr) {
     bs = bs_;
     nrhs = nrhs_;
+    use_graph = o.cuda_graphs != 0;
+    graph_failed = false;
+    gexec.reset();
+    gin = gout = nullptr;
+    gsize = 0;
     nu = std::max(1, o.amg_nu);
     smoother = o.amg_smoother;
     degree = std::max(1, o.amg_degree);
@@ -474,9 +494,69 @@ struct Hierarchy {
     if (cur != out) copy<T>(cur, out, L.n * nrhs, s);
   }
 
+  // record one V-cycle (gin -> gout) as a CUDA graph; on any failure the
+  // hierarchy keeps running V-cycles eagerly
+  template <typename T>
+  void capture(cudaStream_t s) {
+    const long long n = lv[0].n * nrhs;
+    T* in = arena->alloc<T>(n + 1);
+    T* out = arena->alloc<T>(n + 1);
+    fill<T>(in, (T)0, n, s);
+    // an eager V-cycle first: kernels configured on first use are set up
+    // outside the capture
+    cycle<T>(0, in, out, s);
+    SCR_CUDA(cudaStreamSynchronize(s));
+    const long long l0 = counters().launches, b0 = counters().spmv_bytes;
+    // recorded on a private stream (the caller's stream may be the legacy
+    // default stream, which cannot be captured); replayed on the caller's
+    cudaStream_t cs = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      try {
+        cycle<T>(0, in, out, cs);
+      } catch (const CudaError&) {
+        e = cudaErrorStreamCaptureInvalidated;
+      }
+      const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+      if (e == cudaSuccess) e = e2;
+    }
+    if (cs) cudaStreamDestroy(cs);
+    glaunches = counters().launches - l0;
+    gbytes = counters().spmv_bytes - b0;
+    counters().launches = l0;  // the captured work has not run yet
+    counters().spmv_bytes = b0;
+    cudaGraphExec_t ex = nullptr;
+    if (e == cudaSuccess && g) e = cudaGraphInstantiate(&ex, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess || !ex) {
+      cudaGetLastError();
+      graph_failed = true;
+      return;
+    }
+    gexec.reset(ex);
+    gin = in;
+    gout = out;
+    gsize = sizeof(T);
+  }
+
   template <typename T>
   void apply(const T* b, T* x, cudaStream_t s) {
     ++vcycles;
+    // the per-launch event profiler needs the launches themselves
+    if (use_graph && !graph_failed && !profiler().active) {
+      if (!gexec) capture<T>(s);
+      if (gexec && gsize == sizeof(T)) {
+        const long long n = lv[0].n * nrhs;
+        copy<T>(b, static_cast<T*>(gin), n, s);
+        SCR_CUDA(cudaGraphLaunch(gexec.get(), s));
+        copy<T>(static_cast<const T*>(gout), x, n, s);
+        counters().launches += glaunches;
+        counters().spmv_bytes += gbytes;
+        return;
+      }
+    }
     cycle<T>(0, b, x, s);
   }
 };
@@ -906,6 +986,7 @@ int scr_default_opts(scr_opts* o) {
   o->stages = 2;
   o->l2_prefetch = 192;
   o->amg_coarse_bf16 = 1;
+  o->cuda_graphs = 1;
   o->mm_rtol = 1e-8;
   o->mm_max_it = 500;
   o->verbose = 0;

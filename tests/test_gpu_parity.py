@@ -318,6 +318,32 @@ def test_block_solve_with_staged_products_matches_direct(small, small_direct, pr
 
 
 @pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
+def test_cuda_graph_vcycles_equal_eager_vcycles(small, precision):
+    """A V-cycle replayed from its CUDA graph launches the same kernels with
+    the same arguments as the eager V-cycle: V-cycles of A, Shat and L (each
+    applied twice, so the second runs from the graph) and a whole solve are
+    bit-identical with and without graphs, and the launch counter still
+    counts the replayed kernels."""
+    res = {}
+    for graphs in (0, 1):
+        with pkg.BlockSolver(cuda_graphs=graphs, precision=precision) as sol:
+            sol.setup(small.A, small.B, small.C, small.D)
+            sol.mesh_setup(small.L)
+            first = _three_vcycles(sol, small)
+            l0 = sol.stats()["kernel_launches"]
+            second = _three_vcycles(sol, small)
+            launched = sol.stats()["kernel_launches"] - l0
+            x = sol.solve(small.b.copy())
+            res[graphs] = (first, second, x, launched, sol.iters())
+    for a, b in zip(res[0][0] + res[0][1], res[1][0] + res[1][1]):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(res[0][2], res[1][2])
+    assert res[0][4] == res[1][4]
+    # three replayed V-cycles: the eager kernels plus one copy in and one out each
+    assert res[1][3] == res[0][3] + 2 * 3
+
+
+@pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
 def test_l2_prefetch_changes_no_result(small, precision):
     """The bulk L2 prefetch of the scalar-row products only moves data into
     L2: V-cycles are bit-identical with it off, 1 CTA ahead and 192 ahead
