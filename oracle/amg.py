@@ -53,6 +53,7 @@ class Level:
     omega: float = 0.0
     dinv: np.ndarray | None = None   # 1 / diag(A)
     lam: float = 0.0                 # 1.1 x power-iteration estimate of rho(D^{-1} A)
+    cheb: bool = True                # Chebyshev smoothing on this level (else l1-Jacobi)
 
 
 @dataclasses.dataclass
@@ -274,11 +275,34 @@ def l1_diag(A: sp.csr_matrix) -> np.ndarray:
     return np.asarray(abs(A).sum(axis=1)).ravel()
 
 
-def _finish_levels(levels, smoother: str):
-    for lev in levels:
+# Chebyshev guard: the smoother's error propagation is run CHEB_GUARD_SWEEPS
+# times on the homogeneous problem from the normalised power-iteration start
+# vector; a level whose error grows beyond CHEB_GUARD_GROWTH uses l1-Jacobi
+# instead (nonsymmetric coarse operators, e.g. Galerkin levels of Shat, can
+# have eigenvalues of D^{-1} A off the interval [lam/30, lam], where the
+# polynomial amplifies instead of damping).
+CHEB_GUARD_SWEEPS = 5
+CHEB_GUARD_GROWTH = 10.0
+
+
+def cheb_guard_growth(A: sp.csr_matrix, dinv: np.ndarray, lam: float, degree: int) -> float:
+    """||e_5|| for e_0 = the normalised start vector, e_{k+1} = the
+    Chebyshev smoother applied to A e = 0 from e_k."""
+    e = power_start(A.shape[0])
+    e = e / np.linalg.norm(e)
+    zero = np.zeros_like(e)
+    for _ in range(CHEB_GUARD_SWEEPS):
+        e = cheb_smooth(A, dinv, lam, degree, e, zero, False)
+    return float(np.linalg.norm(e))
+
+
+def _finish_levels(levels, smoother: str, cheb_degree: int = 3):
+    for l, lev in enumerate(levels):
         lev.dinv = 1.0 / lev.A.diagonal()
         if smoother == "cheb":
             lev.lam = power_lambda(lev.A, lev.dinv)
+            if l + 1 < len(levels):
+                lev.cheb = cheb_guard_growth(lev.A, lev.dinv, lev.lam, cheb_degree) <= CHEB_GUARD_GROWTH
 
 
 def setup(A: sp.csr_matrix, bs: int, theta: float = 0.08, max_levels: int = 10,
@@ -308,7 +332,7 @@ def setup(A: sp.csr_matrix, bs: int, theta: float = 0.08, max_levels: int = 10,
         lev.P, lev.R, lev.agg, lev.omega = P, R, agg, omega
         Al = Ac
     lu = sla.lu_factor(levels[-1].A.toarray())
-    _finish_levels(levels, smoother)
+    _finish_levels(levels, smoother, cheb_degree)
     return Hierarchy(levels=levels, coarse_lu=lu, nu_pre=nu_pre, nu_post=nu_post, smoother=smoother,
                      cheb_degree=cheb_degree)
 
@@ -326,7 +350,7 @@ def hierarchy_from_matrices(As, Ps, bs: int, nu_pre: int = 1, nu_post: int = 1, 
             lev.R = lev.P.T.tocsr()
         levels.append(lev)
     lu = sla.lu_factor(levels[-1].A.toarray())
-    _finish_levels(levels, smoother)
+    _finish_levels(levels, smoother, cheb_degree)
     return Hierarchy(levels=levels, coarse_lu=lu, nu_pre=nu_pre, nu_post=nu_post, smoother=smoother,
                      cheb_degree=cheb_degree)
 
@@ -337,7 +361,7 @@ def vcycle(H: Hierarchy, b: np.ndarray, level: int = 0) -> np.ndarray:
     b = np.asarray(b, dtype=np.float64)
     if level == H.n_levels - 1:
         return sla.lu_solve(H.coarse_lu, b)
-    if H.smoother == "cheb":
+    if H.smoother == "cheb" and lev.cheb:
         x = cheb_smooth(lev.A, lev.dinv, lev.lam, H.cheb_degree, None, b, True)
         r = b - lev.A @ x
         x = x + lev.P @ vcycle(H, lev.R @ r, level + 1)

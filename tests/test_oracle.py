@@ -462,3 +462,38 @@ def test_simplec_full_solve_matches_direct(mini_system, mini_direct):
     assert info.converged
     assert s.rel_residual(x, mini_system.b) <= 1e-8
     assert np.linalg.norm(x - mini_direct) <= 1e-6 * np.linalg.norm(mini_direct)
+
+
+# ------------------------------------------------------------- Chebyshev guard
+def test_cheb_guard_keeps_chebyshev_on_spd_and_switches_on_rotation():
+    """The guard's test (5 homogeneous Chebyshev sweeps from the fixed start
+    vector) contracts for a 1D Laplacian and blows up for a matrix whose
+    D^{-1} A has complex eigenvalues 1 +- a i (2x2 rotation blocks), far off
+    the real interval the polynomial damps."""
+    n = 200
+    T = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]).tocsr()
+    d = 1.0 / T.diagonal()
+    assert amg.cheb_guard_growth(T, d, amg.power_lambda(T, d), 3) <= 1.0
+    for a in (0.5, 3.0):
+        R = sp.block_diag([sp.csr_matrix(np.array([[1.0, a], [-a, 1.0]]))] * (n // 2)).tocsr()
+        d = 1.0 / R.diagonal()
+        assert amg.cheb_guard_growth(R, d, amg.power_lambda(R, d), 3) > amg.CHEB_GUARD_GROWTH
+
+
+def test_cheb_guard_decisions_on_the_tube(tiny_system):
+    """Default tube: every level of every hierarchy keeps Chebyshev; a stiff,
+    heavy wall (rho_s = 100) makes level 1 of the Shat hierarchy switch to
+    l1-Jacobi, and the preconditioned GMRES on Shat then converges."""
+    s = F.tube_system("tube_small")
+    op = BlockOperator.from_system(s)
+    for M, bs in ((op.A, 3), (schur.schur_hat(op), 1), (to_csr(s.L), 1)):
+        H = amg.setup(M, bs, 0.08, 10, 64, 1, 1, 0.3, 5, "cheb", 3)
+        assert all(lv.cheb for lv in H.levels[:-1])
+    s = F.tube_system("tube_small", rho_s=100.0)
+    Sh = schur.schur_hat(BlockOperator.from_system(s))
+    H = amg.setup(Sh, 1, 0.08, 10, 64, 1, 1, 0.3, 5, "cheb", 3)
+    assert [lv.cheb for lv in H.levels[:-1]] == [True, False, True]
+    b = np.random.default_rng(0).standard_normal(Sh.shape[0])
+    _, info = krylov.gmres(lambda v: Sh @ v, b, lambda v: amg.vcycle(H, v), tol=1e-3, maxit=200, restart=30)
+    assert info.converged
+    del tiny_system
