@@ -158,6 +158,17 @@ __global__ void k_rsqrt_scalar(const double* __restrict__ in, double* __restrict
   *out = v > 0.0 ? 1.0 / sqrt(v) : 0.0;
 }
 
+void power_start_unit(double* v, long long n, const Reducer& red, double* nrm, cudaStream_t s) {
+  if (n == 0) return;
+  k_power_start<<<ceil_div(n, 256), 256, 0, s>>>(v, n);
+  SCR_LAUNCH();
+  norm2<double>(v, n, nrm, red, s);
+  k_rsqrt_scalar<<<1, 1, 0, s>>>(nrm, nrm + 1);
+  SCR_LAUNCH();
+  scale_by<double>(v, nrm + 1, v, n, s);
+  counters().launches += 2;
+}
+
 double power_lambda(const DBsr<double>& A, const double* dinv, int iters, cudaStream_t s) {
   const long long n = (long long)A.nbr * A.br;
   if (n == 0) return 0.0;

@@ -217,6 +217,9 @@ void inv_diag(const DBsr<double>& A, double* dinv, cudaStream_t s);
 double power_lambda(const DBsr<double>& A, const double* dinv, int iters, cudaStream_t s);
 // 1/ sum_j |a_ij| per scalar row
 void l1_inv(const DBsr<double>& A, double* dinv, cudaStream_t s);
+// v = the power-iteration start vector 1 + ((i * 2654435761) mod 2^32 mod
+// 1000) / 1000, normalised; nrm: 2 doubles of scratch
+void power_start_unit(double* v, long long n, const Reducer& red, double* nrm, cudaStream_t s);
 // d_i = sum_j |a_ij| per scalar row (SIMPLEC's lumped diagonal)
 void abs_rowsum(const DBsr<double>& A, double* d, cudaStream_t s);
 // max_i sum_j |a_ij| / |a_ii| (device scalar)

@@ -75,6 +75,7 @@ struct Level {
   double* dd = nullptr;     // Chebyshev: 1 / a_ii
   float* ddf = nullptr;
   double lam = 0.0;         // Chebyshev interval [lam/30, lam]
+  bool cheb_off = false;    // the Chebyshev guard switched this level to l1-Jacobi
   double *d0 = nullptr, *d1 = nullptr;
   float *d0f = nullptr, *d1f = nullptr;
   int* agg = nullptr;
@@ -267,6 +268,9 @@ struct Hierarchy {
         L.dd = ar.alloc<double>(L.n + 1);
         inv_diag(L.A, L.dd, s);
         L.lam = power_lambda(L.A, L.dd, 20, s);
+        L.cheb_off = cheb_guard_growth(L, s) > kChebGuardGrowth;
+        if (o.verbose && L.cheb_off)
+          fprintf(stderr, "[amg bs=%d] level %zu: Chebyshev guard -> l1-Jacobi\n", bs, l);
         if (f32) {
           L.ddf = ar.alloc<float>(L.n + 1);
           cast_d2f(L.dd, L.ddf, L.n, s);
@@ -349,6 +353,63 @@ struct Hierarchy {
   template <typename T>
   const T* dv(Level& L) {
     if constexpr (sizeof(T) == 8) return L.dinv; else return L.dinvf;
+  }
+
+  // Chebyshev guard: the smoother's error propagation run kChebGuardSweeps
+  // times on the homogeneous problem (FP64, level operator and inverse
+  // diagonal of the set-up) from the normalised power-iteration start
+  // vector; returns ||e||.  A level whose error grows beyond
+  // kChebGuardGrowth is smoothed by l1-Jacobi instead: nonsymmetric coarse
+  // operators (Galerkin levels of Shat with a heavy, stiff wall) can have
+  // eigenvalues of D^{-1}A off [lam/30, lam], where the polynomial amplifies.
+  static constexpr int kChebGuardSweeps = 5;
+  static constexpr double kChebGuardGrowth = 10.0;
+  double cheb_guard_growth(Level& L, cudaStream_t s) {
+    const long long n = L.n;
+    DeviceArena tmp(s);
+    Reducer red = make_reducer(tmp);
+    double* e = tmp.alloc<double>(n + 1);
+    double* out = tmp.alloc<double>(n + 1);
+    double* r = tmp.alloc<double>(n + 1);
+    double* d0 = tmp.alloc<double>(n + 1);
+    double* d1 = tmp.alloc<double>(n + 1);
+    double* zero = tmp.alloc<double>(n + 1);
+    double* nrm = tmp.alloc<double>(2);
+    fill<double>(zero, 0.0, n, s);
+    power_start_unit(e, n, red, nrm, s);
+    double inv_theta;
+    std::vector<std::pair<double, double>> st;
+    cheb_coeffs(L.lam, degree, &inv_theta, st);
+    for (int k = 0; k < kChebGuardSweeps; ++k) {
+      EpiArgs f;
+      f.kind = Epi::ChebFirst;
+      f.alpha = inv_theta;
+      f.z = zero;
+      f.xs = e;
+      f.dinv = L.dd;
+      f.r = r;
+      f.dout = d0;
+      spmv<double, double>(L.A, e, out, 1, f, s);
+      double *a = d0, *b = d1;
+      EpiArgs g;
+      g.kind = Epi::ChebStep;
+      g.dinv = L.dd;
+      g.r = r;
+      for (auto& ab : st) {
+        g.alpha = ab.first;
+        g.beta = ab.second;
+        g.dout = b;
+        g.xsol = out;
+        spmv<double, double>(L.A, a, b, 1, g, s);
+        std::swap(a, b);
+      }
+      std::swap(e, out);
+    }
+    norm2<double>(e, n, nrm, red, s);
+    double h = 0.0;
+    SCR_CUDA(cudaMemcpyAsync(&h, nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+    SCR_CUDA(cudaStreamSynchronize(s));
+    return std::sqrt(h);
   }
 
   // Chebyshev coefficients on [lam/30, lam]: 1/theta and (alpha_j, beta_j)
@@ -447,7 +508,7 @@ struct Hierarchy {
       else dense_apply_f(cinvf, b, out, nc, nrhs, s);
       return;
     }
-    if (smoother == SCR_SMOOTH_CHEB) {
+    if (smoother == SCR_SMOOTH_CHEB && !L.cheb_off) {
       cycle_cheb<T>(l, b, out, s);
       return;
     }

@@ -247,6 +247,25 @@ def test_mixed_solve_with_fp32_coarse_levels(small, small_direct):
         pkg.BlockSolver(amg_coarse_bf16=2)
 
 
+def test_vcycle_with_chebyshev_guard_matches_oracle():
+    """Heavy, stiff wall (rho_s = 100): a Galerkin level of the Shat hierarchy
+    fails the Chebyshev guard on both sides and is smoothed by l1-Jacobi; the
+    GPU V-cycle equals the oracle's on the exported hierarchy (whose guard
+    takes the same per-level decisions) and a Shat solve converges."""
+    s = F.tube_system("tube_small", rho_s=100.0)
+    with pkg.BlockSolver() as sol:
+        sol.setup(s.A, s.B, s.C, s.D)
+        which = pkg.SCR_HIER_SHAT
+        nl = sol.amg_levels(which)
+        As = [to_csr(sol.export(which, l, pkg.SCR_EXPORT_OPERATOR)) for l in range(nl)]
+        Ps = [to_csr(sol.export(which, l, pkg.SCR_EXPORT_PROLONGATOR)) for l in range(nl - 1)]
+        b = np.random.default_rng(4).standard_normal(As[0].shape[0])
+        x = sol.amg_apply(which, _dev(b)).cpu().numpy()
+    H = amg.hierarchy_from_matrices(As, Ps, 1, 1, 1, "cheb", 3)
+    assert not all(lv.cheb for lv in H.levels[:-1])
+    assert _rel(x, amg.vcycle(H, b)) < 1e-11
+
+
 @pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
 def test_sliced_ell_products_match_slab_products(small, precision):
     """The sliced block-ELL copies of A, Shat and L give the same V-cycles as
