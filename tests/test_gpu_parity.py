@@ -688,6 +688,22 @@ def test_time_step_trends_scr_versus_simple():
     assert inner[(1e-3, pkg.SCR_PC_SCR)] > inner[(1e-4, pkg.SCR_PC_SCR)], inner
 
 
+def test_smallest_time_step_converges_with_the_guard():
+    """dt = 1e-5 (the smallest step of Sec. 6's time-step study): the Galerkin
+    levels of the Shat hierarchy fail the Chebyshev guard and are smoothed by
+    l1-Jacobi; SCR and SIMPLEC then reach the tolerance (CPU oracle: 13 and
+    18 outer iterations; SIMPLE still stalls, as every Shat solve hits its
+    iteration cap)."""
+    s = F.tube_system("tube_small", dt=1e-5)
+    op = BlockOperator.from_system(s)
+    for pc in (pkg.SCR_PC_SCR, pkg.SCR_PC_SIMPLEC):
+        with pkg.BlockSolver(precond=pc) as sol:
+            sol.setup(s.A, s.B, s.C, s.D)
+            x = sol.solve(s.b.copy())
+            assert sol.iters()[0] <= 40
+        assert rel_residual(op, x, s.b) <= 1e-8
+
+
 @pytest.mark.parametrize("rho_s,E_s", [(1e-2, 4e6), (1e2, 4e6), (1.0, 1e6), (1.0, 1e8)])
 def test_wall_parameter_robustness(rho_s, E_s):
     """Robustness over the wall density and Young's modulus (Sec. 6, table of
