@@ -123,6 +123,8 @@ typedef struct {
                          staging vectors) for every later V-cycle; 0: every V-cycle launched
                          kernel by kernel.  V-cycles run kernel by kernel while scr_profile_begin
                          is active.  Results are the same either way. */
+  int nrhs;           /* right-hand sides of the block solve: 1 (default, scr_solve) or 8
+                         (scr_solve_multi: the block products act on 8 interleaved vectors at once) */
   double mm_rtol;     /* mesh CG relative residual, 1e-8 */
   int mm_max_it;      /* mesh CG iteration cap, 500 */
   int verbose;        /* 0 quiet */
@@ -213,6 +215,24 @@ int scr_iters(scr_handle h, int* outer, int* inner_total);
 
 /* FP64 ||b - calA x||_2 / ||b||_2 of the last scr_solve. */
 int scr_residual(scr_handle h, double* rel_res);
+
+/* Several right-hand sides with one set-up (the block product form of the
+   multi-right-hand-side solve): for a handle created with nrhs = 8, solves
+   calA x_c = b_c for c = 0..7.  b and x are arrays of 8 pointers to vectors
+   laid out as for scr_solve (host pointers when dev == 0, device pointers
+   otherwise; the caller owns them).  Inside, the right-hand sides are
+   interleaved (entry i of b_c at i * 8 + c), so every product with A, B, C,
+   D, Shat and the AMG levels reads the stored blocks once for all eight
+   columns; one FGMRES runs on the interleaved system with the tolerance
+   rtol * min_c ||b_c|| / ||b||, which bounds every column's relative
+   residual by rtol.  rel_res (8 doubles, may be NULL) receives each
+   column's FP64 ||b_c - calA x_c|| / ||b_c||.  Returns SCR_NOT_CONVERGED if
+   a column misses rtol; SCR_INVALID_ARG before scr_setup or for NULL
+   pointers.  With nrhs = 1 it solves one right-hand side like scr_solve.
+   scr_solve, scr_setup_batch, scr_apply_* and scr_amg_apply on the block
+   hierarchies take nrhs = 1 handles only.  Not in the paper: the
+   multi-right-hand-side form is an addition of this library. */
+int scr_solve_multi(scr_handle h, const double* const* b, double* const* x, int dev, double* rel_res);
 
 /* Counters and timings (see scr_stats). */
 int scr_get_stats(scr_handle h, scr_stats* s);

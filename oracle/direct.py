@@ -27,3 +27,11 @@ def solve_mesh(s) -> np.ndarray:
     lu = spl.splu(L, permc_spec="MMD_AT_PLUS_A")
     g = np.asarray(s.mesh_b, dtype=np.float64).reshape(-1, 3)
     return np.column_stack([lu.solve(g[:, c].copy()) for c in range(3)]).reshape(-1)
+
+
+def solve_block_many(s, rhs) -> list[np.ndarray]:
+    """x*_c with calA x*_c = b_c for several right-hand sides of one block
+    system (one LU, one solve per column)."""
+    op = BlockOperator.from_system(s)
+    lu = spl.splu(op.full().tocsc(), permc_spec="MMD_ATA")
+    return [lu.solve(np.asarray(b, dtype=np.float64)) for b in rhs]

@@ -33,6 +33,7 @@ class Opts(C.Structure):
         ("amg_smoother", C.c_int), ("amg_degree", C.c_int), ("spmv_group", C.c_int),
         ("sell", C.c_int), ("staged", C.c_int), ("stage_kb", C.c_int), ("stages", C.c_int),
         ("l2_prefetch", C.c_int), ("amg_coarse_bf16", C.c_int), ("cuda_graphs", C.c_int),
+        ("nrhs", C.c_int),
         ("mm_rtol", C.c_double), ("mm_max_it", C.c_int), ("verbose", C.c_int),
     ]
 
@@ -75,6 +76,7 @@ EXPORTED = [
     "scr_apply_op", "scr_apply_pc", "scr_apply_schur", "scr_amg_apply", "scr_amg_levels",
     "scr_export", "scr_bsr_spmv", "scr_profile_begin", "scr_profile_end", "scr_bsr_spmv_noalloc",
     "scr_setup_batch", "scr_solve_batch", "scr_batch_residuals", "scr_tune_save", "scr_tune_load",
+    "scr_solve_multi",
 ]
 
 _lib = None

@@ -74,6 +74,24 @@ template void copy<double>(const double*, double*, long long, cudaStream_t);
 template void copy<float>(const float*, float*, long long, cudaStream_t);
 template void copy<int>(const int*, int*, long long, cudaStream_t);
 
+// k vectors of length n stored one after another (in[c * n + i]) <->
+// interleaved (out[i * k + c])
+__global__ void k_interleave(const double* __restrict__ in, double* __restrict__ out, long long n, int k,
+                             int to_interleaved) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= n * k) return;
+  const long long i = t / k, c = t - i * k;  // t walks the interleaved layout
+  if (to_interleaved) out[t] = in[c * n + i];
+  else out[c * n + i] = in[t];
+}
+
+void interleave(const double* in, double* out, long long n, int k, bool to_interleaved, cudaStream_t s) {
+  if (n * k == 0) return;
+  k_interleave<<<ceil_div(n * k, 256), 256, 0, s>>>(in, out, n, k, to_interleaved ? 1 : 0);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
 void cast_d2f(const double* x, float* y, long long n, cudaStream_t s) {
   if (n <= 0) return;
   k_d2f_b<<<grid_for(n), 256, 0, s>>>(x, y, n);

@@ -72,6 +72,13 @@ struct EpiArgs {
 template <typename VT, typename XT>
 void spmv(const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const EpiArgs& e, cudaStream_t s);
 
+// Block products with kSpmmCols interleaved right-hand sides (x[(j * bc +
+// c) * kSpmmCols + h], y likewise), any block shape of the solver
+// (spmm.cu); called by spmv for nrhs == kSpmmCols.
+constexpr int kSpmmCols = 8;
+template <typename VT, typename XT>
+void spmm_launch(int G, const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& e, cudaStream_t s);
+
 // build the sliced block-ELL copy of M (values converted to VT)
 template <typename VT>
 void build_sell(const DBsr<double>& M, DSell<VT>& S, DeviceArena& a, cudaStream_t s, int window);
@@ -106,10 +113,11 @@ bool spmv_staged(int G, const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const E
 // stage wait ran out; 2: a tile exceeded its stage), cleared on read
 int staged_status_take(cudaStream_t s);
 
-// y = epilogue([[A, B], [C, D]] x) in FP64 (the outer operator calA)
+// y = epilogue([[A, B], [C, D]] x) in FP64 (the outer operator calA); nrhs
+// interleaved right-hand sides (1 or kSpmmCols)
 void block_op(const DBsr<double>& A, const DBsr<double>& B, const DBsr<double>& C,
               const DBsr<double>& D, const double* x, double* y, const double* z, bool resid,
-              cudaStream_t s);
+              cudaStream_t s, int nrhs = 1);
 
 // --------------------------------------------------------------- BLAS-1
 constexpr int kMaxBasis = 64;  // largest restart length + 1
@@ -134,6 +142,9 @@ void cast_d2f(const double* x, float* y, long long n, cudaStream_t s);
 void cast_f2d(const float* x, double* y, long long n, cudaStream_t s);
 // y = a*x + b*y
 void axpby(double a, const double* x, double b, double* y, long long n, cudaStream_t s);
+// k vectors of length n one after another <-> interleaved (entry i of vector c
+// at i * k + c)
+void interleave(const double* in, double* out, long long n, int k, bool to_interleaved, cudaStream_t s);
 template <typename T>
 void axpby_t(double a, const T* x, double b, T* y, long long n, cudaStream_t s);
 // x[o*nrhs+h] = b[o*nrhs+h] * d[o]  (l1-Jacobi sweep from a zero iterate)

@@ -748,6 +748,11 @@ struct scr_ctx {
   HostScalars mhs;
   scr_stats stats;
   int counters_outer = 0;
+  // interleaved right-hand sides of the block solve (options.nrhs): every
+  // vector of the block path holds k of them, entry i of right-hand side c
+  // at i * k + c, and every product acts as M (x) I_k
+  int k = 1;
+  double* mstage = nullptr;  // k vectors one after another (multi-right-hand-side staging)
   // batched form: member sizes and offsets inside the union system
   int nbatch = 0;
   std::vector<int> b_nv, b_np, b_vo, b_po;
@@ -895,32 +900,32 @@ PcView<float> view32(scr_ctx* h) {
 template <typename T>
 void apply_S(scr_ctx* h, PcView<T>& v, const T* xp, T* yp) {
   cudaStream_t s = h->s;
-  spmv<T, T>(*v.B, xp, v.xbar, 1, EpiArgs(), s);
-  typename Gmres<T>::Op opA = [&](const T* x, T* y) { spmv<T, T>(*v.A, x, y, 1, EpiArgs(), s); };
+  spmv<T, T>(*v.B, xp, v.xbar, h->k, EpiArgs(), s);
+  typename Gmres<T>::Op opA = [&](const T* x, T* y) { spmv<T, T>(*v.A, x, y, h->k, EpiArgs(), s); };
   typename Gmres<T>::Op pcA = [&](const T* b, T* x) { v.hA->template apply<T>(b, x, s); };
   int it = 0;
   double rel = 0;
   v.gI->solve(opA, &pcA, v.xbar, v.xt, h->o.rtol_I, h->o.max_I, h->red, s, &it, &rel);
   h->stats.i_iters += it;
-  spmv<T, T>(*v.D, xp, yp, 1, EpiArgs(), s);
+  spmv<T, T>(*v.D, xp, yp, h->k, EpiArgs(), s);
   EpiArgs sub;
   sub.kind = Epi::Axpby;
   sub.alpha = -1.0;
   sub.beta = 1.0;
   sub.z = yp;
-  spmv<T, T>(*v.C, v.xt, yp, 1, sub, s);
+  spmv<T, T>(*v.C, v.xt, yp, h->k, sub, s);
 }
 
 // Algorithm 1: y = P_SCR^{-1} r
 template <typename T>
 void apply_pc(scr_ctx* h, PcView<T>& v, const T* r, T* y) {
   cudaStream_t s = h->s;
-  const long long nv3 = 3LL * h->nv;
+  const long long nv3 = 3LL * h->nv * h->k;
   const T* rv = r;
   const T* rp = r + nv3;
   T* yv = y;
   T* yp = y + nv3;
-  typename Gmres<T>::Op opA = [&](const T* x, T* o) { spmv<T, T>(*v.A, x, o, 1, EpiArgs(), s); };
+  typename Gmres<T>::Op opA = [&](const T* x, T* o) { spmv<T, T>(*v.A, x, o, h->k, EpiArgs(), s); };
   typename Gmres<T>::Op pcA = [&](const T* b, T* x) { v.hA->template apply<T>(b, x, s); };
   typename Gmres<T>::Op opS = [&](const T* x, T* o) { apply_S<T>(h, v, x, o); };
   typename Gmres<T>::Op pcS = [&](const T* b, T* x) { v.hS->template apply<T>(b, x, s); };
@@ -936,13 +941,13 @@ void apply_pc(scr_ctx* h, PcView<T>& v, const T* r, T* y) {
   e.alpha = -1.0;
   e.beta = 1.0;
   e.z = rp;
-  spmv<T, T>(*v.C, v.yhat, v.rp2, 1, e, s);
+  spmv<T, T>(*v.C, v.yhat, v.rp2, h->k, e, s);
   // 3. S y_p = r_p
   v.gS->solve(opS, &pcS, v.rp2, yp, h->o.rtol_S, h->o.max_S, h->red, s, &it, &rel);
   h->stats.s_iters += it;
   // 4. r_v <- r_v - B y_p
   e.z = rv;
-  spmv<T, T>(*v.B, yp, v.rv2, 1, e, s);
+  spmv<T, T>(*v.B, yp, v.rv2, h->k, e, s);
   // 5. A y_v = r_v
   v.gA->solve(opA, &pcA, v.rv2, yv, h->o.rtol_A, h->o.max_A, h->red, s, &it, &rel);
   h->stats.a_solves++;
@@ -956,14 +961,14 @@ void apply_pc(scr_ctx* h, PcView<T>& v, const T* r, T* y) {
 template <typename T>
 void apply_simple(scr_ctx* h, PcView<T>& v, const T* r, T* y) {
   cudaStream_t s = h->s;
-  const long long nv3 = 3LL * h->nv;
+  const long long nv3 = 3LL * h->nv * h->k;
   const T* rv = r;
   const T* rp = r + nv3;
   T* yv = y;
   T* yp = y + nv3;
-  typename Gmres<T>::Op opA = [&](const T* x, T* o) { spmv<T, T>(*v.A, x, o, 1, EpiArgs(), s); };
+  typename Gmres<T>::Op opA = [&](const T* x, T* o) { spmv<T, T>(*v.A, x, o, h->k, EpiArgs(), s); };
   typename Gmres<T>::Op pcA = [&](const T* b, T* x) { v.hA->template apply<T>(b, x, s); };
-  typename Gmres<T>::Op opS = [&](const T* x, T* o) { spmv<T, T>(*v.Shat, x, o, 1, EpiArgs(), s); };
+  typename Gmres<T>::Op opS = [&](const T* x, T* o) { spmv<T, T>(*v.Shat, x, o, h->k, EpiArgs(), s); };
   typename Gmres<T>::Op pcS = [&](const T* b, T* x) { v.hS->template apply<T>(b, x, s); };
   int it = 0;
   double rel = 0;
@@ -975,20 +980,20 @@ void apply_simple(scr_ctx* h, PcView<T>& v, const T* r, T* y) {
   e.alpha = -1.0;
   e.beta = 1.0;
   e.z = rp;
-  spmv<T, T>(*v.C, v.yhat, v.rp2, 1, e, s);
+  spmv<T, T>(*v.C, v.yhat, v.rp2, h->k, e, s);
   v.gS->solve(opS, &pcS, v.rp2, yp, h->o.rtol_S, h->o.max_S, h->red, s, &it, &rel);
   h->stats.s_iters += it;
   EpiArgs u;
   u.kind = Epi::ScaledSub;
   u.z = v.yhat;
   u.dinv = v.dAinv;
-  spmv<T, T>(*v.B, yp, yv, 1, u, s);
+  spmv<T, T>(*v.B, yp, yv, h->k, u, s);
 }
 
 void apply_pc_any(scr_ctx* h, const double* r, double* y) {
   const bool simple = h->o.precond == SCR_PC_SIMPLE || h->o.precond == SCR_PC_SIMPLEC;
   if (h->o.precision == SCR_MIXED) {
-    const long long n = 3LL * h->nv + h->np;
+    const long long n = (3LL * h->nv + h->np) * h->k;
     cast_d2f(r, h->pr, n, h->s);
     PcView<float> v = view32(h);
     if (simple) apply_simple<float>(h, v, h->pr, h->py);
@@ -1002,8 +1007,8 @@ void apply_pc_any(scr_ctx* h, const double* r, double* y) {
 }
 
 double true_rel_block(scr_ctx* h, const double* b, const double* x) {
-  const long long n = 3LL * h->nv + h->np;
-  block_op(h->A, h->B, h->C, h->D, x, h->rvec, b, true, h->s);
+  const long long n = (3LL * h->nv + h->np) * h->k;
+  block_op(h->A, h->B, h->C, h->D, x, h->rvec, b, true, h->s, h->k);
   ArnoldiState* st = h->gOuter.st;
   norm2<double>(h->rvec, n, &st->nrm2, h->red, h->s);
   double r2 = 0, b2 = 0;
@@ -1048,6 +1053,7 @@ int scr_default_opts(scr_opts* o) {
   o->l2_prefetch = 192;
   o->amg_coarse_bf16 = 1;
   o->cuda_graphs = 1;
+  o->nrhs = 1;
   o->mm_rtol = 1e-8;
   o->mm_max_it = 500;
   o->verbose = 0;
@@ -1075,6 +1081,7 @@ int scr_create(scr_handle* out, const scr_opts* o, void* stream) {
     if (op.staged && (op.stage_kb < 4 || op.stage_kb > 96 || op.stages < 2 || op.stages > 4))
       throw std::invalid_argument("staged products: stage_kb must lie in [4, 96] and stages in [2, 4]");
     if (op.l2_prefetch < 0) throw std::invalid_argument("l2_prefetch must be >= 0");
+    if (op.nrhs != 1 && op.nrhs != kSpmmCols) throw std::invalid_argument("nrhs must be 1 or 8");
     if (op.amg_coarse_bf16 != 0 && op.amg_coarse_bf16 != 1) throw std::invalid_argument("amg_coarse_bf16 must be 0 or 1");
     std::unique_ptr<scr_ctx> h(new scr_ctx());
     h->o = op;
@@ -1123,6 +1130,8 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
     DeviceArena& a = *h->mats;
     h->nv = nv;
     h->np = np;
+    h->k = h->o.nrhs;
+    h->mstage = nullptr;
     h->A = upload(A, dev, a, s);
     h->B = upload(B, dev, a, s);
     h->C = upload(C, dev, a, s);
@@ -1174,8 +1183,8 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
     }
     if (h->o.verbose)
       fprintf(stderr, "[setup] lane groups: A %d, Shat %d, A(fp32) %d\n", h->A.g, h->Shat.g, h->Af.g);
-    h->hA.build(h->A, 3, 1, h->o, f32, s, f32 ? &h->Af : nullptr);
-    h->hS.build(h->Shat, 1, 1, h->o, f32, s);
+    h->hA.build(h->A, 3, h->k, h->o, f32, s, f32 ? &h->Af : nullptr);
+    h->hS.build(h->Shat, 1, h->k, h->o, f32, s);
     if (f32 && h->o.sell && h->hS.n_levels() > 0) {
       build_sell<float>(h->Shat, h->Shatf_sell, a, s, h->o.sell);
       h->hS.lv[0].Af.sell = &h->Shatf_sell;
@@ -1184,16 +1193,18 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
     h->work.reset(new DeviceArena(s));
     DeviceArena& w = *h->work;
     h->red = make_reducer(w);
-    const long long n = 3LL * nv + np, nv3 = 3LL * nv;
+    const int k = h->k;
+    const long long n = (3LL * nv + np) * k, nv3 = 3LL * nv * k;
     h->gOuter.init(w, n, h->o.restart);
+    if (k > 1) h->mstage = w.alloc<double>(n + 1);
     h->bvec = w.alloc<double>(n + 1);
     h->xvec = w.alloc<double>(n + 1);
     h->rvec = w.alloc<double>(n + 1);
     if (f32) {
-      h->dAinvf = w.alloc<float>(nv3 + 1);
-      cast_d2f(h->dAinv, h->dAinvf, nv3, s);
+      h->dAinvf = w.alloc<float>(3LL * nv + 1);
+      cast_d2f(h->dAinv, h->dAinvf, 3LL * nv, s);
       h->gAf.init(w, nv3, h->o.restart_inner);
-      h->gSf.init(w, np, h->o.restart_inner);
+      h->gSf.init(w, (long long)np * k, h->o.restart_inner);
       h->gIf.init(w, nv3, h->o.restart_inner);
       h->pr = w.alloc<float>(n + 1);
       h->py = w.alloc<float>(n + 1);
@@ -1201,16 +1212,16 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
       h->rv2f = w.alloc<float>(nv3 + 1);
       h->xbarf = w.alloc<float>(nv3 + 1);
       h->xtf = w.alloc<float>(nv3 + 1);
-      h->rp2f = w.alloc<float>(np + 1);
+      h->rp2f = w.alloc<float>((long long)np * k + 1);
     } else {
       h->gA.init(w, nv3, h->o.restart_inner);
-      h->gS.init(w, np, h->o.restart_inner);
+      h->gS.init(w, (long long)np * k, h->o.restart_inner);
       h->gI.init(w, nv3, h->o.restart_inner);
       h->yhat = w.alloc<double>(nv3 + 1);
       h->rv2 = w.alloc<double>(nv3 + 1);
       h->xbar = w.alloc<double>(nv3 + 1);
       h->xt = w.alloc<double>(nv3 + 1);
-      h->rp2 = w.alloc<double>(np + 1);
+      h->rp2 = w.alloc<double>((long long)np * k + 1);
     }
     SCR_CUDA(cudaStreamSynchronize(s));
     h->have_block = true;
@@ -1231,7 +1242,7 @@ static int solve_impl(scr_ctx* h, const double* b, double* x, double rtol) {
   const long long n = 3LL * h->nv + h->np;
   reset_solve_stats(h);
   Gmres<double>::Op op = [&](const double* xi, double* y) {
-    block_op(h->A, h->B, h->C, h->D, xi, y, nullptr, false, h->s);
+    block_op(h->A, h->B, h->C, h->D, xi, y, nullptr, false, h->s, h->k);
   };
   Gmres<double>::Op pc = [&](const double* r, double* y) { apply_pc_any(h, r, y); };
   std::function<double(const double*)> tr = [&](const double* xi) { return true_rel_block(h, b, xi); };
@@ -1255,6 +1266,10 @@ int scr_solve(scr_handle h, const double* b, double* x, int dev) {
     set_last_error("scr_solve before scr_setup");
     return SCR_INVALID_ARG;
   }
+  if (h->k != 1) {
+    set_last_error("scr_solve: the handle was set up for %d right-hand sides; use scr_solve_multi", h->k);
+    return SCR_INVALID_ARG;
+  }
   int status = SCR_OK;
   int rc = guarded([&] {
     auto t0 = Clock::now();
@@ -1276,6 +1291,73 @@ int scr_solve(scr_handle h, const double* b, double* x, int dev) {
   if (status == SCR_NOT_CONVERGED)
     set_last_error("FGMRES stopped at %d iterations with relative residual %.3e", h->stats.outer_iters,
                    h->stats.rel_res);
+  return status;
+}
+
+int scr_solve_multi(scr_handle h, const double* const* b, double* const* x, int dev, double* rel_res) {
+  if (!h || !b || !x) return SCR_INVALID_ARG;
+  if (!h->have_block) {
+    set_last_error("scr_solve_multi before scr_setup");
+    return SCR_INVALID_ARG;
+  }
+  const int k = h->k;
+  for (int c = 0; c < k; ++c)
+    if (!b[c] || !x[c]) {
+      set_last_error("scr_solve_multi: NULL right-hand side or solution pointer");
+      return SCR_INVALID_ARG;
+    }
+  int status = SCR_OK;
+  int rc = guarded([&] {
+    auto t0 = Clock::now();
+    const long long n = 3LL * h->nv + h->np;
+    cudaStream_t s = h->s;
+    const cudaMemcpyKind kin = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const cudaMemcpyKind kout = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    // right-hand sides one after another, their norms, then interleaved
+    double* st = k > 1 ? h->mstage : h->bvec;
+    for (int c = 0; c < k; ++c) SCR_CUDA(cudaMemcpyAsync(st + c * n, b[c], sizeof(double) * n, kin, s));
+    std::vector<double> bn(k, 0.0), rn(k, 0.0);
+    ArnoldiState* ast = h->gOuter.st;
+    for (int c = 0; c < k; ++c) {
+      norm2<double>(st + c * n, n, &ast->nrm2, h->red, s);
+      SCR_CUDA(cudaMemcpyAsync(&bn[c], &ast->nrm2, sizeof(double), cudaMemcpyDeviceToHost, s));
+      SCR_CUDA(cudaStreamSynchronize(s));
+    }
+    if (k > 1) interleave(st, h->bvec, n, k, true, s);
+    // the union tolerance rtol * min_c ||b_c|| / ||b|| bounds every
+    // right-hand side's relative residual by rtol
+    double b2 = 0.0, bmin = 0.0;
+    for (int c = 0; c < k; ++c) {
+      b2 += bn[c];
+      if (bn[c] > 0.0 && (bmin == 0.0 || bn[c] < bmin)) bmin = bn[c];
+    }
+    const double rtol = b2 > 0.0 ? h->o.rtol * std::sqrt(bmin / b2) : h->o.rtol;
+    status = solve_impl(h, h->bvec, h->xvec, rtol);
+    // per right-hand side: FP64 residual norms, solutions out
+    block_op(h->A, h->B, h->C, h->D, h->xvec, h->rvec, h->bvec, true, s, k);
+    double* rs = k > 1 ? h->mstage : h->rvec;
+    if (k > 1) interleave(h->rvec, rs, n, k, false, s);
+    double worst = 0.0;
+    for (int c = 0; c < k; ++c) {
+      norm2<double>(rs + c * n, n, &ast->nrm2, h->red, s);
+      SCR_CUDA(cudaMemcpyAsync(&rn[c], &ast->nrm2, sizeof(double), cudaMemcpyDeviceToHost, s));
+      SCR_CUDA(cudaStreamSynchronize(s));
+      const double rel = bn[c] > 0.0 ? std::sqrt(rn[c] / bn[c]) : std::sqrt(rn[c]);
+      if (rel_res) rel_res[c] = rel;
+      worst = std::max(worst, std::isfinite(rel) ? rel : 1e300);
+    }
+    double* xs = k > 1 ? h->mstage : h->xvec;
+    if (k > 1) interleave(h->xvec, xs, n, k, false, s);
+    for (int c = 0; c < k; ++c) SCR_CUDA(cudaMemcpyAsync(x[c], xs + c * n, sizeof(double) * n, kout, s));
+    SCR_CUDA(cudaStreamSynchronize(s));
+    check_staged(h);
+    h->stats.rel_res = worst;
+    status = worst <= h->o.rtol ? SCR_OK : SCR_NOT_CONVERGED;
+    h->stats.solve_ms = ms_since(t0);
+  });
+  if (rc != SCR_OK) return rc;
+  if (status == SCR_NOT_CONVERGED)
+    set_last_error("multi-right-hand-side solve: a right-hand side did not reach the tolerance");
   return status;
 }
 
@@ -1353,6 +1435,10 @@ int scr_setup_batch(scr_handle h, int nb, const scr_bsr* A, const scr_bsr* B, co
                     int dev) {
   if (!h || nb < 1 || !A || !B || !C || !D) {
     set_last_error("scr_setup_batch: NULL argument or nb < 1");
+    return SCR_INVALID_ARG;
+  }
+  if (h->o.nrhs != 1) {
+    set_last_error("scr_setup_batch: the batched form takes one right-hand side per member (nrhs = 1)");
     return SCR_INVALID_ARG;
   }
   std::vector<int> nv(nb), np(nb), vo(nb), po(nb);
@@ -1643,6 +1729,10 @@ int mm_iters(scr_handle h, int* iters, double* rel) {
 }
 
 int scr_apply_op(scr_handle h, const double* x, double* y) {
+  if (h && h->k != 1) {
+    set_last_error("this entry point takes one right-hand side (the handle has nrhs = %d)", h->k);
+    return SCR_INVALID_ARG;
+  }
   if (!h || !x || !y || !h->have_block) return SCR_INVALID_ARG;
   return guarded([&] {
     block_op(h->A, h->B, h->C, h->D, x, y, nullptr, false, h->s);
@@ -1652,6 +1742,10 @@ int scr_apply_op(scr_handle h, const double* x, double* y) {
 }
 
 int scr_apply_pc(scr_handle h, const double* r, double* y) {
+  if (h && h->k != 1) {
+    set_last_error("this entry point takes one right-hand side (the handle has nrhs = %d)", h->k);
+    return SCR_INVALID_ARG;
+  }
   if (!h || !r || !y || !h->have_block) return SCR_INVALID_ARG;
   return guarded([&] {
     reset_solve_stats(h);
@@ -1662,6 +1756,10 @@ int scr_apply_pc(scr_handle h, const double* r, double* y) {
 }
 
 int scr_apply_schur(scr_handle h, const double* xp, double* yp) {
+  if (h && h->k != 1) {
+    set_last_error("this entry point takes one right-hand side (the handle has nrhs = %d)", h->k);
+    return SCR_INVALID_ARG;
+  }
   if (!h || !xp || !yp || !h->have_block) return SCR_INVALID_ARG;
   return guarded([&] {
     reset_solve_stats(h);
@@ -1688,6 +1786,11 @@ static Hierarchy* pick_hier(scr_ctx* h, int which) {
 
 int scr_amg_apply(scr_handle h, int which, const double* b, double* x) {
   if (!h || !b || !x) return SCR_INVALID_ARG;
+  if (h->k != 1 && which != SCR_HIER_MESH) {
+    set_last_error("scr_amg_apply: the block hierarchies of a handle with nrhs = %d act on %d interleaved vectors",
+                   h->k, h->k);
+    return SCR_INVALID_ARG;
+  }
   Hierarchy* H = pick_hier(h, which);
   if (!H) {
     set_last_error("hierarchy not set up");

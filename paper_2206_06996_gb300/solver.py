@@ -205,6 +205,32 @@ class BlockSolver:
         check(st, (SCR_OK,) if raise_on_nonconvergence else (SCR_OK, SCR_NOT_CONVERGED))
         return xs
 
+    def solve_multi(self, bs, xs=None, raise_on_nonconvergence: bool = True):
+        """x_c with calA x_c = b_c for the opts.nrhs right-hand sides bs (all
+        numpy or all CUDA tensors); returns (xs, per-column FP64 relative
+        residuals)."""
+        k = self.opts.nrhs
+        if len(bs) != k:
+            raise ValueError(f"the handle solves {k} right-hand sides at once")
+        keep: list = []
+        if xs is None:
+            xs = [np.empty_like(np.asarray(b, dtype=np.float64)) if isinstance(b, np.ndarray)
+                  else _torch().empty_like(b) for b in bs]
+        pb = (C.c_void_p * k)()
+        px = (C.c_void_p * k)()
+        devs = set()
+        for i in range(k):
+            a, d = _ptr(bs[i], keep)
+            c, e = _ptr(xs[i], keep)
+            pb[i], px[i] = a, c
+            devs.update((d, e))
+        if len(devs) != 1:
+            raise ValueError("vectors must all be host or all device")
+        rel = np.zeros(k)
+        st = self.lib.scr_solve_multi(self.h, pb, px, devs.pop(), rel.ctypes.data_as(C.c_void_p))
+        check(st, (SCR_OK,) if raise_on_nonconvergence else (SCR_OK, SCR_NOT_CONVERGED))
+        return xs, rel
+
     def batch_residuals(self):
         n = len(self.batch_sizes)
         r = (C.c_double * n)()

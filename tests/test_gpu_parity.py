@@ -723,3 +723,45 @@ def test_wall_parameter_robustness(rho_s, E_s):
     assert 1 <= outer[pkg.SCR_PC_SCR] <= 5, outer
     assert outer[pkg.SCR_PC_SCR] < outer[pkg.SCR_PC_SIMPLE], outer
     assert outer[pkg.SCR_PC_SCR] < outer[pkg.SCR_PC_SIMPLEC], outer
+
+
+def _inflow_rhs(name, n_rhs=8, seed=2206):
+    """Right-hand sides -R at states whose inflow peaks are drawn U(0, 60)
+    cm/s (one Jacobian, at the nominal 30 cm/s, solves all of them)."""
+    peaks = np.random.default_rng(seed).uniform(0.0, 60.0, n_rhs)
+    return [F.tube_system(name, u_max=float(u)).b for u in peaks]
+
+
+@pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
+def test_multi_rhs_solve_matches_direct(small, precision):
+    """Eight right-hand sides with one set-up: interleaved vectors, every
+    product with eight columns at once, one FGMRES on the interleaved system;
+    every column meets the tolerance (recomputed by the oracle) and matches
+    the direct solve of its own right-hand side."""
+    op = BlockOperator.from_system(small)
+    rhs = _inflow_rhs("tube_small")
+    ref = direct.solve_block_many(small, rhs)
+    with pkg.BlockSolver(nrhs=8, precision=precision) as sol:
+        sol.setup(small.A, small.B, small.C, small.D)
+        xs, rel = sol.solve_multi([b.copy() for b in rhs])
+        xd, reld = sol.solve_multi([_dev(b) for b in rhs])
+        with pytest.raises(pkg.ScrError):
+            sol.solve(rhs[0].copy())
+    assert np.all(rel <= 1e-8) and np.all(reld <= 1e-8)
+    for b, x, x2, xr in zip(rhs, xs, xd, ref):
+        assert rel_residual(op, x, b) <= 1e-8
+        assert _rel(x, xr) <= 1e-6
+        np.testing.assert_array_equal(x, x2.cpu().numpy())
+
+
+def test_multi_rhs_equal_columns_give_the_single_solution(small, small_direct):
+    """Eight copies of one right-hand side: each column equals the direct
+    solution; zero columns stay zero."""
+    b = small.b
+    with pkg.BlockSolver(nrhs=8) as sol:
+        sol.setup(small.A, small.B, small.C, small.D)
+        xs, rel = sol.solve_multi([b.copy() for _ in range(7)] + [np.zeros_like(b)])
+    for x in xs[:7]:
+        assert _rel(x, small_direct) <= 1e-6
+    assert np.all(xs[7] == 0.0)
+    assert np.all(rel[:7] <= 1e-8)

@@ -497,3 +497,13 @@ def test_cheb_guard_decisions_on_the_tube(tiny_system):
     _, info = krylov.gmres(lambda v: Sh @ v, b, lambda v: amg.vcycle(H, v), tol=1e-3, maxit=200, restart=30)
     assert info.converged
     del tiny_system
+
+
+def test_direct_solve_of_several_right_hand_sides(mini_system, mini_direct):
+    op = BlockOperator.from_system(mini_system)
+    rng = np.random.default_rng(21)
+    rhs = [mini_system.b, rng.standard_normal(op.n), 2.0 * mini_system.b]
+    xs = direct.solve_block_many(mini_system, rhs)
+    assert np.allclose(xs[0], mini_direct, rtol=0, atol=1e-12 * np.abs(mini_direct).max())
+    assert np.allclose(xs[2], 2.0 * mini_direct, rtol=0, atol=1e-11 * np.abs(mini_direct).max())
+    assert rel_residual(op, xs[1], rhs[1]) <= 1e-10
