@@ -53,6 +53,9 @@ def parse():
                     help="autotuner decisions: loaded before the first set-up when the file exists, "
                          "written after the run otherwise (replays one run's kernel choices in another, "
                          "e.g. under a profiler whose instrumentation distorts the autotuner's timings)")
+    ap.add_argument("--multi-rhs", action="store_true",
+                    help="also time eight right-hand sides (inflow peaks U(0, 60) cm/s, one Jacobian) solved as one "
+                         "8-column block solve in mixed precision against the same eight solved one by one")
     ap.add_argument("--batched", action="store_true",
                     help="also time the 64-tube batched form (mixed, one block-diagonal solve) against the "
                          "same 64 tubes solved one by one in FP64")
@@ -378,6 +381,38 @@ def main():
                    "fp64_one_by_one_ms": mss, "speedup_vs_fp64_one_by_one": mss / msb,
                    "max_member_rel_res": float(relb.max())}
 
+    multi = None
+    if args.multi_rhs:
+        peaks_u = np.random.default_rng(2206).uniform(0.0, 60.0, 8)
+        rhs = [torch.as_tensor(F.tube_system(args.workload, u_max=float(u)).b, device=dev) for u in peaks_u]
+        xs8 = [torch.empty_like(b) for b in rhs]
+        solk = pkg.BlockSolver(precision=pkg.SCR_MIXED, nrhs=8)
+        rel8 = None
+
+        def step_multi(sol_):
+            nonlocal rel8
+            sol_.setup(Ad, Bd, Cd, Dd)
+            _, rel8 = sol_.solve_multi(rhs, xs8)
+
+        step_multi(solk)
+        msk, _, _ = timed(solk, step_multi, max(1, args.steps))
+        stk = solk.stats()
+        solk.close()
+        sol1 = pkg.BlockSolver(precision=pkg.SCR_MIXED)
+
+        def step_single(sol_):
+            sol_.setup(Ad, Bd, Cd, Dd)
+            for b, x in zip(rhs, xs8):
+                sol_.solve(b, x)
+
+        step_single(sol1)
+        ms1, _, _ = timed(sol1, step_single, max(1, args.steps))
+        sol1.close()
+        multi = {"rhs": 8, "inflow_peaks_cm_s": [float(u) for u in peaks_u], "precision": "mixed",
+                 "block_ms": msk, "rhs_solves_per_s": 8 * 1000.0 / msk, "one_by_one_ms": ms1,
+                 "speedup_vs_one_by_one": ms1 / msk, "block_outer_iters": stk["outer_iters"],
+                 "max_rel_res": float(np.max(rel8))}
+
     if rank != 0:
         return
     hbm, peak_kind = peaks()
@@ -440,7 +475,7 @@ def main():
         "mesh_iters": st["mm_iters"], "setup_ms": st["setup_ms"], "solve_ms": st["solve_ms"],
         "mm_setup_ms": st["mm_setup_ms"], "mm_solve_ms": st["mm_solve_ms"],
         "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "mixed": mixed,
-        "batched": batched,
+        "batched": batched, "multi_rhs": multi,
         "clocks": clocks, "inputs_build_s": t_in,
     }
     if args.tune_file and not tune_loaded and rank == 0:
