@@ -225,6 +225,12 @@ class BlockSystem:
     mesh_b: np.ndarray | None
     mesh: Mesh | None
     params: dict
+    # resistance outlet (optional): the momentum block's consistent tangent
+    # gains alpha_f gamma dt sum_k m_k a_k a_k^T (Sec. 3.5, outlet coupling
+    # matrix); a_out[k] has the 3 n_v entries int_{outlet k} N_A n_i dGamma
+    # (zero on Dirichlet rows), c_out[k] = alpha_f gamma dt m_k
+    a_out: list | None = None
+    c_out: list | None = None
 
     @property
     def n_v(self) -> int:
@@ -289,6 +295,7 @@ def tube_system(name: str = "tube_small", threads: int = 0, keep_mesh: bool = Fa
     """Build the block system of a preset (``PRESETS``) with overrides."""
     kw = dict(PRESETS[name]) if name in PRESETS else {}
     kw.update(overrides)
+    r_out = float(kw.pop("outlet_resistance", 0.0))
     params = make_params(**kw)
     L = lib()
     if threads:
@@ -316,6 +323,14 @@ def tube_system(name: str = "tube_small", threads: int = 0, keep_mesh: bool = Fa
             mesh_b=(np.ctypeslib.as_array(s.mesh_b, shape=(3 * m.n_fluid,)).copy() if Lraw else None),
             mesh=_mesh_from_c(m) if keep_mesh else None,
             params={f: getattr(params, f) for f, _ in Params._fields_})
+        if r_out > 0.0:
+            a = outlet_vector(_mesh_from_c(m), params.n_ax)
+            # resistance outlet: pressure P = r_out Q with Q = a^T v, so the
+            # momentum residual gains P a and its tangent alpha_f gamma dt
+            # r_out a a^T; b = -R
+            out.b[: 3 * nn] -= r_out * float(a @ v) * a
+            out.a_out, out.c_out = [a], [cf * r_out]
+            out.params["outlet_resistance"] = r_out
         L.tg_system_free(sysp)
         L.tg_raw_free(raw)
         if Lraw:
@@ -323,6 +338,29 @@ def tube_system(name: str = "tube_small", threads: int = 0, keep_mesh: bool = Fa
         return out
     finally:
         L.tg_mesh_free(pm)
+
+
+def outlet_vector(mesh: Mesh, n_ax: int, zero_dirichlet: bool = True) -> np.ndarray:
+    """a_{A,i} = int_{outlet} N_A n_i dGamma over the fluid outlet section
+    (the faces of fluid tets with all three vertices on the last axial
+    layer; outward normal +z, so only the z components are nonzero); a
+    linear shape function integrates to a third of the triangle's area.
+    Entries on Dirichlet velocity rows are zero."""
+    a = np.zeros(3 * mesh.n_nodes)
+    on = mesh.layer == n_ax
+    for e in np.nonzero(mesh.etype == 0)[0]:
+        v = mesh.ien[e]
+        for drop in range(4):
+            f = [v[q] for q in range(4) if q != drop]
+            if not all(on[f]):
+                continue
+            x = mesh.xyz[f]
+            area = 0.5 * np.linalg.norm(np.cross(x[1] - x[0], x[2] - x[0]))
+            for node in f:
+                a[3 * node + 2] += area / 3.0
+    if zero_dirichlet:
+        a[np.repeat(mesh.dir_v, 3)] = 0.0
+    return a
 
 
 class Assembler:

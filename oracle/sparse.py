@@ -38,8 +38,18 @@ class BlockOperator:
     """The 2x2 block matrix calA = [[A, B], [C, D]] of Sec. 5.2.1 with the
     vector split x = [x_v; x_p]."""
 
-    def __init__(self, A, B, C, D):
-        self.A = to_csr(A)
+    def __init__(self, A, B, C, D, a_out=None, c_out=None):
+        self.A_sparse = to_csr(A)
+        self.A = self.A_sparse
+        # resistance outlets (Sec. 3.5, outlet coupling matrix): the momentum
+        # block is A + sum_k c_k a_k a_k^T, written out as explicit entries
+        # on the outlet rows and columns
+        if a_out is not None:
+            for a, c in zip(a_out, c_out):
+                a = sp.csr_matrix(np.asarray(a, dtype=np.float64).reshape(-1, 1))
+                self.A = (self.A + c * (a @ a.T)).tocsr()
+            self.A.sum_duplicates()
+            self.A.sort_indices()
         self.B = to_csr(B)
         self.C = to_csr(C)
         self.D = to_csr(D)
@@ -49,7 +59,7 @@ class BlockOperator:
 
     @classmethod
     def from_system(cls, s) -> "BlockOperator":
-        return cls(s.A, s.B, s.C, s.D)
+        return cls(s.A, s.B, s.C, s.D, getattr(s, "a_out", None), getattr(s, "c_out", None))
 
     def split(self, x):
         return x[: self.nv], x[self.nv:]

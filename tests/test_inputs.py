@@ -403,3 +403,38 @@ def test_generator_deterministic_across_threads():
         assert np.array_equal(M.val, N.val)
     assert np.array_equal(a.b, b.b)
     F.lib().tg_set_threads(os.cpu_count() or 1)
+
+
+# ---------------------------------------------------------------- resistance outlet
+def test_outlet_vector_integrates_the_outlet_section():
+    """a_{A,z} = int_outlet N_A dGamma sums to the area of the outlet's lumen
+    polygon (n_circ vertices on the lumen radius: n/2 R^2 sin(2 pi / n)),
+    only z components are nonzero, and a^T v is the discrete Poiseuille flux
+    pi R^2 u_max / 2 up to the O(h^2) interpolation error."""
+    s = F.tube_system("tube_small", keep_mesh=True)
+    p = s.params
+    a = F.outlet_vector(s.mesh, p["n_ax"], zero_dirichlet=False)
+    nc, R = p["n_circ"], p["R"]
+    assert abs(a.sum() - 0.5 * nc * R * R * np.sin(2 * np.pi / nc)) <= 1e-12 * a.sum()
+    assert np.all(a.reshape(-1, 3)[:, :2] == 0.0)
+    z_nodes = np.nonzero(a.reshape(-1, 3)[:, 2])[0]
+    assert np.all(s.mesh.layer[z_nodes] == p["n_ax"]) and np.all(s.mesh.fluid_id[z_nodes] >= 0)
+    v = np.zeros(3 * s.mesh.n_nodes)
+    r2 = s.mesh.xyz[:, 0] ** 2 + s.mesh.xyz[:, 1] ** 2
+    v[2::3] = np.where(s.mesh.fluid_id >= 0, p["u_max"] * np.clip(1 - r2 / R ** 2, 0, None), 0.0)
+    q = a @ v
+    assert abs(q - np.pi * R * R * p["u_max"] / 2) <= 0.1 * q
+
+
+def test_resistance_outlet_terms():
+    """c = alpha_f gamma dt R_out (closed form); a is zero on Dirichlet rows;
+    zero resistance gives the zero-traction system unchanged."""
+    r_out = 2.7e4
+    s = F.tube_system("tube_mini", outlet_resistance=r_out, keep_mesh=True)
+    am, af, ga = F.genalpha(s.params["rho_inf"])
+    assert s.c_out[0] == pytest.approx(af * ga * s.params["dt"] * r_out, rel=1e-15)
+    a = s.a_out[0]
+    assert np.all(a[np.repeat(s.mesh.dir_v, 3)] == 0.0) and a.sum() > 0
+    s0 = F.tube_system("tube_mini")
+    s1 = F.tube_system("tube_mini", outlet_resistance=0.0)
+    assert s1.a_out is None and np.array_equal(s0.b, s1.b)

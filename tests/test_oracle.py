@@ -507,3 +507,23 @@ def test_direct_solve_of_several_right_hand_sides(mini_system, mini_direct):
     assert np.allclose(xs[0], mini_direct, rtol=0, atol=1e-12 * np.abs(mini_direct).max())
     assert np.allclose(xs[2], 2.0 * mini_direct, rtol=0, atol=1e-11 * np.abs(mini_direct).max())
     assert rel_residual(op, xs[1], rhs[1]) <= 1e-10
+
+
+# ---------------------------------------------------------------- resistance outlet
+def test_outlet_term_in_the_block_operator():
+    """calA with a resistance outlet: the momentum block acts as
+    A v + c a (a^T v) (checked against that expression), its diagonal gains
+    c a_i^2 (enters Shat), and the SCR-FGMRES solve of the oracle matches the
+    direct solve of the full system."""
+    s = F.tube_system("tube_mini", outlet_resistance=2.7e4)
+    op = BlockOperator.from_system(s)
+    a, c = s.a_out[0], s.c_out[0]
+    v = np.random.default_rng(5).standard_normal(op.nv)
+    assert np.allclose(op.A @ v, op.A_sparse @ v + c * a * (a @ v), rtol=1e-13, atol=1e-13 * np.abs(op.A @ v).max())
+    assert np.allclose(op.A.diagonal(), op.A_sparse.diagonal() + c * a * a, rtol=1e-14)
+    assert np.any(c * a * a > 1e-3 * np.abs(op.A_sparse.diagonal()))
+    x_ref = direct.solve_block(s)
+    sol = scr.SCRSolver(s)
+    x, info = sol.solve(s.b)
+    assert info.converged and rel_residual(op, x, s.b) <= 1e-8
+    assert np.linalg.norm(x - x_ref) <= 1e-6 * np.linalg.norm(x_ref)
