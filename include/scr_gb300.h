@@ -234,6 +234,19 @@ int scr_residual(scr_handle h, double* rel_res);
    multi-right-hand-side form is an addition of this library. */
 int scr_solve_multi(scr_handle h, const double* const* b, double* const* x, int dev, double* rel_res);
 
+/* Resistance outlets (Sec. 3.5, outlet coupling matrix): the momentum block
+   of calA becomes A + sum_j c_j a_j a_j^T, with a_j[3 A + i] = the integral
+   of N_A n_i over outlet j and c_j = alpha_f gamma dt m_j (m_j = dP/dQ of the
+   outlet model).  a: n_out vectors of len = 3 n_v doubles one after
+   another, c: n_out doubles (host memory, copied).  Takes effect at the
+   next scr_setup: every product with A on the Krylov path and calA add the
+   rank-1 terms (one dot and one update per outlet), diag(A) in Shat and in
+   SIMPLE's update includes sum_j c_j a_j^2; the AMG hierarchies are built
+   from the sparse A.  n_out = 0 removes the outlets.  SCR_INVALID_ARG for
+   NULL arrays, a non-finite coefficient, or (at scr_setup) len != 3 n_v,
+   nrhs != 1 or SCR_PC_SIMPLEC. */
+int scr_set_outlets(scr_handle h, int n_out, int len, const double* a, const double* c);
+
 /* Counters and timings (see scr_stats). */
 int scr_get_stats(scr_handle h, scr_stats* s);
 

@@ -74,6 +74,48 @@ template void copy<double>(const double*, double*, long long, cudaStream_t);
 template void copy<float>(const float*, float*, long long, cudaStream_t);
 template void copy<int>(const int*, int*, long long, cudaStream_t);
 
+// y += (c * dot[0]) a  (dot: a device scalar)
+template <typename T>
+__global__ void k_axpy_dev(const T* __restrict__ a, const double* __restrict__ dot, double c, T* __restrict__ y,
+                           long long n) {
+  const double f = c * dot[0];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] += (T)(f * (double)a[i]);
+}
+template <typename T>
+void axpy_dev(const T* a, const double* dot, double c, T* y, long long n, cudaStream_t s) {
+  if (n == 0) return;
+  k_axpy_dev<T><<<grid_for(n), 256, 0, s>>>(a, dot, c, y, n);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+template void axpy_dev<double>(const double*, const double*, double, double*, long long, cudaStream_t);
+template void axpy_dev<float>(const float*, const double*, double, float*, long long, cudaStream_t);
+
+// d[i] += c a[i]^2
+__global__ void k_add_sq(double* __restrict__ d, const double* __restrict__ a, double c, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) d[i] += c * a[i] * a[i];
+}
+void add_scaled_squares(double* d, const double* a, double c, long long n, cudaStream_t s) {
+  if (n == 0) return;
+  k_add_sq<<<ceil_div(n, 256), 256, 0, s>>>(d, a, c, n);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
+// y[i] = 1 / x[i]
+__global__ void k_recip(const double* __restrict__ x, double* __restrict__ y, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = 1.0 / x[i];
+}
+void reciprocal(const double* x, double* y, long long n, cudaStream_t s) {
+  if (n == 0) return;
+  k_recip<<<ceil_div(n, 256), 256, 0, s>>>(x, y, n);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
 // k vectors of length n stored one after another (in[c * n + i]) <->
 // interleaved (out[i * k + c])
 __global__ void k_interleave(const double* __restrict__ in, double* __restrict__ out, long long n, int k,

@@ -142,6 +142,13 @@ void cast_d2f(const double* x, float* y, long long n, cudaStream_t s);
 void cast_f2d(const float* x, double* y, long long n, cudaStream_t s);
 // y = a*x + b*y
 void axpby(double a, const double* x, double b, double* y, long long n, cudaStream_t s);
+// y += (c * dot[0]) a with dot a device scalar (rank-1 outlet term)
+template <typename T>
+void axpy_dev(const T* a, const double* dot, double c, T* y, long long n, cudaStream_t s);
+// d += c a .* a
+void add_scaled_squares(double* d, const double* a, double c, long long n, cudaStream_t s);
+// y = 1 ./ x
+void reciprocal(const double* x, double* y, long long n, cudaStream_t s);
 // k vectors of length n one after another <-> interleaved (entry i of vector c
 // at i * k + c)
 void interleave(const double* in, double* out, long long n, int k, bool to_interleaved, cudaStream_t s);

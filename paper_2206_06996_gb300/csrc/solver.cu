@@ -753,6 +753,14 @@ struct scr_ctx {
   // at i * k + c, and every product acts as M (x) I_k
   int k = 1;
   double* mstage = nullptr;  // k vectors one after another (multi-right-hand-side staging)
+  // resistance outlets (scr_set_outlets): A acts as A + sum_j c_j a_j a_j^T
+  int n_out = 0;                    // outlets in effect (from the last scr_setup)
+  std::vector<double> out_c;
+  int pend_n = 0, pend_len = 0;     // set by scr_set_outlets, used by the next scr_setup
+  std::vector<double> pend_a, pend_c;
+  double* out_a = nullptr;    // device, n_out x 3 n_v
+  float* out_af = nullptr;    // FP32 copy (mixed precision)
+  double* out_dot = nullptr;  // device, n_out scratch dots
   // batched form: member sizes and offsets inside the union system
   int nbatch = 0;
   std::vector<int> b_nv, b_np, b_vo, b_po;
@@ -885,15 +893,40 @@ struct PcView {
   Gmres<T>*gA, *gS, *gI;
   T *yhat, *rp2, *rv2, *xbar, *xt;
   const T* dAinv;
+  const T* out_a;  // outlet vectors in this precision (n_out x 3 n_v) or null
 };
 
 PcView<double> view64(scr_ctx* h) {
   return PcView<double>{&h->A, &h->B, &h->C, &h->D, &h->Shat, &h->hA, &h->hS, &h->gA, &h->gS, &h->gI,
-                        h->yhat, h->rp2, h->rv2, h->xbar, h->xt, h->dAinv};
+                        h->yhat, h->rp2, h->rv2, h->xbar, h->xt, h->dAinv, h->out_a};
 }
 PcView<float> view32(scr_ctx* h) {
   return PcView<float>{&h->Af, &h->Bf, &h->Cf, &h->Df, &h->hS.lv[0].Af, &h->hA, &h->hS, &h->gAf, &h->gSf, &h->gIf,
-                       h->yhatf, h->rp2f, h->rv2f, h->xbarf, h->xtf, h->dAinvf};
+                       h->yhatf, h->rp2f, h->rv2f, h->xbarf, h->xtf, h->dAinvf, h->out_af};
+}
+
+// y += sign * sum_j c_j a_j (a_j^T x) on the velocity rows (the outlets'
+// rank-1 terms of the momentum block; one dot and one update per outlet)
+template <typename T>
+void outlet_terms(scr_ctx* h, const T* a, const T* x, T* y, double sign) {
+  const long long nv3 = 3LL * h->nv;
+  for (int j = 0; j < h->n_out; ++j) {
+    multidot<T>(a + j * nv3, 0, 1, x, nv3, h->out_dot + j, h->red, h->s);
+    axpy_dev<T>(a + j * nv3, h->out_dot + j, sign * h->out_c[j], y, nv3, h->s);
+  }
+}
+
+// the momentum block's action: y = A x (+ the outlet terms)
+template <typename T>
+void apply_A(scr_ctx* h, PcView<T>& v, const T* x, T* y) {
+  spmv<T, T>(*v.A, x, y, h->k, EpiArgs(), h->s);
+  if (h->n_out) outlet_terms<T>(h, v.out_a, x, y, 1.0);
+}
+
+// y = calA x, or y = z - calA x (resid), with the outlet terms, in FP64
+void apply_calA(scr_ctx* h, const double* x, double* y, const double* z, bool resid) {
+  block_op(h->A, h->B, h->C, h->D, x, y, z, resid, h->s, h->k);
+  if (h->n_out) outlet_terms<double>(h, h->out_a, x, y, resid ? -1.0 : 1.0);
 }
 
 // Algorithm 2: y_p = D x_p - C A^{-1} (B x_p), A^{-1} by inner GMRES + P_I
@@ -901,7 +934,7 @@ template <typename T>
 void apply_S(scr_ctx* h, PcView<T>& v, const T* xp, T* yp) {
   cudaStream_t s = h->s;
   spmv<T, T>(*v.B, xp, v.xbar, h->k, EpiArgs(), s);
-  typename Gmres<T>::Op opA = [&](const T* x, T* y) { spmv<T, T>(*v.A, x, y, h->k, EpiArgs(), s); };
+  typename Gmres<T>::Op opA = [&](const T* x, T* y) { apply_A<T>(h, v, x, y); };
   typename Gmres<T>::Op pcA = [&](const T* b, T* x) { v.hA->template apply<T>(b, x, s); };
   int it = 0;
   double rel = 0;
@@ -925,7 +958,7 @@ void apply_pc(scr_ctx* h, PcView<T>& v, const T* r, T* y) {
   const T* rp = r + nv3;
   T* yv = y;
   T* yp = y + nv3;
-  typename Gmres<T>::Op opA = [&](const T* x, T* o) { spmv<T, T>(*v.A, x, o, h->k, EpiArgs(), s); };
+  typename Gmres<T>::Op opA = [&](const T* x, T* o) { apply_A<T>(h, v, x, o); };
   typename Gmres<T>::Op pcA = [&](const T* b, T* x) { v.hA->template apply<T>(b, x, s); };
   typename Gmres<T>::Op opS = [&](const T* x, T* o) { apply_S<T>(h, v, x, o); };
   typename Gmres<T>::Op pcS = [&](const T* b, T* x) { v.hS->template apply<T>(b, x, s); };
@@ -966,7 +999,7 @@ void apply_simple(scr_ctx* h, PcView<T>& v, const T* r, T* y) {
   const T* rp = r + nv3;
   T* yv = y;
   T* yp = y + nv3;
-  typename Gmres<T>::Op opA = [&](const T* x, T* o) { spmv<T, T>(*v.A, x, o, h->k, EpiArgs(), s); };
+  typename Gmres<T>::Op opA = [&](const T* x, T* o) { apply_A<T>(h, v, x, o); };
   typename Gmres<T>::Op pcA = [&](const T* b, T* x) { v.hA->template apply<T>(b, x, s); };
   typename Gmres<T>::Op opS = [&](const T* x, T* o) { spmv<T, T>(*v.Shat, x, o, h->k, EpiArgs(), s); };
   typename Gmres<T>::Op pcS = [&](const T* b, T* x) { v.hS->template apply<T>(b, x, s); };
@@ -1008,7 +1041,7 @@ void apply_pc_any(scr_ctx* h, const double* r, double* y) {
 
 double true_rel_block(scr_ctx* h, const double* b, const double* x) {
   const long long n = (3LL * h->nv + h->np) * h->k;
-  block_op(h->A, h->B, h->C, h->D, x, h->rvec, b, true, h->s, h->k);
+  apply_calA(h, x, h->rvec, b, true);
   ArnoldiState* st = h->gOuter.st;
   norm2<double>(h->rvec, n, &st->nrm2, h->red, h->s);
   double r2 = 0, b2 = 0;
@@ -1132,7 +1165,23 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
     h->np = np;
     h->k = h->o.nrhs;
     h->mstage = nullptr;
+    h->n_out = 0;
+    h->out_a = nullptr;
+    h->out_af = nullptr;
+    if (h->pend_n) {
+      if (h->pend_len != 3 * nv) throw std::invalid_argument("outlet vectors must have 3 n_v entries");
+      if (h->k != 1) throw std::invalid_argument("outlet terms take one right-hand side (nrhs = 1)");
+      if (h->o.precond == SCR_PC_SIMPLEC) throw std::invalid_argument("SIMPLEC with outlet terms is not supported");
+    }
     h->A = upload(A, dev, a, s);
+    if (h->pend_n) {
+      const long long len = (long long)h->pend_n * 3 * nv;
+      h->out_a = a.alloc<double>(len + 1);
+      SCR_CUDA(cudaMemcpyAsync(h->out_a, h->pend_a.data(), sizeof(double) * len, cudaMemcpyHostToDevice, s));
+      h->out_dot = a.alloc<double>(h->pend_n);
+      h->out_c = h->pend_c;
+      h->n_out = h->pend_n;
+    }
     h->B = upload(B, dev, a, s);
     h->C = upload(C, dev, a, s);
     h->D = upload(D, dev, a, s);
@@ -1151,6 +1200,12 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
       if (hb) throw std::invalid_argument("A has a missing or zero diagonal entry");
       // SIMPLEC: the diagonal lumped from the absolute values of A's entries
       if (h->o.precond == SCR_PC_SIMPLEC) abs_rowsum(h->A, d, s);
+      // outlets: diag(A + sum_j c_j a_j a_j^T) = diag(A) + sum_j c_j a_j .* a_j
+      for (int j = 0; j < h->n_out; ++j) add_scaled_squares(d, h->out_a + 3LL * nv * j, h->out_c[j], 3LL * nv, s);
+      if (h->n_out) {
+        h->dAinv = a.alloc<double>(3LL * nv + 1);
+        reciprocal(d, h->dAinv, 3LL * nv, s);
+      }
       DBsr<double> Bs, T;
       scale_rows_inv(h->B, d, Bs, tmp, s);
       spgemm(h->C, Bs, T, tmp, s);
@@ -1158,9 +1213,11 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
       SCR_CUDA(cudaStreamSynchronize(s));
     }
     if (h->o.verbose) fprintf(stderr, "[setup] Shat %.2f ms (%lld entries)\n", ms_since(t1), h->Shat.nnzb);
-    h->dAinv = a.alloc<double>(3LL * nv + 1);
-    if (h->o.precond == SCR_PC_SIMPLEC) l1_inv(h->A, h->dAinv, s);  // 1 / sum_j |a_ij|
-    else inv_diag(h->A, h->dAinv, s);
+    if (!h->n_out) {
+      h->dAinv = a.alloc<double>(3LL * nv + 1);
+      if (h->o.precond == SCR_PC_SIMPLEC) l1_inv(h->A, h->dAinv, s);  // 1 / sum_j |a_ij|
+      else inv_diag(h->A, h->dAinv, s);
+    }
     const bool f32 = h->o.precision == SCR_MIXED;
     if (h->o.sell) {
       build_sell<double>(h->A, h->A_sell, a, s, h->o.sell);
@@ -1203,6 +1260,10 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
     if (f32) {
       h->dAinvf = w.alloc<float>(3LL * nv + 1);
       cast_d2f(h->dAinv, h->dAinvf, 3LL * nv, s);
+      if (h->n_out) {
+        h->out_af = w.alloc<float>((long long)h->n_out * 3 * nv + 1);
+        cast_d2f(h->out_a, h->out_af, (long long)h->n_out * 3 * nv, s);
+      }
       h->gAf.init(w, nv3, h->o.restart_inner);
       h->gSf.init(w, (long long)np * k, h->o.restart_inner);
       h->gIf.init(w, nv3, h->o.restart_inner);
@@ -1241,9 +1302,7 @@ static void reset_solve_stats(scr_ctx* h) {
 static int solve_impl(scr_ctx* h, const double* b, double* x, double rtol) {
   const long long n = 3LL * h->nv + h->np;
   reset_solve_stats(h);
-  Gmres<double>::Op op = [&](const double* xi, double* y) {
-    block_op(h->A, h->B, h->C, h->D, xi, y, nullptr, false, h->s, h->k);
-  };
+  Gmres<double>::Op op = [&](const double* xi, double* y) { apply_calA(h, xi, y, nullptr, false); };
   Gmres<double>::Op pc = [&](const double* r, double* y) { apply_pc_any(h, r, y); };
   std::function<double(const double*)> tr = [&](const double* xi) { return true_rel_block(h, b, xi); };
   int it = 0;
@@ -1334,7 +1393,7 @@ int scr_solve_multi(scr_handle h, const double* const* b, double* const* x, int 
     const double rtol = b2 > 0.0 ? h->o.rtol * std::sqrt(bmin / b2) : h->o.rtol;
     status = solve_impl(h, h->bvec, h->xvec, rtol);
     // per right-hand side: FP64 residual norms, solutions out
-    block_op(h->A, h->B, h->C, h->D, h->xvec, h->rvec, h->bvec, true, s, k);
+    apply_calA(h, h->xvec, h->rvec, h->bvec, true);
     double* rs = k > 1 ? h->mstage : h->rvec;
     if (k > 1) interleave(h->rvec, rs, n, k, false, s);
     double worst = 0.0;
@@ -1735,7 +1794,7 @@ int scr_apply_op(scr_handle h, const double* x, double* y) {
   }
   if (!h || !x || !y || !h->have_block) return SCR_INVALID_ARG;
   return guarded([&] {
-    block_op(h->A, h->B, h->C, h->D, x, y, nullptr, false, h->s);
+    apply_calA(h, x, y, nullptr, false);
     SCR_CUDA(cudaStreamSynchronize(h->s));
     check_staged(h);
   });
@@ -1859,6 +1918,21 @@ int scr_export(scr_handle h, int which, int level, int kind, scr_bsr_out* out) {
     SCR_CUDA(cudaMemcpyAsync(out->col_idx, M->col, sizeof(int) * M->nnzb, cudaMemcpyDeviceToHost, h->s));
     SCR_CUDA(cudaMemcpyAsync(out->val, v, sizeof(double) * nv, cudaMemcpyDeviceToHost, h->s));
     SCR_CUDA(cudaStreamSynchronize(h->s));
+  });
+}
+
+int scr_set_outlets(scr_handle h, int n_out, int len, const double* a, const double* c) {
+  if (!h || n_out < 0 || (n_out > 0 && (!a || !c || len <= 0))) {
+    set_last_error("scr_set_outlets: NULL argument or negative count");
+    return SCR_INVALID_ARG;
+  }
+  return guarded([&] {
+    for (int j = 0; j < n_out; ++j)
+      if (!std::isfinite(c[j])) throw std::invalid_argument("scr_set_outlets: coefficient not finite");
+    h->pend_n = n_out;
+    h->pend_len = n_out ? len : 0;
+    h->pend_a.assign(a, a + (size_t)n_out * len);
+    h->pend_c.assign(c, c + n_out);
   });
 }
 

@@ -205,6 +205,18 @@ class BlockSolver:
         check(st, (SCR_OK,) if raise_on_nonconvergence else (SCR_OK, SCR_NOT_CONVERGED))
         return xs
 
+    def set_outlets(self, a_out, c_out):
+        """Rank-1 outlet terms for the next setup: vectors a_j (3 n_v each)
+        and coefficients c_j; empty lists remove them."""
+        a_out = [np.ascontiguousarray(a, dtype=np.float64) for a in (a_out or [])]
+        c = np.ascontiguousarray(c_out or [], dtype=np.float64)
+        n = len(a_out)
+        if n != c.size:
+            raise ValueError("one coefficient per outlet vector")
+        a = np.concatenate(a_out) if n else np.zeros(1)
+        ln = a_out[0].size if n else 0
+        check(self.lib.scr_set_outlets(self.h, n, ln, a.ctypes.data_as(C.c_void_p), c.ctypes.data_as(C.c_void_p)))
+
     def solve_multi(self, bs, xs=None, raise_on_nonconvergence: bool = True):
         """x_c with calA x_c = b_c for the opts.nrhs right-hand sides bs (all
         numpy or all CUDA tensors); returns (xs, per-column FP64 relative

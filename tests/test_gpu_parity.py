@@ -765,3 +765,59 @@ def test_multi_rhs_equal_columns_give_the_single_solution(small, small_direct):
         assert _rel(x, small_direct) <= 1e-6
     assert np.all(xs[7] == 0.0)
     assert np.all(rel[:7] <= 1e-8)
+
+
+@pytest.fixture(scope="module")
+def outlet_small():
+    return F.tube_system("tube_small", outlet_resistance=2.7e4)
+
+
+def test_outlet_terms_in_calA_and_shat(outlet_small):
+    """Resistance outlet: calA x and Shat with the rank-1 outlet term equal
+    the oracle's (explicit) operator."""
+    s = outlet_small
+    op = BlockOperator.from_system(s)
+    x = np.random.default_rng(6).standard_normal(op.n)
+    with pkg.BlockSolver() as sol:
+        sol.set_outlets(s.a_out, s.c_out)
+        sol.setup(s.A, s.B, s.C, s.D)
+        y = sol.apply_op(_dev(x)).cpu().numpy()
+        Sh = to_csr(sol.export(pkg.SCR_HIER_SHAT, 0, pkg.SCR_EXPORT_OPERATOR))
+    assert _rel(y, op.matvec(x)) < 1e-13
+    want = schur.schur_hat(op)
+    assert abs(Sh - want).max() <= 1e-12 * abs(want).max()
+
+
+@pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
+@pytest.mark.parametrize("precond", [pkg.SCR_PC_SCR, pkg.SCR_PC_SIMPLE])
+def test_outlet_solve_matches_direct(outlet_small, precision, precond):
+    s = outlet_small
+    op = BlockOperator.from_system(s)
+    x_ref = direct.solve_block(s)
+    with pkg.BlockSolver(precision=precision, precond=precond) as sol:
+        sol.set_outlets(s.a_out, s.c_out)
+        sol.setup(s.A, s.B, s.C, s.D)
+        x = sol.solve(s.b.copy())
+        assert sol.residual() <= 1e-8
+    assert rel_residual(op, x, s.b) <= 1e-8
+    assert _rel(x, x_ref) <= 1e-6
+
+
+def test_outlet_option_checks(outlet_small):
+    s = outlet_small
+    with pkg.BlockSolver(precond=pkg.SCR_PC_SIMPLEC) as sol:
+        sol.set_outlets(s.a_out, s.c_out)
+        with pytest.raises(pkg.ScrError):
+            sol.setup(s.A, s.B, s.C, s.D)
+    with pkg.BlockSolver(nrhs=8) as sol:
+        sol.set_outlets(s.a_out, s.c_out)
+        with pytest.raises(pkg.ScrError):
+            sol.setup(s.A, s.B, s.C, s.D)
+    with pkg.BlockSolver() as sol:  # removing the outlets gives the sparse operator back
+        sol.set_outlets(s.a_out, s.c_out)
+        sol.set_outlets([], [])
+        sol.setup(s.A, s.B, s.C, s.D)
+        x = np.random.default_rng(7).standard_normal(3 * s.n_v + s.n_p)
+        y = sol.apply_op(_dev(x)).cpu().numpy()
+    op0 = BlockOperator(s.A, s.B, s.C, s.D)
+    assert _rel(y, op0.matvec(x)) < 1e-13
