@@ -247,6 +247,56 @@ int scr_solve_multi(scr_handle h, const double* const* b, double* const* x, int 
    nrhs != 1 or SCR_PC_SIMPLEC. */
 int scr_set_outlets(scr_handle h, int n_out, int len, const double* a, const double* c);
 
+/* Residual assembly on the GPU (Sec. 3.2 fluid and Sec. 3.5 solid element
+   residuals of the unified-continuum VMS formulation on linear tets, 4-point
+   Gauss rule; the element loop of the segregated multi-corrector step).
+   scr_assembly_setup copies the mesh (host arrays): node coordinates xyz
+   (3 n_nodes), velocity connectivity ien and pressure-index connectivity
+   pien (4 n_elem each, 0-based; pressure indices < n_p), element type (0
+   fluid, 1 solid) and the velocity Dirichlet flag per node (dir_v, may be
+   NULL).  scr_assemble_residual writes R = [R_m (3 n_nodes) | R_p (n_p)], the raw
+   residual before any Dirichlet rows, at the state v (3 n_nodes, at
+   t_{n+alpha_f}), p (n_p), vhat (mesh velocity), vdot (at t_{n+alpha_m})
+   and u (solid displacement); vhat, vdot and u may be NULL (zero).  Host
+   pointers when dev == 0, device pointers otherwise.  Every run adds the
+   same terms in the same order (per-element values, then a fixed-order sum
+   per row).  SCR_INVALID_ARG for NULL arrays, sizes < 0 or out-of-range
+   connectivity. */
+typedef struct {
+  int n_nodes, n_elem, n_p;
+  const double* xyz;
+  const int* ien;
+  const int* pien;
+  const unsigned char* etype;
+  const unsigned char* dir_v;
+} scr_mesh;
+typedef struct {
+  double rho_f, mu_f;        /* fluid density and dynamic viscosity */
+  double rho_s, E_s, nu_s;   /* solid density, Young's modulus, Poisson ratio */
+  double dt, rho_inf;        /* time step, generalized-alpha spectral radius */
+  double c_m_solid, c_c_solid; /* solid stabilisation constants */
+} scr_physics;
+int scr_assembly_setup(scr_handle h, const scr_mesh* m, const scr_physics* ph);
+int scr_assemble_residual(scr_handle h, const double* v, const double* vhat, const double* p,
+                          const double* vdot, const double* u, double* R, int dev);
+
+/* Segregated multi-corrector iterations (Sec. 3.5) on the GPU: with the
+   tangent of the last scr_setup held fixed (modified Newton) and the mesh
+   of scr_assembly_setup held fixed (no mesh-motion update inside the loop),
+   n_iter times: R = scr_assemble_residual at the state, b = -R with the
+   velocity Dirichlet rows zeroed, solve calA x = b (SCR-FGMRES + AMG, the
+   handle's options), then vdot += alpha_m x_v, v += alpha_f gamma dt x_v,
+   p += alpha_f gamma dt x_p, u += (alpha_f gamma dt)^2 / alpha_m x_v
+   (generalized-alpha weights from scr_physics.rho_inf and dt).  v, vdot, u
+   (3 n_nodes) and p (n_p) are updated in place (host pointers when dev ==
+   0, device pointers otherwise); res_norms (host, n_iter + 1 doubles)
+   receives ||b|| before each solve and after the last update.  Returns
+   SCR_NOT_CONVERGED if an inner solve missed rtol (the iterations still
+   run); SCR_INVALID_ARG without both set-ups on the same mesh or with
+   nrhs != 1. */
+int scr_corrector(scr_handle h, double* v, double* p, double* vdot, double* u, int n_iter, double* res_norms,
+                  int dev);
+
 /* Counters and timings (see scr_stats). */
 int scr_get_stats(scr_handle h, scr_stats* s);
 

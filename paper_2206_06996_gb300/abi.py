@@ -38,6 +38,17 @@ class Opts(C.Structure):
     ]
 
 
+class Mesh(C.Structure):
+    _fields_ = [("n_nodes", C.c_int), ("n_elem", C.c_int), ("n_p", C.c_int), ("xyz", C.c_void_p),
+                ("ien", C.c_void_p), ("pien", C.c_void_p), ("etype", C.c_void_p), ("dir_v", C.c_void_p)]
+
+
+class Physics(C.Structure):
+    _fields_ = [("rho_f", C.c_double), ("mu_f", C.c_double), ("rho_s", C.c_double), ("E_s", C.c_double),
+                ("nu_s", C.c_double), ("dt", C.c_double), ("rho_inf", C.c_double), ("c_m_solid", C.c_double),
+                ("c_c_solid", C.c_double)]
+
+
 class Bsr(C.Structure):
     _fields_ = [("nb_rows", C.c_int), ("nb_cols", C.c_int), ("br", C.c_int), ("bc", C.c_int),
                 ("nnzb", C.c_int), ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("val", C.c_void_p)]
@@ -76,7 +87,8 @@ EXPORTED = [
     "scr_apply_op", "scr_apply_pc", "scr_apply_schur", "scr_amg_apply", "scr_amg_levels",
     "scr_export", "scr_bsr_spmv", "scr_profile_begin", "scr_profile_end", "scr_bsr_spmv_noalloc",
     "scr_setup_batch", "scr_solve_batch", "scr_batch_residuals", "scr_tune_save", "scr_tune_load",
-    "scr_solve_multi", "scr_set_outlets",
+    "scr_solve_multi", "scr_set_outlets", "scr_assembly_setup", "scr_assemble_residual",
+    "scr_corrector",
 ]
 
 _lib = None

@@ -104,6 +104,22 @@ void add_scaled_squares(double* d, const double* a, double c, long long n, cudaS
   counters().launches++;
 }
 
+// b = -R on the first n entries with the rows of flagged nodes (3 rows per
+// node on the first nv3 entries) set to zero; mask may be null
+__global__ void k_neg_masked(const double* __restrict__ R, const unsigned char* __restrict__ mask,
+                             double* __restrict__ b, long long nv3, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  b[i] = (mask && i < nv3 && mask[i / 3]) ? 0.0 : -R[i];
+}
+void negate_masked(const double* R, const unsigned char* mask, double* b, long long nv3, long long n,
+                   cudaStream_t s) {
+  if (n == 0) return;
+  k_neg_masked<<<ceil_div(n, 256), 256, 0, s>>>(R, mask, b, nv3, n);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
 // y[i] = 1 / x[i]
 __global__ void k_recip(const double* __restrict__ x, double* __restrict__ y, long long n) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;

@@ -113,6 +113,28 @@ bool spmv_staged(int G, const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const E
 // stage wait ran out; 2: a tile exceeded its stage), cleared on read
 int staged_status_take(cudaStream_t s);
 
+// Residual assembly of the VMS formulation on the GPU (residual.cu): the
+// mesh and the (element, vertex) lists of every row live on the device;
+// evaluate() writes R = [R_m (3 n_nodes) | R_p (n_p)] (raw, before the
+// Dirichlet rows) for the state v, vhat, p, vdot, u (device pointers;
+// vhat, vdot, u may be null for zero).
+struct ResidualPhysics {
+  double rho_f, mu_f, rho_s, mu_s, dt, c_m_solid, c_c_solid;
+};
+struct ResidualAssembler {
+  int nn = 0, ne = 0, np = 0;
+  ResidualPhysics ph{};
+  double* d_xyz = nullptr;
+  int *d_ien = nullptr, *d_pien = nullptr;
+  unsigned char* d_etype = nullptr;
+  int *d_vptr = nullptr, *d_vent = nullptr, *d_pptr = nullptr, *d_pent = nullptr;
+  double* d_E = nullptr;
+  void setup(int nn, int ne, int np, const double* xyz, const int* ien, const int* pien,
+             const unsigned char* etype, const ResidualPhysics& ph, DeviceArena& a, cudaStream_t s);
+  void evaluate(const double* v, const double* vhat, const double* p, const double* vd, const double* u,
+                double* R, cudaStream_t s);
+};
+
 // y = epilogue([[A, B], [C, D]] x) in FP64 (the outer operator calA); nrhs
 // interleaved right-hand sides (1 or kSpmmCols)
 void block_op(const DBsr<double>& A, const DBsr<double>& B, const DBsr<double>& C,
@@ -147,6 +169,9 @@ template <typename T>
 void axpy_dev(const T* a, const double* dot, double c, T* y, long long n, cudaStream_t s);
 // d += c a .* a
 void add_scaled_squares(double* d, const double* a, double c, long long n, cudaStream_t s);
+// b = -R, zero on the velocity rows of flagged nodes (mask per node, may be null)
+void negate_masked(const double* R, const unsigned char* mask, double* b, long long nv3, long long n,
+                   cudaStream_t s);
 // y = 1 ./ x
 void reciprocal(const double* x, double* y, long long n, cudaStream_t s);
 // k vectors of length n one after another <-> interleaved (entry i of vector c

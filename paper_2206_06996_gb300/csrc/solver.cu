@@ -761,6 +761,14 @@ struct scr_ctx {
   double* out_a = nullptr;    // device, n_out x 3 n_v
   float* out_af = nullptr;    // FP32 copy (mixed precision)
   double* out_dot = nullptr;  // device, n_out scratch dots
+  // residual assembly (scr_assembly_setup)
+  ResidualAssembler ra;
+  std::unique_ptr<DeviceArena> rmats;
+  bool have_residual = false;
+  std::vector<unsigned char> dir_v;  // velocity Dirichlet flag per node (empty: none)
+  scr_physics phys{};
+  double* r_in = nullptr;  // host-path staging: v, vhat, p, vdot, u, R
+  unsigned char* d_dir = nullptr;  // device copy of dir_v
   // batched form: member sizes and offsets inside the union system
   int nbatch = 0;
   std::vector<int> b_nv, b_np, b_vo, b_po;
@@ -1919,6 +1927,133 @@ int scr_export(scr_handle h, int which, int level, int kind, scr_bsr_out* out) {
     SCR_CUDA(cudaMemcpyAsync(out->val, v, sizeof(double) * nv, cudaMemcpyDeviceToHost, h->s));
     SCR_CUDA(cudaStreamSynchronize(h->s));
   });
+}
+
+int scr_assembly_setup(scr_handle h, const scr_mesh* m, const scr_physics* ph) {
+  if (!h || !m || !ph || m->n_nodes < 0 || m->n_elem < 0 || m->n_p < 0 ||
+      (m->n_elem > 0 && (!m->ien || !m->pien || !m->etype)) || (m->n_nodes > 0 && !m->xyz)) {
+    set_last_error("scr_assembly_setup: NULL argument or negative size");
+    return SCR_INVALID_ARG;
+  }
+  return guarded([&] {
+    if (!(ph->rho_s > 0.0) || !(ph->E_s > 0.0) || !(ph->dt > 0.0) || !(ph->rho_f > 0.0))
+      throw std::invalid_argument("scr_assembly_setup: densities, modulus and time step must be positive");
+    cudaStream_t s = h->s;
+    h->have_residual = false;
+    h->rmats.reset(new DeviceArena(s));
+    ResidualPhysics rp{ph->rho_f, ph->mu_f, ph->rho_s, ph->E_s / (2.0 * (1.0 + ph->nu_s)), ph->dt,
+                       ph->c_m_solid, ph->c_c_solid};
+    h->ra.setup(m->n_nodes, m->n_elem, m->n_p, m->xyz, m->ien, m->pien, m->etype, rp, *h->rmats, s);
+    if (m->dir_v) h->dir_v.assign(m->dir_v, m->dir_v + m->n_nodes);
+    else h->dir_v.clear();
+    h->phys = *ph;
+    const long long nv3 = 3LL * m->n_nodes;
+    // staging for the host path: v, vhat, vdot, u (3 n_nodes each), p (n_p), R (3 n_nodes + n_p)
+    h->r_in = h->rmats->alloc<double>(5 * nv3 + 2LL * m->n_p + 1);
+    h->d_dir = nullptr;
+    if (!h->dir_v.empty()) {
+      h->d_dir = h->rmats->alloc<unsigned char>(h->dir_v.size());
+      SCR_CUDA(cudaMemcpyAsync(h->d_dir, h->dir_v.data(), h->dir_v.size(), cudaMemcpyHostToDevice, s));
+      SCR_CUDA(cudaStreamSynchronize(s));
+    }
+    h->have_residual = true;
+  });
+}
+
+int scr_assemble_residual(scr_handle h, const double* v, const double* vhat, const double* p,
+                          const double* vdot, const double* u, double* R, int dev) {
+  if (!h || !v || !p || !R) return SCR_INVALID_ARG;
+  if (!h->have_residual) {
+    set_last_error("scr_assemble_residual before scr_assembly_setup");
+    return SCR_INVALID_ARG;
+  }
+  return guarded([&] {
+    cudaStream_t s = h->s;
+    const long long nv3 = 3LL * h->ra.nn, np = h->ra.np;
+    if (dev) {
+      h->ra.evaluate(v, vhat, p, vdot, u, R, s);
+    } else {
+      double* dv = h->r_in;
+      double* dvh = dv + nv3;
+      double* dvd = dvh + nv3;
+      double* du = dvd + nv3;
+      double* dp = du + nv3;
+      double* dR = dp + np;  // 3 n_nodes + n_p
+      auto in = [&](const double* src, double* dst, long long n) -> const double* {
+        if (!src) return nullptr;
+        SCR_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        return dst;
+      };
+      const double* a = in(v, dv, nv3);
+      const double* b = in(vhat, dvh, nv3);
+      const double* c = in(vdot, dvd, nv3);
+      const double* d = in(u, du, nv3);
+      const double* e = in(p, dp, np);
+      h->ra.evaluate(a, b, e, c, d, dR, s);
+      SCR_CUDA(cudaMemcpyAsync(R, dR, sizeof(double) * (nv3 + np), cudaMemcpyDeviceToHost, s));
+    }
+    SCR_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+int scr_corrector(scr_handle h, double* v, double* p, double* vdot, double* u, int n_iter, double* res_norms,
+                  int dev) {
+  if (!h || !v || !p || !vdot || !u || n_iter < 0 || !res_norms) return SCR_INVALID_ARG;
+  if (!h->have_block || !h->have_residual || h->k != 1 || h->ra.nn != h->nv || h->ra.np != h->np) {
+    set_last_error("scr_corrector: needs scr_setup (nrhs = 1) and scr_assembly_setup on the same mesh");
+    return SCR_INVALID_ARG;
+  }
+  int status = SCR_OK;
+  int rc = guarded([&] {
+    cudaStream_t s = h->s;
+    const long long nv3 = 3LL * h->nv, np = h->np, n = nv3 + np;
+    // generalized-alpha weights of the rate increments (Sec. 3.4)
+    const double rho = h->phys.rho_inf;
+    const double am = 0.5 * (3.0 - rho) / (1.0 + rho), af = 1.0 / (1.0 + rho), ga = af;
+    const double cf = af * ga * h->phys.dt, cu = cf * cf / am;
+    // state on the device
+    double *dv = v, *dp = p, *dvd = vdot, *du = u;
+    if (!dev) {
+      dv = h->r_in;
+      dvd = dv + nv3;
+      du = dvd + nv3;
+      dp = du + nv3;
+      SCR_CUDA(cudaMemcpyAsync(dv, v, sizeof(double) * nv3, cudaMemcpyHostToDevice, s));
+      SCR_CUDA(cudaMemcpyAsync(dvd, vdot, sizeof(double) * nv3, cudaMemcpyHostToDevice, s));
+      SCR_CUDA(cudaMemcpyAsync(du, u, sizeof(double) * nv3, cudaMemcpyHostToDevice, s));
+      SCR_CUDA(cudaMemcpyAsync(dp, p, sizeof(double) * np, cudaMemcpyHostToDevice, s));
+    }
+    double* R = h->r_in + 4 * nv3 + np;  // 3 n_nodes + n_p
+    ArnoldiState* st = h->gOuter.st;
+    for (int it = 0; it <= n_iter; ++it) {
+      h->ra.evaluate(dv, nullptr, dp, dvd, du, R, s);
+      negate_masked(R, h->d_dir, h->bvec, nv3, n, s);
+      norm2<double>(h->bvec, n, &st->nrm2, h->red, s);
+      double r2 = 0.0;
+      SCR_CUDA(cudaMemcpyAsync(&r2, &st->nrm2, sizeof(double), cudaMemcpyDeviceToHost, s));
+      SCR_CUDA(cudaStreamSynchronize(s));
+      res_norms[it] = std::sqrt(r2);
+      if (it == n_iter) break;
+      const int st_solve = solve_impl(h, h->bvec, h->xvec, h->o.rtol);
+      if (st_solve != SCR_OK) status = st_solve;
+      // rates at t_{n+alpha_m} move by alpha_m, values at t_{n+alpha_f} by
+      // alpha_f gamma dt, the solid displacement by (alpha_f gamma dt)^2 / alpha_m
+      axpby(am, h->xvec, 1.0, dvd, nv3, s);
+      axpby(cf, h->xvec, 1.0, dv, nv3, s);
+      axpby(cu, h->xvec, 1.0, du, nv3, s);
+      axpby(cf, h->xvec + nv3, 1.0, dp, np, s);
+    }
+    if (!dev) {
+      SCR_CUDA(cudaMemcpyAsync(v, dv, sizeof(double) * nv3, cudaMemcpyDeviceToHost, s));
+      SCR_CUDA(cudaMemcpyAsync(vdot, dvd, sizeof(double) * nv3, cudaMemcpyDeviceToHost, s));
+      SCR_CUDA(cudaMemcpyAsync(u, du, sizeof(double) * nv3, cudaMemcpyDeviceToHost, s));
+      SCR_CUDA(cudaMemcpyAsync(p, dp, sizeof(double) * np, cudaMemcpyDeviceToHost, s));
+    }
+    SCR_CUDA(cudaStreamSynchronize(s));
+    check_staged(h);
+  });
+  if (rc != SCR_OK) return rc;
+  return status;
 }
 
 int scr_set_outlets(scr_handle h, int n_out, int len, const double* a, const double* c) {

@@ -7,8 +7,8 @@ import os
 
 import numpy as np
 
-from .abi import (BsrOut, Bsr, KProf, Opts, SCR_NOT_CONVERGED, SCR_OK, ScrError, Stats, check,
-                  load_library)
+from .abi import (BsrOut, Bsr, KProf, Mesh, Opts, Physics, SCR_NOT_CONVERGED, SCR_OK, ScrError, Stats,
+                  check, load_library)
 
 
 def _torch():
@@ -204,6 +204,50 @@ class BlockSolver:
         st = self.lib.scr_solve_batch(self.h, pb, px, devs.pop())
         check(st, (SCR_OK,) if raise_on_nonconvergence else (SCR_OK, SCR_NOT_CONVERGED))
         return xs
+
+    def assembly_setup(self, mesh, params: dict):
+        """Upload a mesh (arrays xyz, ien, pien, etype, dir_v, sizes
+        n_nodes, n_elem, n_p) and the physical parameters for scr_residual."""
+        keep = [np.ascontiguousarray(mesh.xyz, dtype=np.float64), np.ascontiguousarray(mesh.ien, dtype=np.int32),
+                np.ascontiguousarray(mesh.pien, dtype=np.int32), np.ascontiguousarray(mesh.etype, dtype=np.uint8),
+                np.ascontiguousarray(mesh.dir_v, dtype=np.uint8)]
+        m = Mesh(mesh.n_nodes, mesh.n_elem, mesh.n_p, *(k.ctypes.data_as(C.c_void_p) for k in keep))
+        ph = Physics(*(float(params[f]) for f, _ in Physics._fields_))
+        check(self.lib.scr_assembly_setup(self.h, C.byref(m), C.byref(ph)))
+        self._res_sizes = (mesh.n_nodes, mesh.n_p)
+
+    def assemble_residual(self, v, p, vhat=None, vdot=None, u=None):
+        """R = [R_m | R_p] at the state (numpy in -> numpy out, CUDA tensors
+        in -> CUDA tensor out)."""
+        nn, np_ = self._res_sizes
+        keep: list = []
+        pv, dev = _ptr(v, keep)
+        pp, _ = _ptr(p, keep)
+        opt = [(_ptr(a, keep)[0] if a is not None else None) for a in (vhat, vdot, u)]
+        if dev:
+            R = _torch().empty(3 * nn + np_, dtype=_torch().float64, device=v.device)
+        else:
+            R = np.empty(3 * nn + np_)
+        pr, _ = _ptr(R, keep)
+        vp = lambda a: None if a is None else C.c_void_p(a)
+        check(self.lib.scr_assemble_residual(self.h, vp(pv), vp(opt[0]), vp(pp), vp(opt[1]), vp(opt[2]), vp(pr), dev))
+        return R
+
+    def corrector(self, v, p, vdot, u, n_iter: int):
+        """n_iter multi-corrector iterations on the state (updated in place:
+        numpy arrays or CUDA tensors); returns the residual norms."""
+        keep: list = []
+        ptrs = [_ptr(a, keep) for a in (v, p, vdot, u)]
+        devs = {d for _, d in ptrs}
+        if len(devs) != 1:
+            raise ValueError("state vectors must all be host or all device")
+        if not devs.pop() and any(k is not a for k, a in zip(keep, (v, p, vdot, u))):
+            raise TypeError("host state vectors must be contiguous float64 arrays (updated in place)")
+        norms = np.zeros(n_iter + 1)
+        st = self.lib.scr_corrector(self.h, *(C.c_void_p(q) for q, _ in ptrs), int(n_iter),
+                                    norms.ctypes.data_as(C.c_void_p), ptrs[0][1])
+        check(st, (SCR_OK, SCR_NOT_CONVERGED))
+        return norms
 
     def set_outlets(self, a_out, c_out):
         """Rank-1 outlet terms for the next setup: vectors a_j (3 n_v each)

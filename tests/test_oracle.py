@@ -527,3 +527,23 @@ def test_outlet_term_in_the_block_operator():
     x, info = sol.solve(s.b)
     assert info.converged and rel_residual(op, x, s.b) <= 1e-8
     assert np.linalg.norm(x - x_ref) <= 1e-6 * np.linalg.norm(x_ref)
+
+
+# ---------------------------------------------------------------- multi-corrector
+def test_corrector_starts_from_the_system_rhs_and_contracts():
+    """The oracle's corrector evaluates b = -R at the assembly state, which is
+    the block system's right-hand side; with the consistent tangent
+    (alpha_m dR/dvdot + alpha_f gamma dt dR/dy, frozen tau) and the matching
+    generalized-alpha updates the residual drops by orders of magnitude per
+    iteration (a wrong weight or sign in the update would stall it)."""
+    from oracle import corrector
+    s = F.tube_system("tube_mini", keep_mesh=True)
+    asm = F.Assembler(F.make_params(**F.PRESETS["tube_mini"]))
+    v, p = asm.initial_state()
+    nn = s.mesh.n_nodes
+    *_, norms = corrector.corrector(s, asm, v, p, np.zeros(3 * nn), np.zeros(3 * nn), 3)
+    assert norms[0] == pytest.approx(np.linalg.norm(s.b), rel=1e-13)
+    assert norms[1] < 1e-3 * norms[0] and norms[2] < 1e-2 * norms[1] and norms[3] < norms[2]
+    am, cf, cu = corrector.genalpha_weights(0.5, 1e-4)
+    assert am == pytest.approx(5.0 / 6.0) and cf == pytest.approx(4.0 / 9.0 * 1e-4)
+    assert cu == pytest.approx(cf * cf / am)
