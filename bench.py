@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--multi-rhs", action="store_true",
                     help="also time eight right-hand sides (inflow peaks U(0, 60) cm/s, one Jacobian) solved as one "
                          "8-column block solve in mixed precision against the same eight solved one by one")
+    ap.add_argument("--assembly", action="store_true",
+                    help="also time the GPU residual assembly (element loop) and one multi-corrector iteration "
+                         "(residual, FP64 solve, updates) on the workload's mesh")
     ap.add_argument("--batched", action="store_true",
                     help="also time the 64-tube batched form (mixed, one block-diagonal solve) against the "
                          "same 64 tubes solved one by one in FP64")
@@ -381,6 +384,40 @@ def main():
                    "fp64_one_by_one_ms": mss, "speedup_vs_fp64_one_by_one": mss / msb,
                    "max_member_rel_res": float(relb.max())}
 
+    assembly = None
+    if args.assembly:
+        sm = F.tube_system(args.workload, keep_mesh=True)
+        asm_h = F.Assembler(F.make_params(**F.PRESETS[args.workload]))
+        v0, p0 = asm_h.initial_state()
+        asm_h.close()
+        sola = pkg.BlockSolver()
+        sola.assembly_setup(sm.mesh, sm.params)
+        vd0 = torch.zeros(3 * sm.mesh.n_nodes, dtype=torch.float64, device=dev)
+        vt, pt = torch.as_tensor(v0, device=dev), torch.as_tensor(p0, device=dev)
+        for _ in range(3):
+            sola.assemble_residual(vt, pt, vdot=vd0, u=vd0)
+        torch.cuda.synchronize(dev)
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        for _ in range(10):
+            sola.assemble_residual(vt, pt, vdot=vd0, u=vd0)
+        eb.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_res = ea.elapsed_time(eb) / 10
+        sola.setup(Ad, Bd, Cd, Dd)
+        vc, pc, vdc, uc = vt.clone(), pt.clone(), vd0.clone(), vd0.clone()
+        torch.cuda.synchronize(dev)
+        ea.record(stream)
+        norms = sola.corrector(vc, pc, vdc, uc, 1)
+        eb.record(stream)
+        torch.cuda.synchronize(dev)
+        sola.close()
+        assembly = {"elements": int(sm.mesh.n_elem), "residual_ms": ms_res,
+                    "elements_per_s": sm.mesh.n_elem * 1000.0 / ms_res,
+                    "corrector_iteration_ms": ea.elapsed_time(eb),
+                    "corrector_residual_drop": float(norms[1] / norms[0])}
+        del sm
+
     multi = None
     if args.multi_rhs:
         peaks_u = np.random.default_rng(2206).uniform(0.0, 60.0, 8)
@@ -475,7 +512,7 @@ def main():
         "mesh_iters": st["mm_iters"], "setup_ms": st["setup_ms"], "solve_ms": st["solve_ms"],
         "mm_setup_ms": st["mm_setup_ms"], "mm_solve_ms": st["mm_solve_ms"],
         "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "mixed": mixed,
-        "batched": batched, "multi_rhs": multi,
+        "batched": batched, "multi_rhs": multi, "assembly": assembly,
         "clocks": clocks, "inputs_build_s": t_in,
     }
     if args.tune_file and not tune_loaded and rank == 0:
