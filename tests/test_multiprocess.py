@@ -1,0 +1,61 @@
+"""The N > 1 host logic of bench.py on CPU ranks (gloo, world size 2): the
+path does not partition a solve (replicas), so the only cross-rank steps are
+the barrier around the timed region and the max over ranks of the step time
+that gives the whole-job throughput."""
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank: int, world: int, port: int, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import bench
+    w, r, local, pg = bench.dist_init("gloo")
+    try:
+        bench.barrier(pg)
+        ms_local = 100.0 + 50.0 * r  # rank 1 is the slow one
+        ms, value = bench.job_value(pg, ms_local, w, torch.device("cpu"))
+        bench.barrier(pg)
+        out.put((r, w, ms, value))
+    finally:
+        pg.destroy_process_group()
+
+
+def test_two_cpu_ranks_time_by_the_slowest_rank():
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(out.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r for r, *_ in res] == [0, 1]
+    for _, w, ms, value in res:
+        assert w == 2 and ms == 150.0 and value == pytest.approx(2 * 1000.0 / 150.0)
+
+
+def test_single_process_needs_no_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.pop("WORLD_SIZE", None)
+    w, r, local, pg = bench.dist_init()
+    assert (w, r, pg) == (1, 0, None)
+    assert bench.job_value(pg, 80.0, 1, torch.device("cpu")) == (80.0, 12.5)
