@@ -283,8 +283,9 @@ int scr_assemble_residual(scr_handle h, const double* v, const double* vhat, con
 /* Segregated multi-corrector iterations (Sec. 3.5) on the GPU: with the
    tangent of the last scr_setup held fixed (modified Newton) and the mesh
    of scr_assembly_setup held fixed (no mesh-motion update inside the loop),
-   n_iter times: R = scr_assemble_residual at the state, b = -R with the
-   velocity Dirichlet rows zeroed, solve calA x = b (SCR-FGMRES + AMG, the
+   n_iter times: R = scr_assemble_residual at the state (plus the outlet
+   tractions m_j (a_j^T v) a_j of scr_set_outlets, with m_j = c_j / (alpha_f
+   gamma dt)), b = -R with the velocity Dirichlet rows zeroed, solve calA x = b (SCR-FGMRES + AMG, the
    handle's options), then vdot += alpha_m x_v, v += alpha_f gamma dt x_v,
    p += alpha_f gamma dt x_p, u += (alpha_f gamma dt)^2 / alpha_m x_v
    (generalized-alpha weights from scr_physics.rho_inf and dt).  v, vdot, u

@@ -9,7 +9,9 @@ velocity rows of the right-hand side zeroed) exactly, and moves the state by
 the generalized-alpha weights of the rate increment (Sec. 3.4):
 vdot += alpha_m x_v, v += alpha_f gamma dt x_v, p += alpha_f gamma dt x_p,
 u += (alpha_f gamma dt)^2 / alpha_m x_v.  The residual is the generator's
-element loop (the input module's assembly of the VMS formulation).
+element loop (the input module's assembly of the VMS formulation), plus the
+traction m_k (a_k^T v) a_k of resistance outlets (Sec. 3.5: its derivative
+is the rank-1 term c_k a_k a_k^T of the tangent, c_k = alpha_f gamma dt m_k).
 """
 from __future__ import annotations
 
@@ -38,9 +40,15 @@ def corrector(system, assembler, v, p, vdot, u, n_iter: int):
     dirichlet = np.repeat(np.asarray(system.mesh.dir_v, dtype=bool), 3)
     nv3 = v.size
     norms = []
+    a_out = getattr(system, "a_out", None) or []
+    c_out = getattr(system, "c_out", None) or []
     for it in range(n_iter + 1):
         R = assembler.evaluate(v, p, vd=vdot, u=u, want_mat=False)
-        b = -np.concatenate([R["Rm"], R["Rp"]])
+        Rm = R["Rm"].copy()
+        # resistance outlets: traction m_k (a_k^T v) a_k, m_k = c_k / c_f
+        for a, c in zip(a_out, c_out):
+            Rm += (c / cf) * float(a @ v) * a
+        b = -np.concatenate([Rm, R["Rp"]])
         b[:nv3][dirichlet] = 0.0
         norms.append(float(np.linalg.norm(b)))
         if it == n_iter:

@@ -2027,6 +2027,10 @@ int scr_corrector(scr_handle h, double* v, double* p, double* vdot, double* u, i
     ArnoldiState* st = h->gOuter.st;
     for (int it = 0; it <= n_iter; ++it) {
       h->ra.evaluate(dv, nullptr, dp, dvd, du, R, s);
+      // resistance outlets: the traction P_j a_j with P_j = m_j (a_j^T v)
+      // (the term whose derivative is the rank-1 tangent c_j a_j a_j^T,
+      // c_j = alpha_f gamma dt m_j)
+      if (h->n_out) outlet_terms<double>(h, h->out_a, dv, R, 1.0 / cf);
       negate_masked(R, h->d_dir, h->bvec, nv3, n, s);
       norm2<double>(h->bvec, n, &st->nrm2, h->red, s);
       double r2 = 0.0;

@@ -884,3 +884,24 @@ def test_gpu_corrector_matches_the_oracle_loop(small, precision):
         assert _rel(a, b) < 1e-7
     np.testing.assert_array_equal(norms, norms_d)
     np.testing.assert_array_equal(v, dv.cpu().numpy())
+
+
+def test_gpu_corrector_with_a_resistance_outlet(outlet_small):
+    """Corrector with the outlet traction in the residual and the rank-1 term
+    in the tangent: follows the oracle's loop and contracts."""
+    from oracle import corrector
+    s = F.tube_system("tube_small", keep_mesh=True, outlet_resistance=2.7e4)
+    asm = F.Assembler(F.make_params(**F.PRESETS["tube_small"]))
+    v0, p0 = asm.initial_state()
+    z = np.zeros(3 * s.mesh.n_nodes)
+    vr, pr, _, _, nr = corrector.corrector(s, asm, v0, p0, z, z, 2)
+    with pkg.BlockSolver() as sol:
+        sol.set_outlets(s.a_out, s.c_out)
+        sol.setup(s.A, s.B, s.C, s.D)
+        sol.assembly_setup(s.mesh, s.params)
+        v, p, vd, u = v0.copy(), p0.copy(), z.copy(), z.copy()
+        norms = sol.corrector(v, p, vd, u, 2)
+    assert norms[0] == pytest.approx(nr[0], rel=1e-12)
+    assert norms[1] == pytest.approx(nr[1], rel=1e-3) and norms[2] < 1e-2 * norms[1]
+    assert _rel(v, vr) < 1e-7 and _rel(p, pr) < 1e-7
+    del outlet_small

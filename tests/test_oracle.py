@@ -547,3 +547,17 @@ def test_corrector_starts_from_the_system_rhs_and_contracts():
     am, cf, cu = corrector.genalpha_weights(0.5, 1e-4)
     assert am == pytest.approx(5.0 / 6.0) and cf == pytest.approx(4.0 / 9.0 * 1e-4)
     assert cu == pytest.approx(cf * cf / am)
+
+
+def test_corrector_with_a_resistance_outlet_contracts():
+    """With the outlet traction in the residual and its rank-1 derivative in
+    the tangent, the corrector starts from the system's right-hand side and
+    contracts as fast as without outlets."""
+    from oracle import corrector
+    s = F.tube_system("tube_mini", keep_mesh=True, outlet_resistance=2.7e4)
+    asm = F.Assembler(F.make_params(**F.PRESETS["tube_mini"]))
+    v, p = asm.initial_state()
+    nn = s.mesh.n_nodes
+    *_, norms = corrector.corrector(s, asm, v, p, np.zeros(3 * nn), np.zeros(3 * nn), 2)
+    assert norms[0] == pytest.approx(np.linalg.norm(s.b), rel=1e-12)
+    assert norms[1] < 1e-3 * norms[0] and norms[2] < 1e-2 * norms[1]
