@@ -200,12 +200,12 @@ def cpu_threads() -> int:
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle as it stands, on the host cores."""
-    world, rank, local, pg = dist_init()
-    if rank != 0:
+    """Reference arm: the CPU oracle as it stands, on the host cores.  Under
+    torchrun only rank 0 runs it (no process group is needed); the other
+    ranks exit without work."""
+    if int(os.environ.get("RANK", "0")) != 0:
         return
     import fsi_inputs as F
-    n_large = 3 * F.build_mesh(F.make_params(**F.PRESETS[args.workload])).n_nodes
     m = F.build_mesh(F.make_params(**F.PRESETS[args.workload]))
     n_large = 3 * m.n_nodes + m.n_p
     for _ in range(args.warmup):

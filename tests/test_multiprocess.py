@@ -59,3 +59,14 @@ def test_single_process_needs_no_group():
     w, r, local, pg = bench.dist_init()
     assert (w, r, pg) == (1, 0, None)
     assert bench.job_value(pg, 80.0, 1, torch.device("cpu")) == (80.0, 12.5)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    """bench.py --impl reference under torchrun: ranks other than 0 print
+    nothing and do no work."""
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setattr(bench, "oracle_step_sample", lambda *a, **k: pytest.fail("rank 1 must not run the oracle"))
+    bench.run_reference(type("A", (), {"workload": "tube_large", "warmup": 1, "steps": 1, "gpus": 2})())
+    assert capsys.readouterr().out == ""
