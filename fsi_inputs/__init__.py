@@ -340,6 +340,16 @@ def tube_system(name: str = "tube_small", threads: int = 0, keep_mesh: bool = Fa
         L.tg_mesh_free(pm)
 
 
+def interface_follow(mesh: Mesh) -> np.ndarray:
+    """Per fluid node: 1 where the node is a Dirichlet mesh node on the
+    fluid-solid interface (its mesh displacement is the wall's), 0 on the
+    other fluid nodes (inlet and outlet sections, the interior)."""
+    follow = np.zeros(mesh.n_fluid, dtype=np.uint8)
+    nodes = np.flatnonzero(mesh.fluid_id >= 0)
+    follow[mesh.fluid_id[nodes]] = mesh.iface_of[nodes] >= 0
+    return follow & mesh.dir_m.astype(np.uint8)
+
+
 def outlet_vector(mesh: Mesh, n_ax: int, zero_dirichlet: bool = True) -> np.ndarray:
     """a_{A,i} = int_{outlet} N_A n_i dGamma over the fluid outlet section
     (the faces of fluid tets with all three vertices on the last axial

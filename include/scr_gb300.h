@@ -298,6 +298,39 @@ int scr_assemble_residual(scr_handle h, const double* v, const double* vhat, con
 int scr_corrector(scr_handle h, double* v, double* p, double* vdot, double* u, int n_iter, double* res_norms,
                   int dev);
 
+/* Mesh motion for scr_corrector_ale (Sec. 3.5, steps 3-4; Sec. 5.2.2).
+   After scr_assembly_setup.  n_fluid fluid nodes; fluid_id (n_nodes of the
+   assembly mesh) maps a node to its fluid ordinal or -1, every ordinal used
+   exactly once; dir_m (n_fluid) flags the Dirichlet mesh nodes; follow
+   (n_fluid) flags those that take the solid displacement of their node (the
+   fluid-solid interface; the other Dirichlet nodes are held at zero), and
+   follow without dir_m is an error; L_raw (n_fluid x n_fluid, 1x1 blocks)
+   is the mesh Laplacian WITHOUT boundary conditions, used to lift the
+   Dirichlet data into the right-hand side of the eliminated system that
+   mm_setup received.  All arrays are host memory, copied (the caller keeps
+   ownership).  SCR_INVALID_ARG on NULL, sizes or maps that do not fit. */
+int scr_mesh_coupling(scr_handle h, int n_fluid, const int* fluid_id, const unsigned char* dir_m,
+                      const unsigned char* follow, const scr_bsr* L_raw);
+
+/* scr_corrector with the mesh moving inside the loop (Sec. 3.5, steps 3-4).
+   The state enters at the same-Y predictor, so u at entry is u_n.  Before
+   every residual evaluation: u_{n+1} = u_n + (u - u_n) / alpha_f; the
+   Dirichlet data g (u_{n+1} on follow nodes, zero on the other Dirichlet
+   mesh nodes); uhat_{n+1} from CG + AMG (mm_setup's hierarchy, mm_rtol) on
+   the eliminated mesh system with right-hand side g on Dirichlet rows and
+   -(L_raw g) on the free rows; vhat_{n+1} = (uhat_{n+1} - uhat_n) / (gamma
+   dt) + (gamma - 1) / gamma vhat_n and vhat_{n+alpha_f} = vhat_n + alpha_f
+   (vhat_{n+1} - vhat_n) at the fluid nodes (zero elsewhere), passed to the
+   residual as the mesh velocity.  The element geometry stays that of
+   scr_assembly_setup.  uhat_n, vhat_n (may be NULL: zero) and uhat (out:
+   uhat_{n+1} after the last update) have 3 n_fluid interleaved entries, host
+   or device like the state (dev).  Returns SCR_NOT_CONVERGED if an inner
+   block solve or a mesh solve missed its tolerance (the iterations still
+   run); SCR_INVALID_ARG without scr_mesh_coupling and mm_setup on the same
+   n_fluid, or as scr_corrector. */
+int scr_corrector_ale(scr_handle h, double* v, double* p, double* vdot, double* u, const double* uhat_n,
+                      const double* vhat_n, double* uhat, int n_iter, double* res_norms, int dev);
+
 /* Counters and timings (see scr_stats). */
 int scr_get_stats(scr_handle h, scr_stats* s);
 

@@ -88,7 +88,7 @@ EXPORTED = [
     "scr_export", "scr_bsr_spmv", "scr_profile_begin", "scr_profile_end", "scr_bsr_spmv_noalloc",
     "scr_setup_batch", "scr_solve_batch", "scr_batch_residuals", "scr_tune_save", "scr_tune_load",
     "scr_solve_multi", "scr_set_outlets", "scr_assembly_setup", "scr_assemble_residual",
-    "scr_corrector",
+    "scr_corrector", "scr_mesh_coupling", "scr_corrector_ale",
 ]
 
 _lib = None

@@ -120,6 +120,66 @@ void negate_masked(const double* R, const unsigned char* mask, double* b, long l
   counters().launches++;
 }
 
+// Dirichlet data of the mesh-motion problem at t_{n+1}: the interface nodes
+// take the solid displacement u_{n+1} = u_n + (u_{n+alpha_f} - u_n) / alpha_f
+// of their node, the other Dirichlet nodes zero (the entries of free nodes
+// are never read as data: mesh_lift keeps g only on Dirichlet rows)
+__global__ void k_mesh_data(const int* __restrict__ node_of_f, const unsigned char* __restrict__ follow,
+                            const double* __restrict__ u, const double* __restrict__ un, double af,
+                            double* __restrict__ g, long long n3) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  const long long f = i / 3, c = i - 3 * f;
+  const long long j = 3LL * node_of_f[f] + c;
+  g[i] = follow[f] ? un[j] + (u[j] - un[j]) / af : 0.0;
+}
+void mesh_interface_data(const int* node_of_f, const unsigned char* follow, const double* u, const double* un,
+                         double af, double* g, int nf, cudaStream_t s) {
+  const long long n3 = 3LL * nf;
+  if (n3 == 0) return;
+  k_mesh_data<<<ceil_div(n3, 256), 256, 0, s>>>(node_of_f, follow, u, un, af, g, n3);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
+// right-hand side of the Dirichlet-eliminated mesh system: g on Dirichlet
+// rows, -(L_raw g) on the free rows (the lift of the boundary data)
+__global__ void k_mesh_lift(const unsigned char* __restrict__ dir_m, const double* __restrict__ g,
+                            double* __restrict__ b, long long n3) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  b[i] = dir_m[i / 3] ? g[i] : -b[i];
+}
+void mesh_lift(const unsigned char* dir_m, const double* g, double* b, int nf, cudaStream_t s) {
+  const long long n3 = 3LL * nf;
+  if (n3 == 0) return;
+  k_mesh_lift<<<ceil_div(n3, 256), 256, 0, s>>>(dir_m, g, b, n3);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
+// mesh velocity at t_{n+1} from the displacements, then at t_{n+alpha_f}
+// (generalized-alpha, Sec. 3.4), written at the fluid nodes
+__global__ void k_mesh_velocity(const int* __restrict__ node_of_f, const double* __restrict__ uh,
+                                const double* __restrict__ uhn, const double* __restrict__ vn, double af,
+                                double gdt, double cv, double* __restrict__ vhat, long long n3) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n3) return;
+  const long long f = i / 3, c = i - 3 * f;
+  const double v0 = vn[i];
+  const double v1 = (uh[i] - uhn[i]) / gdt + cv * v0;
+  vhat[3LL * node_of_f[f] + c] = v0 + af * (v1 - v0);
+}
+void mesh_velocity(const int* node_of_f, const double* uh, const double* uhn, const double* vn, double af,
+                   double gamma, double dt, double* vhat, int nf, cudaStream_t s) {
+  const long long n3 = 3LL * nf;
+  if (n3 == 0) return;
+  k_mesh_velocity<<<ceil_div(n3, 256), 256, 0, s>>>(node_of_f, uh, uhn, vn, af, gamma * dt,
+                                                    (gamma - 1.0) / gamma, vhat, n3);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
 // y[i] = 1 / x[i]
 __global__ void k_recip(const double* __restrict__ x, double* __restrict__ y, long long n) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;

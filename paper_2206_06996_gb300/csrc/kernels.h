@@ -172,6 +172,16 @@ void add_scaled_squares(double* d, const double* a, double c, long long n, cudaS
 // b = -R, zero on the velocity rows of flagged nodes (mask per node, may be null)
 void negate_masked(const double* R, const unsigned char* mask, double* b, long long nv3, long long n,
                    cudaStream_t s);
+// Mesh motion inside the corrector (Sec. 3.5, steps 3-4), one thread per
+// (fluid node f, component c), entries 3 f + c.
+// g = follow_f ? un + (u - un) / af at node_of_f[f] : 0
+void mesh_interface_data(const int* node_of_f, const unsigned char* follow, const double* u, const double* un,
+                         double af, double* g, int nf, cudaStream_t s);
+// b = g on Dirichlet mesh nodes, -b (b holds L_raw g on entry) elsewhere
+void mesh_lift(const unsigned char* dir_m, const double* g, double* b, int nf, cudaStream_t s);
+// vhat[node_of_f[f]] = vn + af (v1 - vn), v1 = (uh - uhn) / (gamma dt) + (gamma - 1) / gamma vn
+void mesh_velocity(const int* node_of_f, const double* uh, const double* uhn, const double* vn, double af,
+                   double gamma, double dt, double* vhat, int nf, cudaStream_t s);
 // y = 1 ./ x
 void reciprocal(const double* x, double* y, long long n, cudaStream_t s);
 // k vectors of length n one after another <-> interleaved (entry i of vector c

@@ -769,6 +769,17 @@ struct scr_ctx {
   scr_physics phys{};
   double* r_in = nullptr;  // host-path staging: v, vhat, p, vdot, u, R
   unsigned char* d_dir = nullptr;  // device copy of dir_v
+  // mesh motion inside the corrector (scr_mesh_coupling): the fluid nodes'
+  // mesh Laplacian without boundary conditions, their node numbers, the
+  // Dirichlet and interface flags, and the loop's vectors
+  std::unique_ptr<DeviceArena> cmats;
+  bool have_coupling = false;
+  int cpl_nf = 0, cpl_nn = 0;
+  DBsr<double> Lraw;
+  int* d_node_of_f = nullptr;
+  unsigned char *d_dir_m = nullptr, *d_follow = nullptr;
+  double *d_g = nullptr, *d_lift = nullptr, *d_uh = nullptr, *d_uhn = nullptr, *d_vhn = nullptr;
+  double *d_un = nullptr, *d_vhat = nullptr;
   // batched form: member sizes and offsets inside the union system
   int nbatch = 0;
   std::vector<int> b_nv, b_np, b_vo, b_po;
@@ -1996,14 +2007,28 @@ int scr_assemble_residual(scr_handle h, const double* v, const double* vhat, con
   });
 }
 
-int scr_corrector(scr_handle h, double* v, double* p, double* vdot, double* u, int n_iter, double* res_norms,
-                  int dev) {
-  if (!h || !v || !p || !vdot || !u || n_iter < 0 || !res_norms) return SCR_INVALID_ARG;
+namespace {
+
+// mesh-motion arguments of scr_corrector_ale (null: the mesh stays fixed)
+struct AleArgs {
+  const double* uhat_n;
+  const double* vhat_n;  // may be null (zero)
+  double* uhat;
+};
+
+int corrector_run(scr_handle h, double* v, double* p, double* vdot, double* u, int n_iter, double* res_norms,
+                  int dev, const AleArgs* ale) {
   if (!h->have_block || !h->have_residual || h->k != 1 || h->ra.nn != h->nv || h->ra.np != h->np) {
     set_last_error("scr_corrector: needs scr_setup (nrhs = 1) and scr_assembly_setup on the same mesh");
     return SCR_INVALID_ARG;
   }
+  if (ale && (!h->have_coupling || !h->have_mesh || h->nm != h->cpl_nf || h->cpl_nn != h->ra.nn)) {
+    set_last_error("scr_corrector_ale: needs scr_mesh_coupling and mm_setup on the same fluid nodes");
+    return SCR_INVALID_ARG;
+  }
   int status = SCR_OK;
+  int mesh_fail_it = 0;
+  double mesh_fail_rel = 0.0;
   int rc = guarded([&] {
     cudaStream_t s = h->s;
     const long long nv3 = 3LL * h->nv, np = h->np, n = nv3 + np;
@@ -2023,10 +2048,38 @@ int scr_corrector(scr_handle h, double* v, double* p, double* vdot, double* u, i
       SCR_CUDA(cudaMemcpyAsync(du, u, sizeof(double) * nv3, cudaMemcpyHostToDevice, s));
       SCR_CUDA(cudaMemcpyAsync(dp, p, sizeof(double) * np, cudaMemcpyHostToDevice, s));
     }
+    const long long nf3 = 3LL * h->cpl_nf;
+    if (ale) {
+      // the state enters at the same-Y predictor: u is u_n
+      copy<double>(du, h->d_un, nv3, s);
+      const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+      SCR_CUDA(cudaMemcpyAsync(h->d_uhn, ale->uhat_n, sizeof(double) * nf3, k, s));
+      if (ale->vhat_n) SCR_CUDA(cudaMemcpyAsync(h->d_vhn, ale->vhat_n, sizeof(double) * nf3, k, s));
+      else fill<double>(h->d_vhn, 0.0, nf3, s);
+    }
     double* R = h->r_in + 4 * nv3 + np;  // 3 n_nodes + n_p
     ArnoldiState* st = h->gOuter.st;
+    EpiArgs plain;
     for (int it = 0; it <= n_iter; ++it) {
-      h->ra.evaluate(dv, nullptr, dp, dvd, du, R, s);
+      if (ale) {
+        // steps 3-4: mesh displacement at t_{n+1} as the harmonic extension
+        // of the interface displacement (CG + AMG on the eliminated
+        // Laplacian, right-hand side lifted with the raw one), mesh
+        // velocity at t_{n+alpha_f}
+        mesh_interface_data(h->d_node_of_f, h->d_follow, du, h->d_un, af, h->d_g, h->cpl_nf, s);
+        spmv<double, double>(h->Lraw, h->d_g, h->d_lift, 3, plain, s);
+        mesh_lift(h->d_dir_m, h->d_g, h->d_lift, h->cpl_nf, s);
+        int mit = 0;
+        double mrel = 0.0;
+        if (!mesh_cg(h, h->d_lift, h->d_uh, &mit, &mrel)) {
+          status = SCR_NOT_CONVERGED;
+          mesh_fail_it = mit;
+          mesh_fail_rel = mrel;
+        }
+        h->stats.mm_iters = mit;
+        mesh_velocity(h->d_node_of_f, h->d_uh, h->d_uhn, h->d_vhn, af, ga, h->phys.dt, h->d_vhat, h->cpl_nf, s);
+      }
+      h->ra.evaluate(dv, ale ? h->d_vhat : nullptr, dp, dvd, du, R, s);
       // resistance outlets: the traction P_j a_j with P_j = m_j (a_j^T v)
       // (the term whose derivative is the rank-1 tangent c_j a_j a_j^T,
       // c_j = alpha_f gamma dt m_j)
@@ -2053,11 +2106,89 @@ int scr_corrector(scr_handle h, double* v, double* p, double* vdot, double* u, i
       SCR_CUDA(cudaMemcpyAsync(u, du, sizeof(double) * nv3, cudaMemcpyDeviceToHost, s));
       SCR_CUDA(cudaMemcpyAsync(p, dp, sizeof(double) * np, cudaMemcpyDeviceToHost, s));
     }
+    if (ale)
+      SCR_CUDA(cudaMemcpyAsync(ale->uhat, h->d_uh, sizeof(double) * nf3,
+                               dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     SCR_CUDA(cudaStreamSynchronize(s));
     check_staged(h);
   });
   if (rc != SCR_OK) return rc;
+  if (mesh_fail_it)
+    set_last_error("scr_corrector_ale: mesh CG stopped at %d iterations, relative residual %.3e", mesh_fail_it,
+                   mesh_fail_rel);
   return status;
+}
+
+}  // namespace
+
+int scr_corrector(scr_handle h, double* v, double* p, double* vdot, double* u, int n_iter, double* res_norms,
+                  int dev) {
+  if (!h || !v || !p || !vdot || !u || n_iter < 0 || !res_norms) return SCR_INVALID_ARG;
+  return corrector_run(h, v, p, vdot, u, n_iter, res_norms, dev, nullptr);
+}
+
+int scr_corrector_ale(scr_handle h, double* v, double* p, double* vdot, double* u, const double* uhat_n,
+                      const double* vhat_n, double* uhat, int n_iter, double* res_norms, int dev) {
+  if (!h || !v || !p || !vdot || !u || !uhat_n || !uhat || n_iter < 0 || !res_norms) return SCR_INVALID_ARG;
+  const AleArgs ale{uhat_n, vhat_n, uhat};
+  return corrector_run(h, v, p, vdot, u, n_iter, res_norms, dev, &ale);
+}
+
+int scr_mesh_coupling(scr_handle h, int n_fluid, const int* fluid_id, const unsigned char* dir_m,
+                      const unsigned char* follow, const scr_bsr* L_raw) {
+  if (!h || n_fluid <= 0 || !fluid_id || !dir_m || !follow || !L_raw) {
+    set_last_error("scr_mesh_coupling: NULL argument or no fluid nodes");
+    return SCR_INVALID_ARG;
+  }
+  if (!h->have_residual) {
+    set_last_error("scr_mesh_coupling: needs scr_assembly_setup first (the node count)");
+    return SCR_INVALID_ARG;
+  }
+  return guarded([&] {
+    check_bsr(L_raw, 1, 1, n_fluid, n_fluid, "L_raw");
+    const int nn = h->ra.nn;
+    std::vector<int> node_of_f(n_fluid, -1);
+    for (int i = 0; i < nn; ++i) {
+      const int f = fluid_id[i];
+      if (f < -1 || f >= n_fluid) throw std::invalid_argument("scr_mesh_coupling: fluid_id out of range");
+      if (f < 0) continue;
+      if (node_of_f[f] >= 0) throw std::invalid_argument("scr_mesh_coupling: fluid ordinal used twice");
+      node_of_f[f] = i;
+    }
+    for (int f = 0; f < n_fluid; ++f) {
+      if (node_of_f[f] < 0) throw std::invalid_argument("scr_mesh_coupling: fluid ordinal without a node");
+      if (follow[f] && !dir_m[f]) throw std::invalid_argument("scr_mesh_coupling: follow set on a free mesh node");
+    }
+    cudaStream_t s = h->s;
+    SCR_CUDA(cudaStreamSynchronize(s));
+    h->have_coupling = false;
+    h->cmats.reset(new DeviceArena(s));
+    DeviceArena& a = *h->cmats;
+    h->Lraw = upload(L_raw, 0, a, s);
+    scr_opts o = h->o;
+    o.sell = 0;
+    tune_product<double>(h->Lraw, 3, o, a, s);
+    const long long nf3 = 3LL * n_fluid, nv3 = 3LL * nn;
+    h->d_node_of_f = a.alloc<int>(n_fluid);
+    h->d_dir_m = a.alloc<unsigned char>(n_fluid);
+    h->d_follow = a.alloc<unsigned char>(n_fluid);
+    h->d_g = a.alloc<double>(nf3);
+    h->d_lift = a.alloc<double>(nf3);
+    h->d_uh = a.alloc<double>(nf3);
+    h->d_uhn = a.alloc<double>(nf3);
+    h->d_vhn = a.alloc<double>(nf3);
+    h->d_un = a.alloc<double>(nv3);
+    h->d_vhat = a.alloc<double>(nv3);
+    SCR_CUDA(cudaMemcpyAsync(h->d_node_of_f, node_of_f.data(), sizeof(int) * n_fluid, cudaMemcpyHostToDevice, s));
+    SCR_CUDA(cudaMemcpyAsync(h->d_dir_m, dir_m, n_fluid, cudaMemcpyHostToDevice, s));
+    SCR_CUDA(cudaMemcpyAsync(h->d_follow, follow, n_fluid, cudaMemcpyHostToDevice, s));
+    // the mesh velocity is zero away from the fluid nodes
+    fill<double>(h->d_vhat, 0.0, nv3, s);
+    SCR_CUDA(cudaStreamSynchronize(s));
+    h->cpl_nf = n_fluid;
+    h->cpl_nn = nn;
+    h->have_coupling = true;
+  });
 }
 
 int scr_set_outlets(scr_handle h, int n_out, int len, const double* a, const double* c) {

@@ -249,6 +249,56 @@ class BlockSolver:
         check(st, (SCR_OK, SCR_NOT_CONVERGED))
         return norms
 
+    def mesh_coupling(self, L_raw, fluid_id, dir_m, follow):
+        """Mesh motion for ``corrector_ale``: the fluid nodes' mesh Laplacian
+        without boundary conditions (host BSR), the node -> fluid ordinal
+        map (-1 off the fluid), the Dirichlet mesh flags and the flags of
+        the Dirichlet nodes that follow the solid displacement."""
+        keep: list = []
+        sl, dl = _as_bsr(L_raw, keep)
+        if dl:
+            raise TypeError("L_raw must be a host matrix")
+        fid = np.ascontiguousarray(fluid_id, dtype=np.int32)
+        dm = np.ascontiguousarray(dir_m, dtype=np.uint8)
+        fo = np.ascontiguousarray(follow, dtype=np.uint8)
+        nf = int(L_raw.nb_rows)
+        if dm.size != nf or fo.size != nf:
+            raise ValueError("dir_m and follow need one flag per fluid node")
+        check(self.lib.scr_mesh_coupling(self.h, nf, fid.ctypes.data_as(C.c_void_p), dm.ctypes.data_as(C.c_void_p),
+                                         fo.ctypes.data_as(C.c_void_p), C.byref(sl)))
+        self.n_fluid = nf
+
+    def corrector_ale(self, v, p, vdot, u, uhat_n, n_iter: int, vhat_n=None):
+        """``corrector`` with the mesh moving inside the loop; the state
+        (entering at the same-Y predictor) is updated in place.  Returns
+        (residual norms, uhat_{n+1})."""
+        keep: list = []
+        ptrs = [_ptr(a, keep) for a in (v, p, vdot, u)]
+        devs = {d for _, d in ptrs}
+        if len(devs) != 1:
+            raise ValueError("state vectors must all be host or all device")
+        dev = devs.pop()
+        if not dev and any(k is not a for k, a in zip(keep, (v, p, vdot, u))):
+            raise TypeError("host state vectors must be contiguous float64 arrays (updated in place)")
+        n3 = 3 * self.n_fluid
+        if dev:
+            uhat = _torch().empty(n3, dtype=_torch().float64, device=v.device)
+        else:
+            uhat = np.empty(n3)
+        extra = [_ptr(a, keep) for a in (uhat_n, uhat)]
+        pvn = None
+        if vhat_n is not None:
+            pvn, dvn = _ptr(vhat_n, keep)
+            extra.append((pvn, dvn))
+        if any(d != dev for _, d in extra):
+            raise ValueError("uhat_n and vhat_n must live where the state does")
+        norms = np.zeros(n_iter + 1)
+        st = self.lib.scr_corrector_ale(self.h, *(C.c_void_p(q) for q, _ in ptrs), C.c_void_p(extra[0][0]),
+                                        None if pvn is None else C.c_void_p(pvn), C.c_void_p(extra[1][0]),
+                                        int(n_iter), norms.ctypes.data_as(C.c_void_p), dev)
+        check(st, (SCR_OK, SCR_NOT_CONVERGED))
+        return norms, uhat
+
     def set_outlets(self, a_out, c_out):
         """Rank-1 outlet terms for the next setup: vectors a_j (3 n_v each)
         and coefficients c_j; empty lists remove them."""

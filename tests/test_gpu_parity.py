@@ -886,6 +886,67 @@ def test_gpu_corrector_matches_the_oracle_loop(small, precision):
     np.testing.assert_array_equal(v, dv.cpu().numpy())
 
 
+@pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
+def test_gpu_corrector_ale_matches_the_oracle_loop(small, precision):
+    """Multi-corrector with the mesh moving inside the loop (Sec. 3.5, steps
+    3-4): the GPU's mesh CG + AMG on the eliminated Laplacian with the lifted
+    interface displacement, its mesh velocity and the residual at that mesh
+    velocity follow the oracle's loop (direct mesh and block solves): same
+    starting residual, the same contraction, the same state and mesh
+    displacement up to the solves' tolerances; host and device paths agree
+    bit for bit."""
+    from oracle import corrector
+    from oracle.sparse import to_csr
+    s = small
+    m = s.mesh
+    asm = F.Assembler(F.make_params(**F.PRESETS["tube_small"]))
+    L_raw = asm.mesh_laplacian()
+    follow = F.interface_follow(m)
+    v0, p0 = asm.initial_state()
+    z, zf = np.zeros(3 * m.n_nodes), np.zeros(3 * m.n_fluid)
+    vn = 0.01 * np.random.default_rng(4).standard_normal(3 * m.n_fluid)
+    vr, pr, vdr, ur, uhr, nr = corrector.corrector_ale(s, asm, v0, p0, z, z, 3, to_csr(L_raw), m.fluid_id,
+                                                       m.dir_m, follow, zf, vn)
+    with pkg.BlockSolver(precision=precision) as sol:
+        sol.setup(s.A, s.B, s.C, s.D)
+        sol.assembly_setup(m, s.params)
+        sol.mesh_setup(s.L)
+        sol.mesh_coupling(L_raw, m.fluid_id, m.dir_m, follow)
+        v, p, vd, u = v0.copy(), p0.copy(), z.copy(), z.copy()
+        norms, uh = sol.corrector_ale(v, p, vd, u, zf, 3, vhat_n=vn)
+        dv, dp, dvd, du = (_dev(a) for a in (v0, p0, z, z))
+        norms_d, uh_d = sol.corrector_ale(dv, dp, dvd, du, _dev(zf), 3, vhat_n=_dev(vn))
+    assert norms[0] == pytest.approx(nr[0], rel=1e-12)
+    assert norms[1] == pytest.approx(nr[1], rel=1e-3)
+    assert norms[2] < 1e-2 * norms[1] and norms[3] < 1e-2 * norms[2]
+    for a, b in ((v, vr), (p, pr), (vd, vdr), (u, ur), (uh, uhr)):
+        assert _rel(a, b) < 1e-7
+    assert np.abs(uh).max() > 1e-6
+    np.testing.assert_array_equal(norms, norms_d)
+    np.testing.assert_array_equal(uh, uh_d.cpu().numpy())
+
+
+def test_gpu_corrector_ale_rejects_a_missing_coupling(small):
+    """scr_corrector_ale without scr_mesh_coupling, and a coupling whose
+    follow flag sits on a free mesh node, are argument errors."""
+    s = small
+    m = s.mesh
+    z, zf = np.zeros(3 * m.n_nodes), np.zeros(3 * m.n_fluid)
+    with pkg.BlockSolver() as sol:
+        sol.setup(s.A, s.B, s.C, s.D)
+        sol.assembly_setup(m, s.params)
+        sol.mesh_setup(s.L)
+        sol.n_fluid = m.n_fluid
+        v, p = np.zeros(3 * m.n_nodes), np.zeros(m.n_p)
+        with pytest.raises(pkg.ScrError, match="scr_mesh_coupling"):
+            sol.corrector_ale(v, p, z.copy(), z.copy(), zf, 1)
+        bad = F.interface_follow(m).copy()
+        bad[np.flatnonzero(~m.dir_m)[0]] = 1
+        asm = F.Assembler(F.make_params(**F.PRESETS["tube_small"]))
+        with pytest.raises(pkg.ScrError, match="follow"):
+            sol.mesh_coupling(asm.mesh_laplacian(), m.fluid_id, m.dir_m, bad)
+
+
 def test_gpu_corrector_with_a_resistance_outlet(outlet_small):
     """Corrector with the outlet traction in the residual and the rank-1 term
     in the tangent: follows the oracle's loop and contracts."""

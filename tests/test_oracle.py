@@ -561,3 +561,93 @@ def test_corrector_with_a_resistance_outlet_contracts():
     *_, norms = corrector.corrector(s, asm, v, p, np.zeros(3 * nn), np.zeros(3 * nn), 2)
     assert norms[0] == pytest.approx(np.linalg.norm(s.b), rel=1e-12)
     assert norms[1] < 1e-3 * norms[0] and norms[2] < 1e-2 * norms[1]
+
+
+# ------------------------------------------------- mesh motion inside the corrector
+def _ale_case(name="tube_mini"):
+    s = F.tube_system(name, keep_mesh=True)
+    asm = F.Assembler(F.make_params(**F.PRESETS[name]))
+    return s, asm, to_csr(asm.mesh_laplacian()), F.interface_follow(s.mesh)
+
+
+def test_mesh_displacement_reproduces_linear_fields():
+    """Linear finite elements reproduce linear functions, so the harmonic
+    extension (Sec. 5.2.2) of linear Dirichlet data is that linear field at
+    every fluid node: a wrong sign in the lift, a swapped free/Dirichlet
+    block or a component mix-up breaks it."""
+    from oracle import corrector
+    s, asm, L, _ = _ale_case()
+    m = s.mesh
+    nodes = np.flatnonzero(m.fluid_id >= 0)
+    X = np.zeros((m.n_fluid, 3))
+    X[m.fluid_id[nodes]] = m.xyz[nodes]
+    G = np.array([[0.3, -1.1, 0.2], [0.5, 0.7, -0.4], [-0.2, 0.1, 0.9]])
+    want = X @ G.T + np.array([1e-3, -2e-3, 5e-4])
+    g = np.where(m.dir_m[:, None], want, 123.0).ravel()  # free entries must be ignored
+    uh = corrector.mesh_displacement(L, m.dir_m, g)
+    np.testing.assert_allclose(uh, want.ravel(), rtol=0, atol=1e-12 * np.abs(want).max())
+
+
+def test_mesh_velocity_keeps_a_constant_rate_and_drops_the_old_rate():
+    """Step 4 with the generalized-alpha update (Sec. 3.4): a mesh moving at
+    a constant rate w keeps vhat = w at t_{n+1} and t_{n+alpha_f}; with
+    alpha_f = gamma the intermediate mesh velocity is (uhat_{n+1} - uhat_n) / dt
+    whatever vhat_n is."""
+    from oracle import corrector
+    rng = np.random.default_rng(5)
+    dt, t = 1e-4, 0.37
+    w = rng.standard_normal(30)
+    for rho in (0.0, 0.5, 1.0):
+        v1, va = corrector.mesh_velocity(w * (t + dt), w * t, w, rho, dt)
+        np.testing.assert_allclose(v1, w, rtol=1e-9)
+        np.testing.assert_allclose(va, w, rtol=1e-9)
+        u1, u0, vn = (rng.standard_normal(30) for _ in range(3))
+        _, va = corrector.mesh_velocity(u1, u0, vn, rho, dt)
+        np.testing.assert_allclose(va, (u1 - u0) / dt, rtol=1e-9)
+
+
+def test_corrector_ale_without_interface_motion_is_the_fixed_mesh_loop():
+    """No node follows the wall and uhat_n = 0: the mesh stays put, the mesh
+    velocity is zero and the loop is the fixed-mesh corrector."""
+    from oracle import corrector
+    s, asm, L, follow = _ale_case()
+    m = s.mesh
+    v, p = asm.initial_state()
+    z, zf = np.zeros(3 * m.n_nodes), np.zeros(3 * m.n_fluid)
+    ref = corrector.corrector(s, asm, v, p, z, z, 2)
+    got = corrector.corrector_ale(s, asm, v, p, z, z, 2, L, m.fluid_id, m.dir_m, 0 * follow, zf,
+                                  np.random.default_rng(1).standard_normal(3 * m.n_fluid))
+    for a, b in zip(ref[:4], got[:4]):  # zero vhat vs none: rounding of near-zero entries only
+        np.testing.assert_allclose(a, b, rtol=1e-13, atol=1e-13 * np.abs(a).max())
+    np.testing.assert_allclose(ref[4], got[5], rtol=1e-13, atol=1e-13 * ref[4][0])
+    assert not got[4].any()
+
+
+def test_corrector_ale_moves_the_mesh_with_the_wall_and_contracts():
+    """With the interface following the wall the corrector still starts from
+    the system's right-hand side and contracts by orders of magnitude per
+    iteration (the tangent leaves out only the weak mesh-velocity coupling);
+    the final mesh displacement equals u_{n+1} = u_n + (u - u_n) / alpha_f on
+    the interface and zero on the other Dirichlet nodes, the wall moved, and
+    vhat_n drops out (alpha_f = gamma)."""
+    from oracle import corrector
+    s, asm, L, follow = _ale_case()
+    m = s.mesh
+    v, p = asm.initial_state()
+    z, zf = np.zeros(3 * m.n_nodes), np.zeros(3 * m.n_fluid)
+    vn = np.random.default_rng(2).standard_normal(3 * m.n_fluid)
+    vr, pr, vdr, ur, uh, norms = corrector.corrector_ale(s, asm, v, p, z, z, 3, L, m.fluid_id, m.dir_m,
+                                                         follow, zf, vn)
+    assert norms[0] == pytest.approx(np.linalg.norm(s.b), rel=1e-12)
+    assert norms[1] < 1e-2 * norms[0] and norms[2] < 1e-2 * norms[1] and norms[3] < 1e-2 * norms[2]
+    af = 1.0 / (1.0 + s.params["rho_inf"])
+    nodes = np.flatnonzero(m.fluid_id >= 0)
+    U = uh.reshape(-1, 3)
+    u1 = ur.reshape(-1, 3)[nodes] / af
+    f = m.fluid_id[nodes]
+    on = follow[f].astype(bool)
+    np.testing.assert_allclose(U[f[on]], u1[on], rtol=0, atol=1e-15)
+    assert not U[m.dir_m & ~follow.astype(bool)].any()
+    assert np.abs(U[f[on]]).max() > 1e-6
+    *_, norms0 = corrector.corrector_ale(s, asm, v, p, z, z, 3, L, m.fluid_id, m.dir_m, follow, zf, zf)
+    np.testing.assert_allclose(norms, norms0, rtol=1e-9, atol=1e-13 * norms[0])
