@@ -651,3 +651,92 @@ def test_corrector_ale_moves_the_mesh_with_the_wall_and_contracts():
     assert np.abs(U[f[on]]).max() > 1e-6
     *_, norms0 = corrector.corrector_ale(s, asm, v, p, z, z, 3, L, m.fluid_id, m.dir_m, follow, zf, zf)
     np.testing.assert_allclose(norms, norms0, rtol=1e-9, atol=1e-13 * norms[0])
+
+
+# ------------------------------------------------- AMG building blocks, one by one
+def test_chebyshev_residual_polynomial_is_the_scaled_chebyshev_polynomial():
+    """Chebyshev smoothing of degree k from a zero iterate leaves the residual
+    T_k((theta - lambda) / delta) / T_k(theta / delta) b for an operator with
+    eigenvalue lambda (theta, delta: centre and half-width of [lam/30, lam]):
+    checked on a diagonal operator against numpy's Chebyshev series, with
+    D = I and with a general diagonal scaling (the smoother works on D^-1 A)."""
+    from numpy.polynomial import chebyshev as npc
+    from oracle import amg
+    lam = 3.7
+    lo, hi = lam / 30.0, lam
+    theta, delta = (hi + lo) / 2.0, (hi - lo) / 2.0
+    mu = np.concatenate([np.linspace(lo, hi, 9), [0.3 * lo, 1.2 * hi]])  # eigenvalues of D^-1 A
+    for degree in (1, 2, 3, 4):
+        Tk = npc.Chebyshev.basis(degree)
+        want = Tk((theta - mu) / delta) / Tk(theta / delta)
+        for d in (np.ones(mu.size), np.linspace(0.5, 2.0, mu.size)):
+            A = sp.diags(mu * d).tocsr()          # D^-1 A = diag(mu) with D = diag(d)
+            b = np.linspace(1.0, 2.0, mu.size)
+            x = amg.cheb_smooth(A, 1.0 / d, lam, degree, np.zeros_like(b), b, True)
+            np.testing.assert_allclose((b - A @ x) / b, want, rtol=1e-10, atol=1e-13)
+            # from a nonzero iterate the error contracts by the same polynomial
+            x0 = np.cos(np.arange(mu.size))
+            xs = b / A.diagonal()
+            x1 = amg.cheb_smooth(A, 1.0 / d, lam, degree, x0, b, False)
+            np.testing.assert_allclose((x1 - xs) / (x0 - xs), want, rtol=1e-9, atol=1e-12)
+
+
+def test_l1_jacobi_diagonal_dominates_an_spd_matrix():
+    """d_i = sum_j |a_ij| (row sums of absolute values, diagonal included) on a
+    hand example, and for SPD A the l1-Jacobi iteration converges: D_l1 - A
+    is weakly diagonally dominant, so every eigenvalue of D_l1^-1 A lies in
+    (0, 1]."""
+    from oracle import amg
+    M = sp.csr_matrix(np.array([[4.0, -1.0, 2.0], [0.0, 3.0, -3.0], [1.0, 1.0, -5.0]]))
+    np.testing.assert_array_equal(amg.l1_diag(M), [7.0, 6.0, 7.0])
+    rng = np.random.default_rng(11)
+    Q = rng.standard_normal((30, 30))
+    A = Q @ Q.T + 0.1 * np.eye(30)
+    A[np.abs(A) < 2.0] = 0.0
+    w = np.linalg.eigvalsh(A)
+    if w.min() <= 0:
+        A += (1e-3 - w.min()) * np.eye(30)
+    d = amg.l1_diag(sp.csr_matrix(A))
+    ev = np.linalg.eigvals(A / d[:, None])
+    assert ev.real.min() > 0 and ev.real.max() <= 1.0 + 1e-12 and np.abs(ev.imag).max() < 1e-10
+
+
+def test_gershgorin_bound_holds_and_is_tight_on_a_singular_laplacian():
+    """max_i sum_j |a_ij| / |a_ii| bounds the spectral radius of D^-1 A (random
+    nonsymmetric matrices) and equals it for the 1-D Neumann Laplacian, whose
+    D^-1 A has the eigenvalue 2 (the alternating vector)."""
+    from oracle import amg
+    rng = np.random.default_rng(12)
+    for _ in range(5):
+        A = rng.standard_normal((25, 25)) * (rng.random((25, 25)) < 0.2) + np.diag(rng.uniform(1, 3, 25))
+        rho = np.abs(np.linalg.eigvals(A / np.diag(A)[:, None])).max()
+        assert amg.gershgorin_dinv_a(sp.csr_matrix(A)) >= rho - 1e-12
+    n = 12
+    L = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]).tolil()
+    L[0, 0] = L[n - 1, n - 1] = 1.0
+    L = L.tocsr()
+    rho = np.abs(np.linalg.eigvals(L.toarray() / L.diagonal()[:, None])).max()
+    assert amg.gershgorin_dinv_a(L) == pytest.approx(2.0) and rho == pytest.approx(2.0)
+
+
+def test_smoothed_prolongator_keeps_the_near_nullspace_and_lowers_the_energy():
+    """Prolongator smoothing (Sec. 7: smoothed aggregation): where A
+    annihilates the near-nullspace (constants of the Neumann Laplacian),
+    P B_c = P_tent B_c = 1; omega = 4 / (3 lambda) with lambda = 2 there; and
+    damped Jacobi lowers the energy p^T A p of every coarse basis function
+    (a wrong sign raises it)."""
+    from oracle import amg
+    n = 30
+    L = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]).tolil()
+    L[0, 0] = L[n - 1, n - 1] = 1.0
+    L = L.tocsr()
+    agg = np.arange(n) // 3
+    Pt = amg.tentative_prolongator(agg, 1)
+    Bc = np.sqrt(np.bincount(agg).astype(float))
+    np.testing.assert_allclose(Pt @ Bc, np.ones(n), rtol=1e-14)
+    P, omega = amg.smoothed_prolongator(L, Pt)
+    assert omega == pytest.approx(2.0 / 3.0)
+    np.testing.assert_allclose(P @ Bc, np.ones(n), rtol=1e-13)
+    e_t = np.asarray((Pt.T @ (L @ Pt)).diagonal()).ravel()
+    e_s = np.asarray((P.T @ (L @ P)).diagonal()).ravel()
+    assert np.all(e_s < e_t)
