@@ -331,15 +331,20 @@ def main():
     # mixed precision, same step (reported beside the FP64 headline)
     mixed = None
     if prec == pkg.SCR_FP64 and not args.skip_mixed:
+        x64 = xd.clone()  # the FP64 answer; the mixed steps overwrite xd
         solm = make_solver(pkg.SCR_MIXED)
         for _ in range(max(1, args.warmup)):
             step_device(solm)
         msm, _, _ = timed(solm, step_device, args.steps)
         stm = solm.stats()
         msm = allmax(pg, msm, dev)
+        torch.cuda.synchronize(dev)
+        err = float(torch.linalg.vector_norm(xd - x64) / torch.linalg.vector_norm(x64))
         mixed = {"value": world * 1000.0 / msm, "ms_per_step": msm, "outer_iters": stm["outer_iters"],
                  "rel_res": stm["rel_res"], "speedup_vs_fp64": ms / msm,
-                 "solve_ms": stm["solve_ms"], "setup_ms": stm["setup_ms"]}
+                 "solve_ms": stm["solve_ms"], "setup_ms": stm["setup_ms"],
+                 "dofs_iters_per_s": s.n * stm["outer_iters"] * 1000.0 / stm["solve_ms"],
+                 "rel_error_vs_fp64": err}
         solm.close()
 
     # end to end through the public API with host pinned buffers
@@ -540,6 +545,7 @@ def main():
                    "autotune": "decisions loaded from --tune-file" if tune_loaded else "timed at set-up"},
         "rel_res": rel_res, "outer_iters": st["outer_iters"], "inner_iters": st["a_iters"] + st["s_iters"] + st["i_iters"],
         "mesh_iters": st["mm_iters"], "setup_ms": st["setup_ms"], "solve_ms": st["solve_ms"],
+        "dofs_iters_per_s": s.n * st["outer_iters"] * 1000.0 / st["solve_ms"],
         "mm_setup_ms": st["mm_setup_ms"], "mm_solve_ms": st["mm_solve_ms"],
         "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "mixed": mixed,
         "batched": batched, "multi_rhs": multi, "assembly": assembly,
