@@ -72,7 +72,7 @@ __host__ __device__ inline long long slab_index(int s, int k, int t, int r, int 
 
 // --------------------------------------------------------------- memory
 // Stream-ordered device allocations from a pool that keeps its memory, so
-// repeated set-ups reuse the same blocks without returning to the driver.
+// repeated set-ups reuse the same blocks without returning them to the CUDA driver.
 class DeviceArena {
  public:
   static constexpr size_t kSlack = 64;
