@@ -740,3 +740,34 @@ def test_smoothed_prolongator_keeps_the_near_nullspace_and_lowers_the_energy():
     e_t = np.asarray((Pt.T @ (L @ Pt)).diagonal()).ravel()
     e_s = np.asarray((P.T @ (L @ P)).diagonal()).ravel()
     assert np.all(e_s < e_t)
+
+
+def test_strength_graph_by_brute_force():
+    """Block rows i != j are strongly connected when ||A_ij||_F >= theta
+    sqrt(||A_ii||_F ||A_jj||_F) in either direction (the graph is
+    symmetrised), checked pair by pair with dense blocks on a random
+    3x3-block matrix; the edge weight is the larger block norm of the pair."""
+    from oracle import amg
+    rng = np.random.default_rng(13)
+    n, bs, theta = 40, 3, 0.3
+    mask = rng.random((n, n)) < 0.15
+    np.fill_diagonal(mask, True)
+    D = np.zeros((n * bs, n * bs))
+    for i, j in zip(*np.nonzero(mask)):
+        blk = rng.standard_normal((bs, bs)) * (3.0 if i == j else rng.uniform(0.05, 1.5))
+        D[i * bs:(i + 1) * bs, j * bs:(j + 1) * bs] = blk
+    S = amg.strength_graph(sp.csr_matrix(D), bs, theta).toarray()
+    nrm = np.array([[np.linalg.norm(D[i * bs:(i + 1) * bs, j * bs:(j + 1) * bs]) for j in range(n)]
+                    for i in range(n)])
+    want = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            if i == j:
+                continue
+            strong_ij = nrm[i, j] > 0 and nrm[i, j] >= theta * np.sqrt(nrm[i, i] * nrm[j, j])
+            strong_ji = nrm[j, i] > 0 and nrm[j, i] >= theta * np.sqrt(nrm[i, i] * nrm[j, j])
+            w = max(nrm[i, j] if strong_ij else 0.0, nrm[j, i] if strong_ji else 0.0)
+            want[i, j] = w
+    np.testing.assert_allclose(S, want, rtol=1e-14)
+    assert (want > 0).sum() > n  # the case has strong and weak pairs
+    assert ((nrm > 0) & (want == 0) & ~np.eye(n, dtype=bool)).any()
