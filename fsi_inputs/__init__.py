@@ -53,6 +53,7 @@ class Params(C.Structure):
         ("u_max", C.c_double), ("pert_amp", C.c_double), ("mesh_amp", C.c_double),
         ("c_m_solid", C.c_double), ("c_c_solid", C.c_double),
         ("seed", C.c_uint64),
+        ("bif_angle_deg", C.c_double), ("bif_daughter_len", C.c_double), ("bif_tip_layers", C.c_int),
     ]
 
 
@@ -272,6 +273,12 @@ PRESETS = {
     "tube_tiny": dict(n_circ=4, n_rad_f=1, n_rad_s=1, n_ax=2),
     # a few thousand unknowns: several GPU tiles, seconds on the CPU
     "tube_mini": dict(n_circ=12, n_rad_f=3, n_rad_s=2, n_ax=12),
+    # bifurcation (kind 2): parent R = 0.5 cm, wall 0.06 cm (12% of R), 4 cm
+    # parent and 4 cm daughters at +-35 degrees; n_circ = core cells per
+    # side of the O-grid's square, n_rad_f lumen rings, n_rad_s wall rings
+    "bifurcation": dict(kind=2, R=0.5, wall=0.06, L=4.0, n_circ=40, n_rad_f=24, n_rad_s=5, n_ax=633),
+    "bif_small": dict(kind=2, R=0.5, wall=0.06, L=4.0, n_circ=16, n_rad_f=8, n_rad_s=2, n_ax=16),
+    "bif_mini": dict(kind=2, R=0.5, wall=0.06, L=4.0, n_circ=10, n_rad_f=4, n_rad_s=1, n_ax=10),
 }
 
 
@@ -284,6 +291,8 @@ def genalpha(rho_inf: float):
 def build_mesh(params: Params) -> Mesh:
     L = lib()
     pm = L.tg_mesh_build(C.byref(params))
+    if not pm:
+        raise ValueError("no mesh: parameters out of range")
     try:
         return _mesh_from_c(pm.contents)
     finally:
@@ -301,6 +310,8 @@ def tube_system(name: str = "tube_small", threads: int = 0, keep_mesh: bool = Fa
     if threads:
         L.tg_set_threads(threads)
     pm = L.tg_mesh_build(C.byref(params))
+    if not pm:
+        raise ValueError(f"no mesh for {name}: parameters out of range")
     try:
         m = pm.contents
         nn, np_ = m.n_nodes, m.n_p
@@ -350,6 +361,40 @@ def interface_follow(mesh: Mesh) -> np.ndarray:
     return follow & mesh.dir_m.astype(np.uint8)
 
 
+def rhs_only(name: str, **overrides) -> np.ndarray:
+    """The right-hand side b = -[R_m; R_p] (Dirichlet velocity rows zero) of
+    ``tube_system(name, **overrides)`` without assembling the matrices: the
+    same state, the same generalized-alpha coefficients, the same element
+    loop with the tangent switched off (for several right-hand sides on one
+    Jacobian, e.g. inflow peaks)."""
+    kw = dict(PRESETS[name]) if name in PRESETS else {}
+    kw.update(overrides)
+    params = make_params(**kw)
+    L = lib()
+    pm = L.tg_mesh_build(C.byref(params))
+    if not pm:
+        raise ValueError(f"no mesh for {name}")
+    try:
+        m = pm.contents
+        nn, np_ = m.n_nodes, m.n_p
+        v = np.zeros(3 * nn)
+        p = np.zeros(np_)
+        L.tg_state_init(C.byref(params), pm, _dp(v), _dp(p))
+        am, af, ga = genalpha(params.rho_inf)
+        cf = af * ga * params.dt
+        raw = L.tg_assemble(C.byref(params), pm, _dp(v), None, _dp(p), None, None,
+                            am, cf, cf * cf / am, 0, None, 0)
+        r = raw.contents
+        b = -np.concatenate([np.ctypeslib.as_array(r.Rm, shape=(3 * nn,)),
+                             np.ctypeslib.as_array(r.Rp, shape=(np_,))])
+        dv = np.ctypeslib.as_array(m.dir_v, shape=(nn,)).astype(bool)
+        b[:3 * nn][np.repeat(dv, 3)] = 0.0
+        L.tg_raw_free(raw)
+        return b
+    finally:
+        L.tg_mesh_free(pm)
+
+
 def outlet_vector(mesh: Mesh, n_ax: int, zero_dirichlet: bool = True) -> np.ndarray:
     """a_{A,i} = int_{outlet} N_A n_i dGamma over the fluid outlet section
     (the faces of fluid tets with all three vertices on the last axial
@@ -381,6 +426,8 @@ class Assembler:
         self.params = params
         self.L = lib()
         self.pm = self.L.tg_mesh_build(C.byref(params))
+        if not self.pm:
+            raise ValueError("no mesh: parameters out of range")
         self.mesh = _mesh_from_c(self.pm.contents)
 
     def close(self):

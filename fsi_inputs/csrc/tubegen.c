@@ -35,7 +35,7 @@
 /* parameters                                                          */
 /* ------------------------------------------------------------------ */
 typedef struct {
-  int kind;      /* 0 straight tube, 1 stenosed tube                      */
+  int kind;      /* 0 straight tube, 1 stenosed tube, 2 bifurcation        */
   int n_circ;    /* nodes around the circumference                         */
   int n_rad_f;   /* radial node rings in the lumen (the last is the wall)  */
   int n_rad_s;   /* radial node rings in the vessel wall                   */
@@ -47,6 +47,11 @@ typedef struct {
   double u_max, pert_amp, mesh_amp;
   double c_m_solid, c_c_solid;
   uint64_t seed;
+  /* kind 2 (bifurcation): half-angle between each daughter's axis and the
+     parent's (degrees), daughter length along its axis, element layers of
+     the solid carina tip */
+  double bif_angle_deg, bif_daughter_len;
+  int bif_tip_layers;
 } tg_params;
 
 typedef struct {
@@ -80,6 +85,7 @@ void tg_default_params(tg_params *p) {
   p->u_max = 30.0; p->pert_amp = 0.05; p->mesh_amp = 1.0e-3;
   p->c_m_solid = 1.0; p->c_c_solid = 0.0;
   p->seed = 2206;
+  p->bif_angle_deg = 35.0; p->bif_daughter_len = 4.0; p->bif_tip_layers = 2;
 }
 
 /* generalized-alpha constants of the first-order scheme (Sec. 3.4) */
@@ -148,7 +154,223 @@ void tg_mesh_free(tg_mesh *m) {
   free(m);
 }
 
+/* ------------------------------------------------------------------ */
+/* bifurcation (kind 2)                                                */
+/* ------------------------------------------------------------------ */
+/* One cross-section is extruded along z and its cells change class per
+   element layer.  The section is an O-grid of the parent: a square core of
+   NC x NC cells (half-width h = 0.6 R / sqrt 2) and rings along rays from
+   the origin, NRF lumen rings from the square to the lumen circle R and NRS
+   wall rings out to R + wall.  A septum band of core columns through the
+   middle, [c0, c3), and the ring cells over it split the section into side
+   A | wall A [c0, c1) | void [c1, c2) | wall B [c2, c3) | side B.
+     parent layers  (k < k_tip):        the band is lumen (its wall-ring
+                                         cells stay wall): a round tube;
+     carina tip     (k_tip <= k < k_dau): the whole band is solid;
+     daughters      (k >= k_dau):        void cells are removed, wall A / B
+                                         become the daughters' inner walls.
+   Each daughter keeps its half of the parent section (a half-disk lumen
+   with its wall) and is sheared sideways, x -/+= (z - z_dau) tan(angle):
+   a shear has determinant 1, so every tet keeps its volume and its
+   orientation.  Nodes that only removed cells use are dropped. */
+typedef struct {
+  int NC, NRF, NRS, NR, ncore, nsec;
+  int c0, c1, c2, c3;
+  int k_tip, k_dau;
+  double h, dz, tan_a, z_dau;
+} bif_geom;
+
+static int bif_geom_init(const tg_params *p, bif_geom *g) {
+  memset(g, 0, sizeof(*g));
+  g->NC = p->n_circ; g->NRF = p->n_rad_f; g->NRS = p->n_rad_s; g->NR = g->NRF + g->NRS;
+  if (g->NC < 8 || (g->NC & 1) || g->NRF < 1 || g->NRS < 1 || p->n_ax < 4 || p->fluid_only) return -1;
+  g->ncore = (g->NC + 1) * (g->NC + 1);
+  g->nsec = g->ncore + g->NR * 4 * g->NC;
+  g->h = 0.6 * p->R / sqrt(2.0);
+  const double cw = 2.0 * g->h / g->NC;
+  int ws = (int)lround(p->wall / cw);
+  if (ws < 1) ws = 1;
+  g->c1 = g->NC / 2 - 1; g->c2 = g->NC / 2 + 1;
+  g->c0 = g->c1 - ws; g->c3 = g->c2 + ws;
+  if (g->c0 < 2) return -1;
+  const double a = p->bif_angle_deg * M_PI / 180.0;
+  g->tan_a = tan(a);
+  g->dz = (p->L + p->bif_daughter_len * cos(a)) / p->n_ax;
+  g->k_dau = (int)lround(p->L / g->dz);
+  g->k_tip = g->k_dau - (p->bif_tip_layers > 0 ? p->bif_tip_layers : 1);
+  if (g->k_tip < 1 || g->k_dau >= p->n_ax) return -1;
+  g->z_dau = g->k_dau * g->dz;
+  return 0;
+}
+
+/* perimeter node pp of the core square (counter-clockwise from (0, 0)) */
+static void bif_perimeter(const bif_geom *g, int pp, int *i, int *j) {
+  const int NC = g->NC;
+  pp %= 4 * NC;
+  if (pp < NC) { *i = pp; *j = 0; }
+  else if (pp < 2 * NC) { *i = NC; *j = pp - NC; }
+  else if (pp < 3 * NC) { *i = 3 * NC - pp; *j = NC; }
+  else { *i = 0; *j = 4 * NC - pp; }
+}
+
+/* section coordinates of section node s, its core column (the column of the
+   core node it hangs from) and its ring (0: core) */
+static void bif_section_xy(const bif_geom *g, const tg_params *p, int s, double *X, double *Y, int *col,
+                           int *ring) {
+  const int NC = g->NC;
+  int i, j, q = 0;
+  if (s < g->ncore) {
+    i = s % (NC + 1); j = s / (NC + 1);
+    *X = g->h * (2.0 * i / NC - 1.0); *Y = g->h * (2.0 * j / NC - 1.0);
+  } else {
+    const int r = s - g->ncore;
+    q = 1 + r / (4 * NC);
+    bif_perimeter(g, r % (4 * NC), &i, &j);
+    const double Sx = g->h * (2.0 * i / NC - 1.0), Sy = g->h * (2.0 * j / NC - 1.0);
+    const double th = atan2(Sy, Sx);
+    if (q <= g->NRF) {
+      const double f = (double)q / g->NRF;
+      *X = Sx + f * (p->R * cos(th) - Sx); *Y = Sy + f * (p->R * sin(th) - Sy);
+    } else {
+      const double rad = p->R + p->wall * (double)(q - g->NRF) / g->NRS;
+      *X = rad * cos(th); *Y = rad * sin(th);
+    }
+  }
+  *col = i; *ring = q;
+}
+
+/* -1 side A, +1 side B, 0 the void columns, for a node in core column col */
+static int bif_side(const bif_geom *g, int col) { return col <= g->c1 ? -1 : (col >= g->c2 ? 1 : 0); }
+
+/* class of a section cell over core column col (-1: left/right ring cells)
+   in element layer k: 0 fluid, 1 solid, 2 removed */
+static int bif_class(const bif_geom *g, int k, int col, int base_solid) {
+  const int band = col >= g->c0 && col < g->c3;
+  if (!band || k < g->k_tip) return base_solid;
+  if (k < g->k_dau) return 1;
+  if (col >= g->c1 && col < g->c2) return 2;
+  return 1;
+}
+
+static tg_mesh *bif_mesh_build(const tg_params *p) {
+  bif_geom g;
+  if (bif_geom_init(p, &g)) return NULL;
+  const int NC = g.NC, P4 = 4 * NC, nl = p->n_ax + 1;
+  /* section triangles with their column and base class */
+  const int ntri = 2 * NC * NC + 2 * P4 * g.NR;
+  int *tri = (int *)malloc(sizeof(int) * 3 * ntri);
+  int *tcol = (int *)malloc(sizeof(int) * ntri);
+  unsigned char *tbase = (unsigned char *)malloc(ntri);
+  int t = 0;
+  for (int j = 0; j < NC; ++j)
+    for (int i = 0; i < NC; ++i) {
+      const int a = j * (NC + 1) + i, b = a + 1, c = a + NC + 2, d = a + NC + 1;
+      tri[3 * t] = a; tri[3 * t + 1] = b; tri[3 * t + 2] = c; tcol[t] = i; tbase[t++] = 0;
+      tri[3 * t] = a; tri[3 * t + 1] = c; tri[3 * t + 2] = d; tcol[t] = i; tbase[t++] = 0;
+    }
+  for (int q = 0; q < g.NR; ++q)
+    for (int pp = 0; pp < P4; ++pp) {
+      int i0, j0, i1, j1;
+      bif_perimeter(&g, pp, &i0, &j0);
+      bif_perimeter(&g, pp + 1, &i1, &j1);
+      const int a = q == 0 ? j0 * (NC + 1) + i0 : g.ncore + (q - 1) * P4 + pp;
+      const int b = q == 0 ? j1 * (NC + 1) + i1 : g.ncore + (q - 1) * P4 + (pp + 1) % P4;
+      const int c = g.ncore + q * P4 + (pp + 1) % P4, d = g.ncore + q * P4 + pp;
+      const int col = (j0 == j1) ? (i0 < i1 ? i0 : i1) : -1; /* bottom/top edge cells lie over a column */
+      const unsigned char base = (unsigned char)(q >= g.NRF);
+      tri[3 * t] = a; tri[3 * t + 1] = b; tri[3 * t + 2] = c; tcol[t] = col; tbase[t++] = base;
+      tri[3 * t] = a; tri[3 * t + 1] = c; tri[3 * t + 2] = d; tcol[t] = col; tbase[t++] = base;
+    }
+  /* elements over candidate node numbers (layer * nsec + section node) */
+  long long ne = 0;
+  for (int k = 0; k < p->n_ax; ++k)
+    for (int q = 0; q < ntri; ++q) ne += bif_class(&g, k, tcol[q], tbase[q]) != 2;
+  ne *= 3;
+  const long long ncand = (long long)nl * g.nsec;
+  int *ien = (int *)malloc(sizeof(int) * 4 * ne);
+  unsigned char *et = (unsigned char *)malloc(ne);
+  int *newid = (int *)malloc(sizeof(int) * ncand);
+  for (long long c = 0; c < ncand; ++c) newid[c] = -1;
+  long long e = 0;
+  for (int k = 0; k < p->n_ax; ++k)
+    for (int q = 0; q < ntri; ++q) {
+      const int cls = bif_class(&g, k, tcol[q], tbase[q]);
+      if (cls == 2) continue;
+      int v[6], tets[3][4];
+      for (int i = 0; i < 3; ++i) {
+        v[i] = k * g.nsec + tri[3 * q + i];
+        v[i + 3] = (k + 1) * g.nsec + tri[3 * q + i];
+      }
+      split_prism(v, tets);
+      for (int i = 0; i < 3; ++i) {
+        memcpy(&ien[4 * e], tets[i], sizeof(int) * 4);
+        for (int a = 0; a < 4; ++a) newid[tets[i][a]] = 0;
+        et[e++] = (unsigned char)cls;
+      }
+    }
+  free(tri); free(tcol); free(tbase);
+  /* keep the used candidates, in candidate order (the Dompierre splits
+     depend only on the order of the indices, which compaction keeps) */
+  int nn = 0;
+  for (long long c = 0; c < ncand; ++c)
+    if (newid[c] == 0) newid[c] = nn++;
+  tg_mesh *m = (tg_mesh *)calloc(1, sizeof(tg_mesh));
+  m->n_sec = g.nsec;
+  m->n_nodes = nn;
+  m->n_elem = (int)ne;
+  m->xyz = (double *)malloc(sizeof(double) * 3 * nn);
+  m->ring = (int *)malloc(sizeof(int) * nn);
+  m->layer = (int *)malloc(sizeof(int) * nn);
+  m->sec = (int *)malloc(sizeof(int) * nn);
+  for (long long c = 0; c < ncand; ++c) {
+    const int n = newid[c];
+    if (n < 0) continue;
+    const int kn = (int)(c / g.nsec), sidx = (int)(c % g.nsec);
+    double X, Y;
+    int col, q;
+    bif_section_xy(&g, p, sidx, &X, &Y, &col, &q);
+    const double z = kn * g.dz;
+    const double shift = kn > g.k_dau ? bif_side(&g, col) * (z - g.z_dau) * g.tan_a : 0.0;
+    m->xyz[3 * n] = X + shift; m->xyz[3 * n + 1] = Y; m->xyz[3 * n + 2] = z;
+    m->ring[n] = q; m->layer[n] = kn; m->sec[n] = sidx;
+  }
+  m->ien = (int *)malloc(sizeof(int) * 4 * ne);
+  m->pien = (int *)malloc(sizeof(int) * 4 * ne);
+  m->etype = et;
+  for (long long i = 0; i < 4 * ne; ++i) m->ien[i] = newid[ien[i]];
+  free(ien); free(newid);
+  /* interface: nodes of both fluid and solid elements; fluid nodes */
+  unsigned char *hf = (unsigned char *)calloc(nn, 1), *hs = (unsigned char *)calloc(nn, 1);
+  for (long long i = 0; i < ne; ++i)
+    for (int a = 0; a < 4; ++a) (et[i] ? hs : hf)[m->ien[4 * i + a]] = 1;
+  m->iface_of = (int *)malloc(sizeof(int) * nn);
+  m->fluid_id = (int *)malloc(sizeof(int) * nn);
+  int ni = 0, nf = 0;
+  for (int n = 0; n < nn; ++n) {
+    m->iface_of[n] = (hf[n] && hs[n]) ? ni++ : -1;
+    m->fluid_id[n] = hf[n] ? nf++ : -1;
+  }
+  m->n_iface = ni; m->n_fluid = nf; m->n_p = nn + ni;
+  for (long long i = 0; i < ne; ++i)
+    for (int a = 0; a < 4; ++a) {
+      const int n = m->ien[4 * i + a];
+      m->pien[4 * i + a] = (et[i] == 1 && m->iface_of[n] >= 0) ? nn + m->iface_of[n] : n;
+    }
+  /* Dirichlet sets: the whole inlet section, the wall (solid nodes) at the
+     daughters' outlets; mesh: inlet, outlets and the interface */
+  m->dir_v = (unsigned char *)calloc(nn, 1);
+  m->dir_m = (unsigned char *)calloc(nf > 0 ? nf : 1, 1);
+  for (int n = 0; n < nn; ++n) {
+    const int k = m->layer[n];
+    m->dir_v[n] = (unsigned char)(k == 0 || (k == p->n_ax && hs[n]));
+    if (hf[n]) m->dir_m[m->fluid_id[n]] = (unsigned char)(k == 0 || k == p->n_ax || m->iface_of[n] >= 0);
+  }
+  free(hf); free(hs);
+  return m;
+}
+
 tg_mesh *tg_mesh_build(const tg_params *p) {
+  if (p->kind == 2) return bif_mesh_build(p);
   tg_mesh *m = (tg_mesh *)calloc(1, sizeof(tg_mesh));
   const int nc = p->n_circ;
   const int nrad = p->fluid_only ? p->n_rad_f : p->n_rad_f + p->n_rad_s;
@@ -263,7 +485,54 @@ tg_mesh *tg_mesh_build(const tg_params *p) {
    Poiseuille gradient -4 mu u_max / R^2, zero at the outlet; the solid is
    at rest (u = v = p = 0); all time derivatives and the mesh velocity are
    zero (same-Y predictor from a state with zero rates). */
+/* Bifurcation state: a Poiseuille-like profile along the local axis (the
+   parent's z, each daughter's sheared axis), 1 - r^2 / R^2 in section
+   coordinates, in the daughters also ramped to zero over 0.25 R towards the
+   inner wall; the same seeded perturbation as the tube; pressure falling
+   linearly along the arc length with the parent's Poiseuille gradient;
+   interface and solid nodes at rest. */
+static void bif_state_init(const tg_params *p, const tg_mesh *m, double *v, double *pr) {
+  bif_geom g;
+  if (bif_geom_init(p, &g)) return;
+  uint64_t st = p->seed;
+  double a[3];
+  for (int i = 0; i < 3; ++i) a[i] = uniform_pm1(&st);
+  const double G = 4.0 * p->mu_f * p->u_max / (p->R * p->R);
+  const double ang = p->bif_angle_deg * M_PI / 180.0, ca = cos(ang), sa = sin(ang);
+  const double Ltot = p->L + p->bif_daughter_len;
+  const double xa = g.h * (2.0 * g.c0 / g.NC - 1.0), xb = g.h * (2.0 * g.c3 / g.NC - 1.0);
+  for (int n = 0; n < m->n_nodes; ++n) {
+    v[3 * n] = v[3 * n + 1] = v[3 * n + 2] = 0.0;
+    pr[n] = 0.0;
+    if (m->fluid_id[n] < 0) continue;
+    double X, Y;
+    int col, q;
+    bif_section_xy(&g, p, m->sec[n], &X, &Y, &col, &q);
+    const double z = m->xyz[3 * n + 2];
+    const int side = m->layer[n] > g.k_dau ? bif_side(&g, col) : 0;
+    const double s_arc = z <= g.z_dau ? z : g.z_dau + (z - g.z_dau) / ca;
+    pr[n] = G * (Ltot - s_arc);
+    if (m->iface_of[n] >= 0) continue;
+    double phi = 1.0 - (X * X + Y * Y) / (p->R * p->R);
+    if (phi < 0.0) phi = 0.0;
+    if (side != 0) {
+      double d = side < 0 ? xa - X : X - xb;
+      d /= 0.25 * p->R;
+      phi *= d < 0.0 ? 0.0 : (d > 1.0 ? 1.0 : d);
+    }
+    const double dir[3] = {side * sa, 0.0, side ? ca : 1.0};
+    for (int k = 0; k < 3; ++k)
+      v[3 * n + k] = p->u_max * phi * dir[k] +
+                     p->pert_amp * p->u_max * a[k] * sin((double)(k + 1) * M_PI * s_arc / Ltot) * phi;
+  }
+  for (int i = m->n_nodes; i < m->n_p; ++i) pr[i] = 0.0;
+}
+
 void tg_state_init(const tg_params *p, const tg_mesh *m, double *v, double *pr) {
+  if (p->kind == 2) {
+    bif_state_init(p, m, v, pr);
+    return;
+  }
   uint64_t st = p->seed;
   double a[3];
   for (int i = 0; i < 3; ++i) a[i] = uniform_pm1(&st);
@@ -950,15 +1219,28 @@ tg_system *tg_finalize(const tg_mesh *m, const tg_raw *R, const tg_bsr *Lraw, co
      mesh_amp * sin(pi z / L), zero on inlet/outlet sections */
   if (Lraw && nf > 0) {
     S->mesh_g = (double *)calloc((size_t)3 * nf, sizeof(double));
+    bif_geom g;
+    const int bif = P->kind == 2 && bif_geom_init(P, &g) == 0;
     for (int n = 0; n < nn; ++n) {
       int f = m->fluid_id[n];
       if (f < 0 || !m->dir_m[f]) continue;
       int k = m->layer[n];
       if (k == 0 || k == P->n_ax) continue;
-      if (m->ring[n] != P->n_rad_f) continue;
       double x = m->xyz[3 * n], y = m->xyz[3 * n + 1], z = m->xyz[3 * n + 2];
+      double zl = P->L;
+      if (bif) {
+        /* the lateral wall (the lumen circle's ring, in section coordinates:
+           the daughters unsheared); the carina and septum faces stay put */
+        if (m->iface_of[n] < 0) continue;
+        int col, q;
+        bif_section_xy(&g, P, m->sec[n], &x, &y, &col, &q);
+        if (q != g.NRF) continue;
+        zl = P->n_ax * g.dz;
+      } else if (m->ring[n] != P->n_rad_f) {
+        continue;
+      }
       double r = sqrt(x * x + y * y);
-      double a = P->mesh_amp * sin(M_PI * z / P->L);
+      double a = P->mesh_amp * sin(M_PI * z / zl);
       S->mesh_g[3 * f] = a * x / r;
       S->mesh_g[3 * f + 1] = a * y / r;
     }

@@ -438,3 +438,101 @@ def test_resistance_outlet_terms():
     s0 = F.tube_system("tube_mini")
     s1 = F.tube_system("tube_mini", outlet_resistance=0.0)
     assert s1.a_out is None and np.array_equal(s0.b, s1.b)
+
+
+# ------------------------------------------------------------- bifurcation
+def _faces(m):
+    FACES = ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3))
+    f = np.sort(m.ien[:, FACES].reshape(-1, 3), axis=1)
+    key, inv, cnt = np.unique(f, axis=0, return_inverse=True, return_counts=True)
+    return key, inv.ravel(), cnt
+
+
+def test_bifurcation_mesh_is_conforming_sealed_and_splits_in_two():
+    """The bifurcation (one extruded O-grid section whose septum band is lumen
+    in the parent, solid at the carina tip and removed between the sheared
+    daughters): every face is shared by at most two tets, every tet has a
+    positive volume, the lumen touches the outside only at the inlet and
+    outlet planes, the fluid of a parent layer is one connected piece and
+    that of a daughter layer two, and every daughter layer has the same
+    volume (the shear keeps volumes)."""
+    import scipy.sparse as sp
+    import scipy.sparse.csgraph as csg
+    p = F.make_params(**F.PRESETS["bif_mini"])
+    m = F.build_mesh(p)
+    key, inv, cnt = _faces(m)
+    assert cnt.max() == 2
+    x = m.xyz[m.ien]
+    vol = np.abs(np.einsum("ni,ni->n", x[:, 1] - x[:, 0], np.cross(x[:, 2] - x[:, 0], x[:, 3] - x[:, 0]))) / 6
+    assert vol.min() > 0.05 * vol.max()
+    owner = np.repeat(np.arange(m.n_elem), 4)
+    fl = m.etype[owner] == 0
+    kf = np.bincount(inv[fl], minlength=len(key))
+    ks = np.bincount(inv[~fl], minlength=len(key))
+    z = m.xyz[key[(kf == 1) & (ks == 0)]][:, :, 2]
+    zmax = m.xyz[:, 2].max()
+    assert np.all(np.all(z == 0.0, axis=1) | np.all(np.abs(z - zmax) < 1e-12, axis=1))
+    # fluid components per element layer
+    dz = zmax / p.n_ax
+    lay = np.floor(x[:, :, 2].mean(axis=1) / dz).astype(int)
+    both = np.nonzero((kf == 2))[0]
+    fi = np.full(len(key), -1)
+    fj = np.full(len(key), -1)
+    for e, k in zip(owner[fl], inv[fl]):
+        if fi[k] < 0:
+            fi[k] = e
+        else:
+            fj[k] = e
+    adj = sp.coo_matrix((np.ones(both.size), (fi[both], fj[both])), shape=(m.n_elem, m.n_elem)).tocsr()
+    comps = []
+    for k in range(p.n_ax):
+        sel = np.nonzero((lay == k) & (m.etype == 0))[0]
+        comps.append(csg.connected_components(adj[sel][:, sel], directed=False)[0])
+    assert comps[0] == 1 and comps[-1] == 2
+    assert sorted(set(comps)) == [1, 2] and comps == sorted(comps)
+    # the solid carina tip already splits the lumen; the void cells go after it
+    first_dau = comps.index(2) + p.bif_tip_layers
+    vl = np.bincount(lay, weights=vol, minlength=p.n_ax)
+    assert np.allclose(vl[first_dau:], vl[-1], rtol=1e-10) and vl[first_dau - 1] > vl[-1]
+    # the daughters diverge: at the outlet the two lumens lie on either side
+    out = (np.abs(m.xyz[:, 2] - zmax) < 1e-12) & (m.fluid_id >= 0)
+    xs = m.xyz[out, 0]
+    gap = np.sort(xs)
+    assert gap.min() < -p.R and gap.max() > p.R and np.diff(gap).max() > 0.5 * p.R
+
+
+def test_bifurcation_interface_and_pressure_duplication():
+    """Interface nodes are exactly the nodes of both fluid and solid tets;
+    solid tets read the duplicated pressure there, fluid tets the node's;
+    the mesh-motion Laplacian annihilates linear fields in its interior rows
+    and is symmetric positive definite once the Dirichlet rows are
+    eliminated."""
+    p = F.make_params(**F.PRESETS["bif_mini"])
+    asm = F.Assembler(p)
+    m = asm.mesh
+    hf = np.zeros(m.n_nodes, bool)
+    hs = np.zeros(m.n_nodes, bool)
+    hf[m.ien[m.etype == 0].ravel()] = True
+    hs[m.ien[m.etype == 1].ravel()] = True
+    np.testing.assert_array_equal(m.iface_of >= 0, hf & hs)
+    assert m.n_p == m.n_nodes + int((hf & hs).sum())
+    solid = m.etype == 1
+    dup = m.iface_of[m.ien] >= 0
+    np.testing.assert_array_equal(m.pien[solid & dup.any(axis=1)] >= m.n_nodes,
+                                  dup[solid & dup.any(axis=1)])
+    np.testing.assert_array_equal(m.pien[~solid], m.ien[~solid])
+    L = to_csr(asm.mesh_laplacian())
+    fl = np.nonzero(m.fluid_id >= 0)[0]
+    X = m.xyz[fl]
+    free = ~m.dir_m
+    for c in range(3):
+        assert np.allclose((L @ X[:, c])[free], 0.0, atol=1e-12 * np.abs(L).max())
+    Lf = L[free][:, free].toarray()
+    assert np.allclose(Lf, Lf.T) and np.linalg.eigvalsh(Lf).min() > 0
+
+
+def test_rhs_only_matches_the_full_build():
+    """The residual-only right-hand side equals the full build's, bit for
+    bit, for a tube and for the bifurcation at another inflow peak."""
+    for name, u in (("bif_mini", 17.0), ("tube_mini", 44.0)):
+        np.testing.assert_array_equal(F.rhs_only(name, u_max=u), F.tube_system(name, u_max=u).b)

@@ -771,3 +771,22 @@ def test_strength_graph_by_brute_force():
     np.testing.assert_allclose(S, want, rtol=1e-14)
     assert (want > 0).sum() > n  # the case has strong and weak pairs
     assert ((nrm > 0) & (want == 0) & ~np.eye(n, dtype=bool)).any()
+
+
+# ------------------------------------------------------------- bifurcation
+def test_bifurcation_scr_and_mesh_cg_match_direct():
+    """On the bifurcation (parent, carina tip, two sheared half-disk
+    daughters) the oracle's SCR-FGMRES meets 1e-8 and matches the direct
+    solve, and the mesh CG + AMG matches the direct mesh solve."""
+    s = F.tube_system("bif_mini", keep_mesh=True)
+    assert np.isfinite(s.b).all() and np.isfinite(s.mesh_b).all()
+    xd = direct.solve_block(s)
+    sol = scr.SCRSolver(s)
+    x, info = sol.solve(s.b)
+    assert info.converged and sol.rel_residual(x, s.b) <= 1e-8
+    assert np.linalg.norm(x - xd) <= 1e-6 * np.linalg.norm(xd)
+    assert 1 <= info.iters <= 10
+    m = scr.MeshSolver(s, scr.SolverOptions(mm_rtol=1e-12))
+    u, minfo = m.solve(s.mesh_b)
+    ud = direct.solve_mesh(s)
+    assert minfo.converged and np.linalg.norm(u - ud) <= 1e-9 * np.linalg.norm(ud)

@@ -3,9 +3,10 @@ allocating one (scr_bsr_spmv), through the C ABI.
 
 Callers that cannot allocate device memory (graph-captured code, hosts whose
 device memory belongs to another allocator) use the allocation-free entry
-point; it must give the same product.  This file is collected last so that a
-run stopping at the first failure has run every other test before it; it
-also passes when run alone in a fresh process."""
+point; it must give the same product.  This file is collected after the
+others (but the full-size bifurcation) so that a run stopping at the first
+failure has run them before it; it also passes when run alone in a fresh
+process."""
 import numpy as np
 import pytest
 
