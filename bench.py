@@ -34,6 +34,20 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "tube_large"
+
+
+def describe_workload(name: str) -> str:
+    """Geometry of a generator preset in words (circumferential x (lumen +
+    wall rings) x axial layers for the tubes; core, rings and layers for the
+    bifurcation)."""
+    import fsi_inputs as F
+    p = F.PRESETS[name]
+    kind = p.get("kind", 0)
+    if kind == 2:
+        return (f"bifurcation, O-grid core {p['n_circ']}x{p['n_circ']}, ({p['n_rad_f']}+{p['n_rad_s']}) rings, "
+                f"{p['n_ax']} layers, daughters at +-35 degrees")
+    shape = "stenosed tube" if kind == 1 else "straight tube"
+    return f"{shape} {p['n_circ']}x({p['n_rad_f']}+{p['n_rad_s']})x{p['n_ax']}"
 METRIC = "SCR-FGMRES+AMG solves/s to rel-res 1e-8 (mixed vs FP64) on 1 GB300; % HBM peak"
 UNIT = "solves/s"
 
@@ -224,7 +238,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * n_large / n_small * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload} (2,503,844 unknowns); each step one full oracle step on "
+        "config": {"workload": f"{args.workload} ({n_large} unknowns); each step one full oracle step on "
                                f"tube_small ({n_small} unknowns), scaled by the unknown ratio",
                    "precision": "fp64"},
         "cpu_baseline": {"value": scaled, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -538,7 +552,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == pkg.SCR_FP64 else "f64+f32",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}: straight tube 96x(11+5)x400, {s.n_v} nodes, {s.n} unknowns, "
+        "config": {"workload": f"{args.workload}: {describe_workload(args.workload)}, {s.n_v} nodes, {s.n} unknowns, "
                                f"{s.L.nb_rows} mesh nodes", "precision": args.precision,
                    "step": "scr_setup + scr_solve + mm_setup + mm_solve", "l2": "inputs > L2 (no flush)",
                    "parallelism": f"replicas x{world}",
