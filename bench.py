@@ -470,7 +470,7 @@ def main():
     multi = None
     if args.multi_rhs:
         peaks_u = np.random.default_rng(2206).uniform(0.0, 60.0, 8)
-        rhs = [torch.as_tensor(F.tube_system(args.workload, u_max=float(u)).b, device=dev) for u in peaks_u]
+        rhs = [torch.as_tensor(F.rhs_only(args.workload, u_max=float(u)), device=dev) for u in peaks_u]
         xs8 = [torch.empty_like(b) for b in rhs]
         solk = pkg.BlockSolver(precision=pkg.SCR_MIXED, nrhs=8)
         rel8 = None

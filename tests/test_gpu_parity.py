@@ -729,7 +729,7 @@ def _inflow_rhs(name, n_rhs=8, seed=2206):
     """Right-hand sides -R at states whose inflow peaks are drawn U(0, 60)
     cm/s (one Jacobian, at the nominal 30 cm/s, solves all of them)."""
     peaks = np.random.default_rng(seed).uniform(0.0, 60.0, n_rhs)
-    return [F.tube_system(name, u_max=float(u)).b for u in peaks]
+    return [F.rhs_only(name, u_max=float(u)) for u in peaks]
 
 
 @pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
