@@ -653,11 +653,11 @@ struct Gmres {
     ++syncs;
     *iters = 0;
     *rel = 0.0;
-    if (!(hs.h[1] > 0.0)) return true;  // b = 0 -> x = 0
-    if (!std::isfinite(hs.h[1])) {
+    if (!std::isfinite(hs.h[1])) {  // a NaN or infinite right-hand side: x = 0, not converged
       *rel = hs.h[1];
       return false;
     }
+    if (!(hs.h[1] > 0.0)) return true;  // b = 0 -> x = 0
     scale_by<T>(b, &st->inv_hnext, V, n, s);
     for (;;) {
       int k = 0;
@@ -1726,6 +1726,10 @@ static bool mesh_cg(scr_ctx* h, const double* g, double* u, int* iters, double* 
   SCR_CUDA(cudaStreamSynchronize(s));
   *iters = 0;
   *rel = 0.0;
+  if (!std::isfinite(hr[1])) {  // a NaN or infinite right-hand side: u = 0, not converged
+    *rel = hr[1];
+    return false;
+  }
   if (!(hr[1] > 0.0)) return true;
   h->hM.apply<double>(h->mr, h->mz, s);
   cg_dot_rz(h->cg, h->mr, h->mz, n, h->mred, 1, s);
