@@ -556,7 +556,7 @@ def test_nan_right_hand_side_is_reported_and_the_handle_stays_usable(mini):
         sol.solve(mini.b.copy())
         assert sol.residual() <= 1e-8
         sol.mesh_solve(mini.mesh_b.copy())
-        assert sol.mesh_iters()[1] <= 1e-8
+        assert sol.mesh_iters()[1] <= 1e-7  # the true residual of a CG stopped at 1e-8
 
 
 def test_invalid_shapes_rejected(mini):
