@@ -361,6 +361,45 @@ def interface_follow(mesh: Mesh) -> np.ndarray:
     return follow & mesh.dir_m.astype(np.uint8)
 
 
+# --------------------------------------------------------------------------
+# system files (the layout tests/c_abi_client.c reads)
+# --------------------------------------------------------------------------
+def save_system(s: BlockSystem, path: str) -> None:
+    """Write A, B, C, D and b in native byte order: per matrix int32
+    nb_rows, nb_cols, br, bc, nnzb, then int32 row_ptr[nb_rows + 1], int32
+    col[nnzb], float64 val[nnzb * br * bc] (blocks row-major); then float64
+    b[3 n_v + n_p].  A run can restart from the file without the generator."""
+    with open(path, "wb") as f:
+        for M in (s.A, s.B, s.C, s.D):
+            col = np.ascontiguousarray(M.col, dtype=np.int32)
+            np.array([M.nb_rows, M.nb_cols, M.br, M.bc, col.size], dtype=np.int32).tofile(f)
+            np.ascontiguousarray(M.row_ptr, dtype=np.int32).tofile(f)
+            col.tofile(f)
+            np.ascontiguousarray(M.val, dtype=np.float64).tofile(f)
+        np.ascontiguousarray(s.b, dtype=np.float64).tofile(f)
+
+
+def load_system(path: str, name: str = "") -> BlockSystem:
+    """Read a file of ``save_system``; the mesh system and the mesh are not
+    part of it (L, mesh_b and mesh are None)."""
+    with open(path, "rb") as f:
+        mats = []
+        for _ in range(4):
+            nbr, nbc, br, bc, nnzb = (int(v) for v in np.fromfile(f, dtype=np.int32, count=5))
+            rp = np.fromfile(f, dtype=np.int32, count=nbr + 1)
+            col = np.fromfile(f, dtype=np.int32, count=nnzb)
+            val = np.fromfile(f, dtype=np.float64, count=nnzb * br * bc)
+            if rp.size != nbr + 1 or col.size != nnzb or val.size != nnzb * br * bc:
+                raise ValueError(f"{path}: truncated matrix")
+            mats.append(BSR(br, bc, nbr, nbc, rp, col, val))
+        n = 3 * mats[0].nb_rows + mats[3].nb_rows
+        b = np.fromfile(f, dtype=np.float64, count=n)
+        if b.size != n or f.read(1):
+            raise ValueError(f"{path}: wrong right-hand side length")
+    return BlockSystem(name=name, A=mats[0], B=mats[1], C=mats[2], D=mats[3], b=b, L=None, mesh_b=None,
+                       mesh=None, params={})
+
+
 def rhs_only(name: str, **overrides) -> np.ndarray:
     """The right-hand side b = -[R_m; R_p] (Dirichlet velocity rows zero) of
     ``tube_system(name, **overrides)`` without assembling the matrices: the

@@ -9,6 +9,8 @@ import subprocess
 import numpy as np
 import pytest
 
+import fsi_inputs as F
+
 from oracle.sparse import BlockOperator, rel_residual
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -43,17 +45,6 @@ def _compile(out_dir):
     return exe
 
 
-def _write_system(s, path):
-    with open(path, "wb") as f:
-        for M in (s.A, s.B, s.C, s.D):
-            col = np.ascontiguousarray(M.col, dtype=np.int32)
-            np.array([M.nb_rows, M.nb_cols, M.br, M.bc, col.size], dtype=np.int32).tofile(f)
-            np.ascontiguousarray(M.row_ptr, dtype=np.int32).tofile(f)
-            col.tofile(f)
-            np.ascontiguousarray(M.val, dtype=np.float64).tofile(f)
-        np.ascontiguousarray(s.b, dtype=np.float64).tofile(f)
-
-
 def test_header_compiles_as_c_and_the_client_links(tmp_path):
     """No GPU needed: compile with -Wall -Wextra -Werror and link."""
     exe = _compile(str(tmp_path))
@@ -65,7 +56,7 @@ def test_header_compiles_as_c_and_the_client_links(tmp_path):
 def test_c_client_solves_like_the_oracle(tmp_path, mini_system, mini_direct, precision):
     exe = _compile(str(tmp_path))
     sysf, xf = str(tmp_path / "system.bin"), str(tmp_path / "x.bin")
-    _write_system(mini_system, sysf)
+    F.save_system(mini_system, sysf)
     r = subprocess.run([exe, sysf, xf, precision], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
     words = r.stdout.split()

@@ -536,3 +536,24 @@ def test_rhs_only_matches_the_full_build():
     bit, for a tube and for the bifurcation at another inflow peak."""
     for name, u in (("bif_mini", 17.0), ("tube_mini", 44.0)):
         np.testing.assert_array_equal(F.rhs_only(name, u_max=u), F.tube_system(name, u_max=u).b)
+
+
+def test_system_file_round_trip(tmp_path):
+    """save_system / load_system keep every array bit for bit (the layout the
+    C client reads), and a truncated file is rejected."""
+    s = F.tube_system("tube_mini")
+    path = str(tmp_path / "sys.bin")
+    F.save_system(s, path)
+    t = F.load_system(path)
+    for a, b in ((s.A, t.A), (s.B, t.B), (s.C, t.C), (s.D, t.D)):
+        assert (a.br, a.bc, a.nb_rows, a.nb_cols) == (b.br, b.bc, b.nb_rows, b.nb_cols)
+        np.testing.assert_array_equal(a.row_ptr, b.row_ptr)
+        np.testing.assert_array_equal(a.col, b.col)
+        np.testing.assert_array_equal(a.val, b.val)
+    np.testing.assert_array_equal(s.b, t.b)
+    with open(path, "rb") as f:
+        data = f.read()
+    with open(path, "wb") as f:
+        f.write(data[:-8])
+    with pytest.raises(ValueError):
+        F.load_system(path)
