@@ -661,7 +661,7 @@ struct Gmres {
     scale_by<T>(b, &st->inv_hnext, V, n, s);
     for (;;) {
       int k = 0;
-      bool stop = false, breakdown = false;
+      bool breakdown = false;
       double r = 1.0;
       for (int j = 0; j < m; ++j) {
         T* vj = V + (size_t)j * n;
@@ -684,10 +684,7 @@ struct Gmres {
           *rel = r;
           return false;
         }
-        if (r <= tol || *iters >= maxit || breakdown) {
-          stop = true;
-          break;
-        }
+        if (r <= tol || *iters >= maxit || breakdown) break;
       }
       gmres_update<T>(st, k, Z, n, x, n, s);
       *rel = r;
@@ -700,7 +697,6 @@ struct Gmres {
       } else if (*iters >= maxit) {
         return false;
       }
-      (void)stop;
       // restart from the current residual r = b - op(x)
       op(x, w);
       axpby_t<T>(1.0, b, -1.0, w, n, s);
@@ -1319,7 +1315,6 @@ static void reset_solve_stats(scr_ctx* h) {
 }
 
 static int solve_impl(scr_ctx* h, const double* b, double* x, double rtol) {
-  const long long n = 3LL * h->nv + h->np;
   reset_solve_stats(h);
   Gmres<double>::Op op = [&](const double* xi, double* y) { apply_calA(h, xi, y, nullptr, false); };
   Gmres<double>::Op pc = [&](const double* r, double* y) { apply_pc_any(h, r, y); };
@@ -1333,7 +1328,6 @@ static int solve_impl(scr_ctx* h, const double* b, double* x, double rtol) {
   h->stats.vcycles_S = h->hS.vcycles;
   h->stats.syncs = h->gOuter.syncs + h->gA.syncs + h->gS.syncs + h->gI.syncs + h->gAf.syncs + h->gSf.syncs +
                    h->gIf.syncs;
-  (void)n;
   if (!std::isfinite(h->stats.rel_res)) return SCR_NOT_CONVERGED;
   return (ok && h->stats.rel_res <= rtol) ? SCR_OK : SCR_NOT_CONVERGED;
 }
