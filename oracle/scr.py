@@ -32,7 +32,7 @@ import dataclasses
 import numpy as np
 
 from . import amg
-from .krylov import KrylovInfo, fgmres, gmres, pcg
+from .krylov import fgmres, gmres, pcg
 from .schur import schur_hat, simple_diagonal
 from .sparse import BlockOperator, rel_residual, to_csr
 

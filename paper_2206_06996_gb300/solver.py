@@ -7,7 +7,7 @@ import os
 
 import numpy as np
 
-from .abi import (BsrOut, Bsr, KProf, Mesh, Opts, Physics, SCR_NOT_CONVERGED, SCR_OK, ScrError, Stats,
+from .abi import (BsrOut, Bsr, KProf, Mesh, Opts, Physics, SCR_NOT_CONVERGED, SCR_OK, Stats,
                   check, load_library)
 
 
