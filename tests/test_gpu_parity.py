@@ -536,29 +536,6 @@ def test_not_converged_status(mini):
         assert np.all(np.isfinite(x))
 
 
-def test_nan_right_hand_side_is_reported_and_the_handle_stays_usable(mini):
-    """A NaN in the right-hand side of the block solve or of the mesh solve
-    is reported as SCR_NOT_CONVERGED (never as a converged zero), and the
-    same handle then solves a clean system to 1e-8."""
-    with pkg.BlockSolver() as sol:
-        sol.setup(mini.A, mini.B, mini.C, mini.D)
-        b = mini.b.copy()
-        b[7] = np.nan
-        with pytest.raises(pkg.ScrError) as e:
-            sol.solve(b)
-        assert e.value.status == 3
-        sol.mesh_setup(mini.L)
-        g = mini.mesh_b.copy()
-        g[5] = np.nan
-        with pytest.raises(pkg.ScrError) as e:
-            sol.mesh_solve(g)
-        assert e.value.status == 3
-        sol.solve(mini.b.copy())
-        assert sol.residual() <= 1e-8
-        sol.mesh_solve(mini.mesh_b.copy())
-        assert sol.mesh_iters()[1] <= 1e-7  # the true residual of a CG stopped at 1e-8
-
-
 def test_invalid_shapes_rejected(mini):
     with pkg.BlockSolver() as sol:
         with pytest.raises(pkg.ScrError) as e:
@@ -1034,3 +1011,27 @@ def test_gpu_bifurcation_eight_inflow_peaks():
         assert rel_residual(op, x, b) <= 1e-8
     ref, info = scr.SCRSolver(s, scr.SolverOptions(rtol=1e-12)).solve(rhs[0])
     assert info.converged and _rel(xs[0], ref) <= 1e-6
+
+
+# ---------------------------------------------------------------- non-finite input
+def test_nan_right_hand_side_is_reported_and_the_handle_stays_usable(mini):
+    """A NaN in the right-hand side of the block solve or of the mesh solve
+    is reported as SCR_NOT_CONVERGED (never as a converged zero), and the
+    same handle then solves a clean system to 1e-8."""
+    with pkg.BlockSolver() as sol:
+        sol.setup(mini.A, mini.B, mini.C, mini.D)
+        b = mini.b.copy()
+        b[7] = np.nan
+        with pytest.raises(pkg.ScrError) as e:
+            sol.solve(b)
+        assert e.value.status == 3
+        sol.mesh_setup(mini.L)
+        g = mini.mesh_b.copy()
+        g[5] = np.nan
+        with pytest.raises(pkg.ScrError) as e:
+            sol.mesh_solve(g)
+        assert e.value.status == 3
+        sol.solve(mini.b.copy())
+        assert sol.residual() <= 1e-8
+        sol.mesh_solve(mini.mesh_b.copy())
+        assert sol.mesh_iters()[1] <= 1e-7  # the true residual of a CG stopped at 1e-8
