@@ -308,7 +308,8 @@ int scr_corrector(scr_handle h, double* v, double* p, double* vdot, double* u, i
    is the mesh Laplacian WITHOUT boundary conditions, used to lift the
    Dirichlet data into the right-hand side of the eliminated system that
    mm_setup received.  All arrays are host memory, copied (the caller keeps
-   ownership).  SCR_INVALID_ARG on NULL, sizes or maps that do not fit. */
+   ownership).  A later scr_assembly_setup drops the coupling.  SCR_INVALID_ARG
+   on NULL, sizes or maps that do not fit. */
 int scr_mesh_coupling(scr_handle h, int n_fluid, const int* fluid_id, const unsigned char* dir_m,
                       const unsigned char* follow, const scr_bsr* L_raw);
 

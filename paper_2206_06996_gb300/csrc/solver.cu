@@ -1949,6 +1949,7 @@ int scr_assembly_setup(scr_handle h, const scr_mesh* m, const scr_physics* ph) {
       throw std::invalid_argument("scr_assembly_setup: densities, modulus and time step must be positive");
     cudaStream_t s = h->s;
     h->have_residual = false;
+    h->have_coupling = false;  // a mesh coupling belongs to the previous mesh
     h->rmats.reset(new DeviceArena(s));
     ResidualPhysics rp{ph->rho_f, ph->mu_f, ph->rho_s, ph->E_s / (2.0 * (1.0 + ph->nu_s)), ph->dt,
                        ph->c_m_solid, ph->c_c_solid};
