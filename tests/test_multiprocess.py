@@ -70,3 +70,11 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setattr(bench, "oracle_step_sample", lambda *a, **k: pytest.fail("rank 1 must not run the oracle"))
     bench.run_reference(type("A", (), {"workload": "tube_large", "warmup": 1, "steps": 1, "gpus": 2})())
     assert capsys.readouterr().out == ""
+
+
+def test_bench_describes_each_workload_from_its_preset():
+    """The bench line names its workload by the preset's geometry."""
+    import bench
+    assert bench.describe_workload("tube_large") == "straight tube 96x(11+5)x400"
+    assert bench.describe_workload("stenosis") == "stenosed tube 160x(13+7)x600"
+    assert bench.describe_workload("bifurcation").startswith("bifurcation, O-grid core 40x40, (24+5) rings")
