@@ -54,6 +54,7 @@ class Params(C.Structure):
         ("c_m_solid", C.c_double), ("c_c_solid", C.c_double),
         ("seed", C.c_uint64),
         ("bif_angle_deg", C.c_double), ("bif_daughter_len", C.c_double), ("bif_tip_layers", C.c_int),
+        ("bif_bl_layers", C.c_int), ("bif_bl_ratio", C.c_double),
     ]
 
 
@@ -275,8 +276,10 @@ PRESETS = {
     "tube_mini": dict(n_circ=12, n_rad_f=3, n_rad_s=2, n_ax=12),
     # bifurcation (kind 2): parent R = 0.5 cm, wall 0.06 cm (12% of R), 4 cm
     # parent and 4 cm daughters at +-35 degrees; n_circ = core cells per
-    # side of the O-grid's square, n_rad_f lumen rings, n_rad_s wall rings
-    "bifurcation": dict(kind=2, R=0.5, wall=0.06, L=4.0, n_circ=40, n_rad_f=24, n_rad_s=5, n_ax=633),
+    # side of the O-grid's square, n_rad_f lumen rings, n_rad_s wall rings;
+    # the full size has 3 boundary layers (ratio 0.6) next to the lumen wall
+    "bifurcation": dict(kind=2, R=0.5, wall=0.06, L=4.0, n_circ=40, n_rad_f=24, n_rad_s=5, n_ax=633,
+                        bif_bl_layers=3, bif_bl_ratio=0.6),
     "bif_small": dict(kind=2, R=0.5, wall=0.06, L=4.0, n_circ=16, n_rad_f=8, n_rad_s=2, n_ax=16),
     "bif_mini": dict(kind=2, R=0.5, wall=0.06, L=4.0, n_circ=10, n_rad_f=4, n_rad_s=1, n_ax=10),
 }

@@ -52,6 +52,10 @@ typedef struct {
      the solid carina tip */
   double bif_angle_deg, bif_daughter_len;
   int bif_tip_layers;
+  /* kind 2: the last bif_bl_layers lumen-ring intervals next to the wall
+     shrink geometrically by bif_bl_ratio each (0: uniform rings) */
+  int bif_bl_layers;
+  double bif_bl_ratio;
 } tg_params;
 
 typedef struct {
@@ -86,6 +90,7 @@ void tg_default_params(tg_params *p) {
   p->c_m_solid = 1.0; p->c_c_solid = 0.0;
   p->seed = 2206;
   p->bif_angle_deg = 35.0; p->bif_daughter_len = 4.0; p->bif_tip_layers = 2;
+  p->bif_bl_layers = 0; p->bif_bl_ratio = 0.6;
 }
 
 /* generalized-alpha constants of the first-order scheme (Sec. 3.4) */
@@ -173,17 +178,35 @@ void tg_mesh_free(tg_mesh *m) {
    with its wall) and is sheared sideways, x -/+= (z - z_dau) tan(angle):
    a shear has determinant 1, so every tet keeps its volume and its
    orientation.  Nodes that only removed cells use are dropped. */
+#define BIF_MAX_RINGS 256
 typedef struct {
   int NC, NRF, NRS, NR, ncore, nsec;
   int c0, c1, c2, c3;
   int k_tip, k_dau;
   double h, dz, tan_a, z_dau;
+  double frac[BIF_MAX_RINGS + 1]; /* lumen ring q sits at frac[q] of the way from the square to R */
 } bif_geom;
 
 static int bif_geom_init(const tg_params *p, bif_geom *g) {
   memset(g, 0, sizeof(*g));
   g->NC = p->n_circ; g->NRF = p->n_rad_f; g->NRS = p->n_rad_s; g->NR = g->NRF + g->NRS;
   if (g->NC < 8 || (g->NC & 1) || g->NRF < 1 || g->NRS < 1 || p->n_ax < 4 || p->fluid_only) return -1;
+  if (g->NRF > BIF_MAX_RINGS || p->bif_bl_layers < 0 || p->bif_bl_layers > g->NRF) return -1;
+  if (p->bif_bl_layers > 0 && !(p->bif_bl_ratio > 0.0 && p->bif_bl_ratio <= 1.0)) return -1;
+  {
+    /* interval widths: uniform w inside, then w r, w r^2, ..., w r^nbl next to the wall */
+    const int nbl = p->bif_bl_layers;
+    double width[BIF_MAX_RINGS], tot = 0.0, f = 1.0;
+    for (int q = 0; q < g->NRF; ++q) {
+      if (q >= g->NRF - nbl) f *= p->bif_bl_ratio;
+      width[q] = f;
+      tot += f;
+    }
+    g->frac[0] = 0.0;
+    for (int q = 0; q < g->NRF; ++q)
+      g->frac[q + 1] = nbl ? g->frac[q] + width[q] / tot : (double)(q + 1) / g->NRF;
+    g->frac[g->NRF] = 1.0;
+  }
   g->ncore = (g->NC + 1) * (g->NC + 1);
   g->nsec = g->ncore + g->NR * 4 * g->NC;
   g->h = 0.6 * p->R / sqrt(2.0);
@@ -229,7 +252,7 @@ static void bif_section_xy(const bif_geom *g, const tg_params *p, int s, double 
     const double Sx = g->h * (2.0 * i / NC - 1.0), Sy = g->h * (2.0 * j / NC - 1.0);
     const double th = atan2(Sy, Sx);
     if (q <= g->NRF) {
-      const double f = (double)q / g->NRF;
+      const double f = g->frac[q];
       *X = Sx + f * (p->R * cos(th) - Sx); *Y = Sy + f * (p->R * sin(th) - Sy);
     } else {
       const double rad = p->R + p->wall * (double)(q - g->NRF) / g->NRS;

@@ -557,3 +557,25 @@ def test_system_file_round_trip(tmp_path):
         f.write(data[:-8])
     with pytest.raises(ValueError):
         F.load_system(path)
+
+
+def test_bifurcation_boundary_layers_are_graded():
+    """With n boundary layers of ratio r the last n lumen-ring intervals along
+    a ray shrink by r each towards the wall, the inner ones stay uniform, and
+    the graded mesh is still conforming with positive volumes."""
+    kw = dict(F.PRESETS["bif_mini"], bif_bl_layers=3, bif_bl_ratio=0.6)
+    p = F.make_params(**kw)
+    m = F.build_mesh(p)
+    nc, nrf = p.n_circ, p.n_rad_f
+    ncore = (nc + 1) ** 2
+    # the ray through the core corner (0, 0): node layer 0 keeps every section node
+    ids = [0] + [ncore + (q - 1) * 4 * nc for q in range(1, nrf + 1)]
+    r = np.linalg.norm(m.xyz[ids, :2], axis=1)
+    w = np.diff(r)
+    np.testing.assert_allclose(w[-3:] / w[-4:-1], 0.6, rtol=1e-9)
+    np.testing.assert_allclose(r[-1], p.R, rtol=1e-12)
+    key, inv, cnt = _faces(m)
+    assert cnt.max() == 2
+    x = m.xyz[m.ien]
+    vol = np.abs(np.einsum("ni,ni->n", x[:, 1] - x[:, 0], np.cross(x[:, 2] - x[:, 0], x[:, 3] - x[:, 0])))
+    assert vol.min() > 0.01 * vol.max()
