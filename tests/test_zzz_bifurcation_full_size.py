@@ -1,6 +1,7 @@
 """The bifurcation at full size: parent R = 0.5 cm with a 0.06 cm wall, a
 4 cm parent and two 4 cm daughters at +-35 degrees, 40 x 40 core cells, 24
-lumen and 5 wall rings, 633 layers (about 4M nodes, 16M unknowns).  Eight
+lumen rings (the last 3 graded by 0.6 towards the wall) and 5 wall rings,
+633 layers (about 4M nodes, 16M unknowns).  Eight
 right-hand sides -R at inflow peaks drawn U(0, 60) cm/s on one Jacobian
 (the nominal 30 cm/s), solved as one 8-column block solve in mixed
 precision with the FP64 outer FGMRES.  At this size the oracle checks
