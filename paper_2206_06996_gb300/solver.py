@@ -102,6 +102,7 @@ class BlockSolver:
         check(self.lib.scr_create(C.byref(h), C.byref(o), C.c_void_p(stream)))
         self.h = h
         self.n_v = self.n_p = self.n_m = 0
+        self.n_fluid = 0  # fluid nodes of the mesh coupling (mesh_coupling)
 
     # -------------------------------------------------------------- life
     def close(self):
