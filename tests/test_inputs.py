@@ -579,3 +579,50 @@ def test_bifurcation_boundary_layers_are_graded():
     x = m.xyz[m.ien]
     vol = np.abs(np.einsum("ni,ni->n", x[:, 1] - x[:, 0], np.cross(x[:, 2] - x[:, 0], x[:, 3] - x[:, 0])))
     assert vol.min() > 0.01 * vol.max()
+
+
+# ------------------------------------------------- first-order generalized-alpha
+def _sdof_step(rho_inf, Om):
+    """One step of the first-order generalized-alpha scheme (Sec. 3.4) on
+    the single-degree-of-freedom oscillator d' = v, v' = -w^2 d written as a
+    first-order system (dt = 1, w = Om): unknowns (d, v, d', v') at t_{n+1};
+    returns the 4 x 4 amplification matrix built from the scheme's four
+    defining relations and the constants of the generator."""
+    am, af, ga = F.genalpha(rho_inf)
+    w2 = Om * Om
+    M = np.array([[1, 0, -ga, 0], [0, 1, 0, -ga], [0, -af, am, 0], [w2 * af, 0, 0, am]], dtype=float)
+    N = np.array([[1, 0, 1 - ga, 0], [0, 1, 0, 1 - ga], [0, 1 - af, -(1 - am), 0],
+                  [-w2 * (1 - af), 0, 0, -(1 - am)]], dtype=float)
+    return np.linalg.solve(M, N), (am, af, ga)
+
+
+def test_first_order_generalized_alpha_limits_and_order():
+    """The constants alpha_m = (3 - rho) / (2 (1 + rho)), alpha_f = gamma =
+    1 / (1 + rho) make the scheme what the appendix's analysis states: the
+    spectral radius of the amplification matrix tends to 1 as Omega = w dt ->
+    0 and to rho_inf as Omega -> infinity; the first step's displacement at
+    Omega -> infinity is (1 - alpha_m / (alpha_f gamma)) d_0 (the appendix's
+    printed limit); the global error at a fixed time falls four-fold when dt
+    halves (second order).  A wrong constant breaks one of them."""
+    from oracle import corrector
+    for rho in (0.0, 0.25, 0.5, 1.0):
+        A, (am, af, ga) = _sdof_step(rho, 1e9)
+        assert abs(np.abs(np.linalg.eigvals(A)).max() - rho) < 1e-3
+        A0, _ = _sdof_step(rho, 1e-4)
+        assert abs(np.abs(np.linalg.eigvals(A0)).max() - 1.0) < 1e-6
+        d0 = 0.7
+        x1 = A @ np.array([d0, 1.3, 1.3, -1e18 * d0])  # compatible start: d'(0) = v(0), v'(0) = -w^2 d(0)
+        assert x1[0] == pytest.approx((1.0 - am / (af * ga)) * d0, rel=1e-6)
+        # the oracle's corrector weights come from the same constants
+        amo, cf, cu = corrector.genalpha_weights(rho, 1e-4)
+        assert amo == pytest.approx(am, rel=1e-15) and cf == pytest.approx(af * ga * 1e-4, rel=1e-15)
+        assert cu == pytest.approx(cf * cf / am, rel=1e-15)
+    for rho in (0.0, 0.5):
+        errs = []
+        for n in (200, 400):
+            A, _ = _sdof_step(rho, 1.0 / n)
+            x = np.array([1.0, 0.0, 0.0, -1.0 / n ** 2])
+            for _ in range(n):
+                x = A @ x
+            errs.append(abs(x[0] - np.cos(1.0)))
+        assert 3.8 < errs[0] / errs[1] < 4.2
