@@ -626,3 +626,30 @@ def test_first_order_generalized_alpha_limits_and_order():
                 x = A @ x
             errs.append(abs(x[0] - np.cos(1.0)))
         assert 3.8 < errs[0] / errs[1] < 4.2
+
+
+def test_bifurcation_state_inlet_is_poiseuille_and_walls_rest():
+    """The bifurcation's state: at the inlet section the axial velocity is
+    u_max (1 - r^2 / R^2) exactly (the perturbation vanishes there) with no
+    transverse part; interface and solid nodes are at rest; the fluid
+    pressure falls along the arc length (parent z, then each daughter's
+    axis), the same in both daughters by symmetry of the draw's profile."""
+    p = F.make_params(**F.PRESETS["bif_mini"])
+    asm = F.Assembler(p)
+    m = asm.mesh
+    v, pr = asm.initial_state()
+    V = v.reshape(-1, 3)
+    inlet = (m.layer == 0) & (m.fluid_id >= 0) & (m.iface_of < 0)
+    r2 = (m.xyz[inlet, :2] ** 2).sum(axis=1)
+    np.testing.assert_allclose(V[inlet, 2], p.u_max * np.clip(1 - r2 / p.R ** 2, 0, None), rtol=1e-12, atol=1e-12)
+    assert np.all(V[inlet, :2] == 0.0)
+    rest = (m.fluid_id < 0) | (m.iface_of >= 0)
+    assert np.all(V[rest] == 0.0)
+    fl = m.fluid_id >= 0
+    z = m.xyz[fl, 2]
+    order = np.argsort(z)
+    assert np.all(np.diff(pr[:m.n_nodes][fl][order]) <= 1e-12)
+    # the two daughters: mirror pressures at the outlet
+    out = fl & (m.layer == p.n_ax)
+    xo = m.xyz[out, 0]
+    assert np.allclose(np.sort(pr[:m.n_nodes][out][xo < 0]), np.sort(pr[:m.n_nodes][out][xo > 0]))
