@@ -69,9 +69,6 @@ class Hierarchy:
     def n_levels(self) -> int:
         return len(self.levels)
 
-    def operator_complexity(self) -> float:
-        return sum(l.A.nnz for l in self.levels) / self.levels[0].A.nnz
-
 
 def block_norms(A: sp.csr_matrix, bs: int):
     """(rows, cols, norms) of the bs x bs blocks of A."""
