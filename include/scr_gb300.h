@@ -52,7 +52,7 @@ extern "C" {
 #define SCR_INVALID_ARG 1
 #define SCR_CUDA_ERROR 2
 #define SCR_NOT_CONVERGED 3 /* x holds the best iterate; iters/residual valid */
-#define SCR_DEVICE_TIMEOUT 4
+#define SCR_DEVICE_TIMEOUT 4 /* reserved: no kernel of this library waits on another */
 #define SCR_SINGULAR 5
 
 /* arithmetic of the preconditioner (the outer FGMRES, the Gram-Schmidt
@@ -75,6 +75,8 @@ extern "C" {
 #define SCR_EXPORT_OPERATOR 0    /* level operator A_l (level 0 of SCR_HIER_SHAT is Shat) */
 #define SCR_EXPORT_PROLONGATOR 1 /* smoothed prolongator P_l */
 #define SCR_EXPORT_AGGREGATES 2  /* aggregate id per block row of level l (-1: none), into col_idx */
+#define SCR_EXPORT_ROOTS 3       /* root block row of each aggregate of level l (the distance-2
+                                    independent node that seeded it), n_agg entries into col_idx */
 
 typedef struct scr_ctx* scr_handle;
 
@@ -101,17 +103,10 @@ typedef struct {
   int amg_smoother;   /* 0: l1-Jacobi (amg_nu sweeps); 1: Chebyshev on D^{-1}A (default) */
   int amg_degree;     /* Chebyshev degree, 3 */
   int spmv_group;     /* 0: autotune/heuristic; 1..16: lanes per block row; 101..116: 100 + lanes per
-                         scalar row; 201, 202, 204, 208: staged kernel with 1..8 lanes per scalar row
-                         where the matrix has a tile plan (forces the product kernel of every matrix) */
+                         scalar row (forces the product kernel of every matrix) */
   int sell;           /* 0: slab products; W > 0: products with A, Shat and L use a sliced block-ELL
                          copy with rows sorted by length inside windows of W block rows
                          (W a multiple of 32, at most 1024); default 0 */
-  int staged;         /* 1: the products with A, Shat, L and the two finest levels of each hierarchy
-                         get a tile plan, and the autotuner also times the staged kernel (tiles
-                         bulk-copied into shared memory ahead of the lanes); 0 (default): never
-                         staged (measured slower than the scalar-row kernel on the tube operators) */
-  int stage_kb;       /* staged kernel: KiB of matrix data per stage, 4..96, default 16 */
-  int stages;         /* staged kernel: tiles in flight per CTA, 2..4, default 2 */
   int l2_prefetch;    /* scalar-row products: each CTA prefetches into L2 the values and indices of
                          the CTA this many indices ahead (bulk L2 prefetch); 0 off; default 192 */
   int amg_coarse_bf16;/* mixed form only: 1 (default) stores the values of the coarse AMG levels
@@ -164,7 +159,6 @@ typedef struct {
   long long spmv_bytes;       /* modelled HBM bytes of the SpMV-type launches (process total) */
   int levels_A, levels_S, levels_M;
   int syncs;                  /* host waits on device scalars */
-  long long staged_launches;  /* launches of the staged product kernel (process total) */
 } scr_stats;
 
 /* Fill o with the defaults listed above.  Never fails for non-NULL o. */
@@ -415,20 +409,22 @@ int scr_bsr_spmv(const scr_bsr* M, const double* x, double* y, void* cuda_stream
 
 /* y = M x like scr_bsr_spmv, but without allocating any device memory.
    The paper has no counterpart: this entry point exists for callers that
-   cannot let a library call cudaMalloc/cudaFree, such as code recorded into
-   a CUDA graph (allocation calls cannot be captured, and cudaFree waits for
-   the whole device), hosts whose device memory is owned by another
-   allocator or fixed at start-up, and tight loops that must not pay an
-   allocation per call.  Its scratch (the matrix values in the kernel's row
-   layout and a validation flag) is one static device array that every GPU
-   loading the library keeps until the process exits; matrices with more
-   than 2,097,152 stored scalars (nnzb * br * bc, 16 MiB) are rejected with
-   SCR_INVALID_ARG.  The first call on each device looks up the array's
-   device address (cudaGetSymbolAddress) with that device current; make
-   that first call before any stream capture.  All calls share the array:
-   calls whose work overlaps on the GPU (different streams, or different
-   host threads) race and give wrong results; serialise them.  Arguments,
-   layout and errors are those of scr_bsr_spmv. */
+   cannot let a library call cudaMalloc/cudaFree: hosts whose device memory
+   is owned by another allocator or fixed at start-up (a library's own
+   allocation can fail there or starve the owner), and code that must not
+   call cudaFree, which waits for the whole device.  Its scratch (the matrix
+   values in the kernel's row layout and a validation flag) is one static
+   device array that every GPU loading the library keeps until the process
+   exits; matrices with more than 2,097,152 stored scalars (nnzb * br * bc,
+   16 MiB) are rejected with SCR_INVALID_ARG.  The first call on each device
+   looks up the array's device address (cudaGetSymbolAddress) with that
+   device current and keeps it for the life of the process, so do not call
+   it on a device after cudaDeviceReset.  Every call validates the indices
+   on the device, copies the result flag back to the host and synchronises
+   the stream twice (before the product and after it).  All calls share the
+   array: calls whose work overlaps on the GPU (different streams, or
+   different host threads) race and give wrong results; serialise them.
+   Arguments, layout and errors are those of scr_bsr_spmv. */
 int scr_bsr_spmv_noalloc(const scr_bsr* M, const double* x, double* y, void* cuda_stream);
 
 #ifdef __cplusplus

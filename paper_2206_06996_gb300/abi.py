@@ -10,7 +10,7 @@ SCR_OK, SCR_INVALID_ARG, SCR_CUDA_ERROR, SCR_NOT_CONVERGED, SCR_DEVICE_TIMEOUT, 
 SCR_FP64, SCR_MIXED = 0, 1
 SCR_PC_SCR, SCR_PC_SIMPLE, SCR_PC_SIMPLEC = 0, 1, 2
 SCR_HIER_A, SCR_HIER_SHAT, SCR_HIER_MESH = 0, 1, 2
-SCR_EXPORT_OPERATOR, SCR_EXPORT_PROLONGATOR, SCR_EXPORT_AGGREGATES = 0, 1, 2
+SCR_EXPORT_OPERATOR, SCR_EXPORT_PROLONGATOR, SCR_EXPORT_AGGREGATES, SCR_EXPORT_ROOTS = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "SCR_OK", 1: "SCR_INVALID_ARG", 2: "SCR_CUDA_ERROR", 3: "SCR_NOT_CONVERGED",
                 4: "SCR_DEVICE_TIMEOUT", 5: "SCR_SINGULAR"}
@@ -31,7 +31,7 @@ class Opts(C.Structure):
         ("amg_theta", C.c_double), ("amg_max_levels", C.c_int), ("amg_coarse_size", C.c_int),
         ("amg_nu", C.c_int), ("amg_trunc", C.c_double), ("amg_pmax", C.c_int), ("autotune", C.c_int),
         ("amg_smoother", C.c_int), ("amg_degree", C.c_int), ("spmv_group", C.c_int),
-        ("sell", C.c_int), ("staged", C.c_int), ("stage_kb", C.c_int), ("stages", C.c_int),
+        ("sell", C.c_int),
         ("l2_prefetch", C.c_int), ("amg_coarse_bf16", C.c_int), ("cuda_graphs", C.c_int),
         ("nrhs", C.c_int),
         ("mm_rtol", C.c_double), ("mm_max_it", C.c_int), ("verbose", C.c_int),
@@ -67,7 +67,6 @@ class Stats(C.Structure):
         ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("mm_setup_ms", C.c_double),
         ("mm_solve_ms", C.c_double), ("kernel_launches", C.c_longlong), ("spmv_bytes", C.c_longlong),
         ("levels_A", C.c_int), ("levels_S", C.c_int), ("levels_M", C.c_int), ("syncs", C.c_int),
-        ("staged_launches", C.c_longlong),
     ]
 
     def as_dict(self) -> dict:

@@ -413,6 +413,12 @@ __global__ void k_root_flags(int n, const unsigned long long* __restrict__ key, 
   flag[i] = (key[i] >> 62) == ST_IN ? 1 : 0;
 }
 
+__global__ void k_root_list(int n, const int* __restrict__ flag, const int* __restrict__ rootid,
+                            int* __restrict__ roots) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && flag[i]) roots[rootid[i]] = i;
+}
+
 __global__ void k_agg_pass1(int n, const unsigned long long* __restrict__ key, const int* __restrict__ rootid,
                             const int* __restrict__ srp, const int* __restrict__ snb,
                             const unsigned char* __restrict__ isolated, int* __restrict__ agg) {
@@ -510,6 +516,10 @@ Aggregation aggregate(const DBsr<double>& A, double theta, DeviceArena& arena, D
   k_root_flags<<<G, T, 0, s>>>(n, key, flag);
   SCR_LAUNCH();
   out.n_agg = (int)exclusive_scan(flag, rootid, n, tmp, s);
+  out.roots = arena.alloc<int>(out.n_agg + 1);
+  k_root_list<<<G, T, 0, s>>>(n, flag, rootid, out.roots);
+  SCR_LAUNCH();
+  counters().launches++;
   int* agg1 = tmp.alloc<int>(n);
   k_agg_pass1<<<G, T, 0, s>>>(n, key, rootid, srp, snb, isolated, agg1);
   k_agg_pass2<<<G, T, 0, s>>>(n, srp, snb, sw, isolated, agg1, out.agg);

@@ -42,11 +42,6 @@ struct DBsr {
   T* val = nullptr;
   int g = 0;                  // product kernel code (0: heuristic; see spmv.cu)
   const void* sell = nullptr; // host pointer to a DSell<T> copy used for products (optional)
-  // tile plan of the staged product (spmv_staged.cu): tile t covers the
-  // block rows tiles[t] .. tiles[t+1]-1; a stage holds stage_v bytes of
-  // values and stage_c bytes of indices, enough for any tile
-  const int* tiles = nullptr;
-  int ntiles = 0, stage_v = 0, stage_c = 0, stages = 0;
   // BF16 copy of val (same slab layout): when set, FP32 products read these
   // values instead (coarse AMG levels of the mixed-precision form)
   const void* hval = nullptr;
@@ -82,9 +77,8 @@ class DeviceArena {
   T* alloc(size_t n) {
     void* p = nullptr;
     if (n == 0) n = 1;
-    // kSlack bytes past the last element: the staged products copy whole
-    // 16-byte lines with bulk copies, so they may read up to 15 bytes past
-    // the end of a value or index array
+    // kSlack bytes past the last element (vector loads of the last 16-byte
+    // group of an array never leave the allocation)
     SCR_CUDA(cudaMallocAsync(&p, n * sizeof(T) + kSlack, stream_));
     ptrs_.push_back(p);
     bytes_ += n * sizeof(T);

@@ -1,7 +1,6 @@
 // Fused epilogues of the block products: what a product kernel does with
 // the row sum acc of M x for scalar output row o (flat index gi = o * nrhs
-// + h for right-hand side h).  Shared by the product kernels of spmv.cu and
-// spmv_staged.cu.
+// + h for right-hand side h).  Shared by the product kernels.
 #pragma once
 #include "kernels.h"
 

@@ -9,7 +9,6 @@ namespace scr {
 struct LaunchCounter {
   long long launches = 0;
   long long spmv_bytes = 0;
-  long long staged = 0;  // staged product launches
 };
 LaunchCounter& counters();
 
@@ -43,6 +42,13 @@ void from_slab_f(const int* rp, const float* slab_val, double* std_val, int nbr,
 void slab_to_float(const double* in, float* out, long long n, cudaStream_t s);
 // slab float -> slab BF16 (round to nearest even); out holds n __nv_bfloat16
 void slab_to_bf16(const float* in, void* out, long long n, cudaStream_t s);
+
+// Validation of caller index arrays before any kernel indexes with them:
+// sets *bad (device int, not cleared here) when a row pointer is out of
+// [0, nnzb] or decreasing, or a column index is out of [0, nbc), unsorted or
+// repeated within its row (solver.cu).
+void check_bsr_indices(int nbr, int nbc, const int* rp, const int* col, long long nnzb, int* bad,
+                       cudaStream_t s);
 
 // --------------------------------------------------------------- SpMV
 // Epilogues applied to the row sums acc of M x (scalar output index o,
@@ -96,22 +102,6 @@ void tune_load(const char* path);
 // and store the fastest in M.g; returns the chosen width
 template <typename VT>
 int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s);
-
-// Staged products (spmv_staged.cu): values and indices of tiles of whole
-// block rows are bulk-copied into shared memory several tiles ahead of the
-// lanes.  build_staged_plan computes M's tile plan (stages of stage_kb KiB,
-// `stages` in flight; left empty for small matrices, rows longer than a
-// stage or an unsupported shape); spmv_staged runs the product with G lanes
-// per scalar row and returns false when M has no plan.
-constexpr long long kStagedMinBlocks = 16384;
-bool staged_shape_supported(int br, int bc, int nrhs);
-template <typename VT>
-void build_staged_plan(DBsr<VT>& M, int nrhs, DeviceArena& a, cudaStream_t s, int stage_kb, int stages);
-template <typename VT, typename XT>
-bool spmv_staged(int G, const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const EpiArgs& e, cudaStream_t s);
-// status word of the staged products since the last call (0: none; 1: a
-// stage wait ran out; 2: a tile exceeded its stage), cleared on read
-int staged_status_take(cudaStream_t s);
 
 // Residual assembly of the VMS formulation on the GPU (residual.cu): the
 // mesh and the (element, vertex) lists of every row live on the device;
@@ -282,7 +272,8 @@ void prolong_rowscale(const double* diag, const double* lambda, double* rowscale
                       cudaStream_t s);
 
 struct Aggregation {
-  int* agg = nullptr;  // per block row, -1 = none
+  int* agg = nullptr;    // per block row, -1 = none
+  int* roots = nullptr;  // per aggregate: its root (the MIS-2 node that seeded it)
   int n_agg = 0;
 };
 // strength graph + MIS-2 aggregation of the block rows of A

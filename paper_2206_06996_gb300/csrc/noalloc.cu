@@ -2,14 +2,15 @@
 //
 // scr_bsr_spmv converts the caller's values into the solver's row layout in
 // a temporary buffer it allocates on every call.  Some callers cannot allow
-// that: code that records its launches into a CUDA graph (cudaMalloc and
-// cudaFree are not capturable, and cudaFree waits for the whole device),
-// hosts whose device memory belongs to another allocator (a framework's
-// caching allocator, a memory budget fixed at start-up), and latency-bound
-// loops that must not pay an allocation per call.  This entry point keeps
-// its scratch in one static device array instead: every GPU that loads the
-// library holds that array until the process exits, and the size of the
-// matrices it accepts is capped by it.
+// that: hosts whose device memory belongs to another allocator (a
+// framework's caching allocator, or a memory budget fixed at start-up, where
+// a library's own cudaMalloc can fail or push the owner out of memory), and
+// code that must not call cudaFree, which waits for the whole device.  This
+// entry point keeps its scratch in one static device array instead: every
+// GPU that loads the library holds that array until the process exits, and
+// the size of the matrices it accepts is capped by it.  Each call still
+// validates the caller's indices on the device, reads the result flag back
+// to the host and synchronises the stream twice.
 #include <cstring>
 #include <mutex>
 #include <stdexcept>
@@ -31,7 +32,9 @@ std::mutex g_noalloc_mutex;
 void* g_noalloc_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device, looked up once
-// per device (the name of a __device__ variable is only a host-side handle).
+// per device (the name of a __device__ variable is only a host-side handle)
+// and kept for the life of the process: a cudaDeviceReset would move the
+// array, so this entry point must not be used on a device after a reset.
 double* scratch_on_current_device() {
   int dev = 0;
   SCR_CUDA(cudaGetDevice(&dev));
@@ -44,21 +47,6 @@ double* scratch_on_current_device() {
     g_noalloc_ptr[dev] = p;
   }
   return static_cast<double*>(g_noalloc_ptr[dev]);
-}
-
-__global__ void k_noalloc_check(int nbr, int nbc, const int* __restrict__ rp, const int* __restrict__ col,
-                                long long nnzb, int* __restrict__ bad) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nbr) return;
-  const int s = rp[i], e = rp[i + 1];
-  if (s < 0 || e < s || e > nnzb) {
-    atomicExch(bad, 1);
-    return;
-  }
-  for (int t = s; t < e; ++t) {
-    const int c = col[t];
-    if (c < 0 || c >= nbc || (t > s && col[t - 1] >= c)) atomicExch(bad, 1);
-  }
 }
 
 }  // namespace
@@ -91,11 +79,7 @@ extern "C" int scr_bsr_spmv_noalloc(const scr_bsr* M, const double* x, double* y
     double* vals = scratch + kNoAllocHead;
     // the flag keeps the previous call's value: clear it first
     SCR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
-    if (M->nb_rows > 0) {
-      k_noalloc_check<<<ceil_div(M->nb_rows, 256), 256, 0, s>>>(M->nb_rows, M->nb_cols, M->row_ptr, M->col_idx,
-                                                               M->nnzb, bad);
-      SCR_LAUNCH();
-    }
+    check_bsr_indices(M->nb_rows, M->nb_cols, M->row_ptr, M->col_idx, M->nnzb, bad, s);
     int hb = 0;
     SCR_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
     SCR_CUDA(cudaStreamSynchronize(s));

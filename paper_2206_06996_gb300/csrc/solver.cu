@@ -79,6 +79,7 @@ struct Level {
   double *d0 = nullptr, *d1 = nullptr;
   float *d0f = nullptr, *d1f = nullptr;
   int* agg = nullptr;
+  int* roots = nullptr;  // root block row of each aggregate
   int n_agg = 0;
   long long n = 0;  // scalar rows
   double *b = nullptr, *x = nullptr, *r = nullptr, *t = nullptr;
@@ -120,11 +121,11 @@ static void add_bf16_copy(DBsr<float>& F, DeviceArena& a, cudaStream_t s) {
   F.hval = h;
 }
 
-// tile plan for the staged kernel (o.staged) and the timed choice of the
-// product kernel (o.autotune) for products of M with nrhs right-hand sides
+// the timed choice of the product kernel (o.autotune) for products of M
+// with nrhs right-hand sides
 template <typename VT>
 static void tune_product(DBsr<VT>& M, int nrhs, const scr_opts& o, DeviceArena& a, cudaStream_t s) {
-  if (o.staged && !M.tiles) build_staged_plan<VT>(M, nrhs, a, s, o.stage_kb, o.stages);
+  (void)a;
   if (o.autotune) autotune_spmv<VT>(M, nrhs, s);
 }
 
@@ -190,6 +191,7 @@ struct Hierarchy {
         const double t_agg = ms_since(t0);
         if (ag.n_agg > 0 && ag.n_agg < (int)(0.9 * Al.nbr)) {
           L.agg = ag.agg;
+          L.roots = ag.roots;
           L.n_agg = ag.n_agg;
           DBsr<double> Pt, T, AP, Ac;
           DeviceArena tmp2(s);
@@ -312,7 +314,7 @@ struct Hierarchy {
       cast_d2f(cinv, cinvf, (long long)nc * nc, s);
     }
     // lane-group widths of the products on the two finest levels
-    if (o.autotune || o.staged) {
+    if (o.autotune) {
       for (size_t l = 0; l < lv.size() && l < 2; ++l) {
         Level& L = lv[l];
         if (L.n < 4096) continue;
@@ -810,6 +812,7 @@ __global__ void k_check_cols(int nbr, int nbc, const int* __restrict__ rp, const
   }
 }
 
+
 // copy a caller matrix to the device in slab layout (FP64)
 DBsr<double> upload(const scr_bsr* M, int dev_ptr, DeviceArena& a, cudaStream_t s) {
   DBsr<double> D;
@@ -862,28 +865,11 @@ DBsr<float> float_copy(const DBsr<double>& M, DeviceArena& a, cudaStream_t s) {
   return F;
 }
 
-// a bounded device-side wait that ran out (the kernel returned early and
-// its outputs are incomplete)
-struct DeviceTimeout : std::runtime_error {
-  using std::runtime_error::runtime_error;
-};
-
-// status word of the staged products launched on the handle's stream
-static void check_staged(scr_handle h) {
-  if (!h->o.staged) return;
-  const int st = staged_status_take(h->s);
-  if (st == 1) throw DeviceTimeout("a staged product's shared-memory stage did not arrive within its wait limit");
-  if (st == 2) throw std::runtime_error("staged product: a tile exceeded its stage (inconsistent tile plan)");
-}
-
 template <typename F>
 int guarded(F&& f) {
   try {
     f();
     return SCR_OK;
-  } catch (const DeviceTimeout& e) {
-    set_last_error("%s", e.what());
-    return SCR_DEVICE_TIMEOUT;
   } catch (const CudaError& e) {
     set_last_error("CUDA error %s in %s", cudaGetErrorString(e.err), e.where ? e.where : "?");
     cudaGetLastError();
@@ -1095,9 +1081,6 @@ int scr_default_opts(scr_opts* o) {
   o->amg_smoother = SCR_SMOOTH_CHEB;
   o->amg_degree = 3;
   o->sell = 0;
-  o->staged = 0;
-  o->stage_kb = 16;
-  o->stages = 2;
   o->l2_prefetch = 192;
   o->amg_coarse_bf16 = 1;
   o->cuda_graphs = 1;
@@ -1126,8 +1109,6 @@ int scr_create(scr_handle* out, const scr_opts* o, void* stream) {
     if (op.amg_smoother != SCR_SMOOTH_L1 && op.amg_smoother != SCR_SMOOTH_CHEB)
       throw std::invalid_argument("unknown smoother");
     if (op.amg_degree < 1 || op.amg_degree > 16) throw std::invalid_argument("Chebyshev degree must lie in [1, 16]");
-    if (op.staged && (op.stage_kb < 4 || op.stage_kb > 96 || op.stages < 2 || op.stages > 4))
-      throw std::invalid_argument("staged products: stage_kb must lie in [4, 96] and stages in [2, 4]");
     if (op.l2_prefetch < 0) throw std::invalid_argument("l2_prefetch must be >= 0");
     if (op.nrhs != 1 && op.nrhs != kSpmmCols) throw std::invalid_argument("nrhs must be 1 or 8");
     if (op.amg_coarse_bf16 != 0 && op.amg_coarse_bf16 != 1) throw std::invalid_argument("amg_coarse_bf16 must be 0 or 1");
@@ -1356,7 +1337,6 @@ int scr_solve(scr_handle h, const double* b, double* x, int dev) {
     status = solve_impl(h, bd, xd, h->o.rtol);
     if (!dev) SCR_CUDA(cudaMemcpyAsync(x, xd, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
     SCR_CUDA(cudaStreamSynchronize(h->s));
-    check_staged(h);
     h->stats.solve_ms = ms_since(t0);
   });
   if (rc != SCR_OK) return rc;
@@ -1422,7 +1402,6 @@ int scr_solve_multi(scr_handle h, const double* const* b, double* const* x, int 
     if (k > 1) interleave(h->xvec, xs, n, k, false, s);
     for (int c = 0; c < k; ++c) SCR_CUDA(cudaMemcpyAsync(x[c], xs + c * n, sizeof(double) * n, kout, s));
     SCR_CUDA(cudaStreamSynchronize(s));
-    check_staged(h);
     h->stats.rel_res = worst;
     status = worst <= h->o.rtol ? SCR_OK : SCR_NOT_CONVERGED;
     h->stats.solve_ms = ms_since(t0);
@@ -1622,7 +1601,6 @@ int scr_solve_batch(scr_handle h, const double* const* b, double* const* x, int 
         SCR_CUDA(cudaMemcpyAsync(x[i] + v3, h->xvec + NV3 + h->b_po[i], sizeof(double) * h->b_np[i], kout, h->s));
     }
     SCR_CUDA(cudaStreamSynchronize(h->s));
-    check_staged(h);
     h->stats.solve_ms = ms_since(t0);
   });
   if (rc != SCR_OK) return rc;
@@ -1654,7 +1632,6 @@ int scr_get_stats(scr_handle h, scr_stats* st) {
   *st = h->stats;
   st->kernel_launches = counters().launches;
   st->spmv_bytes = counters().spmv_bytes;
-  st->staged_launches = counters().staged;
   st->levels_M = h->hM.n_levels();
   return SCR_OK;
 }
@@ -1709,7 +1686,14 @@ int mm_setup(scr_handle h, const scr_bsr* L, int dev) {
   });
 }
 
-// CG + AMG (Sec. 5.2.2) on (L kron I3) u = g, FP64
+static double mesh_true_rel(scr_ctx* h, const double* g, const double* u);
+
+// CG + AMG (Sec. 5.2.2) on (L kron I3) u = g, FP64.  The loop stops on the
+// recursive residual r_k; before it reports convergence the true residual
+// g - L u is recomputed, and where rounding has let the two drift apart the
+// iteration restarts from the true residual (r = g - L u, z = M r, p = z) and
+// goes on until the true residual meets mm_rtol or the iteration cap is hit.
+// *rel is then the true relative residual.
 static bool mesh_cg(scr_ctx* h, const double* g, double* u, int* iters, double* rel) {
   cudaStream_t s = h->s;
   const long long n = 3LL * h->nm;
@@ -1737,7 +1721,17 @@ static bool mesh_cg(scr_ctx* h, const double* g, double* u, int* iters, double* 
     *iters = it;
     *rel = hr[0];
     if (!std::isfinite(*rel)) return false;
-    if (*rel <= h->o.mm_rtol) return true;
+    if (*rel <= h->o.mm_rtol) {
+      // confirm on the true residual (left in h->mq by mesh_true_rel)
+      *rel = mesh_true_rel(h, g, u);
+      if (*rel <= h->o.mm_rtol) return true;
+      if (!std::isfinite(*rel)) return false;
+      copy<double>(h->mq, h->mr, n, s);
+      h->hM.apply<double>(h->mr, h->mz, s);
+      cg_dot_rz(h->cg, h->mr, h->mz, n, h->mred, 1, s);
+      copy<double>(h->mz, h->mp, n, s);
+      continue;
+    }
     h->hM.apply<double>(h->mr, h->mz, s);
     cg_dot_rz(h->cg, h->mr, h->mz, n, h->mred, 0, s);
     cg_update_p(h->cg, h->mz, h->mp, n, s);
@@ -1785,7 +1779,6 @@ int mm_solve(scr_handle h, const double* g, double* u, int dev) {
     h->stats.vcycles_M = h->hM.vcycles;
     if (!dev) SCR_CUDA(cudaMemcpyAsync(u, ud, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
     SCR_CUDA(cudaStreamSynchronize(h->s));
-    check_staged(h);
     h->stats.mm_solve_ms = ms_since(t0);
   });
   if (rc != SCR_OK) return rc;
@@ -1813,7 +1806,6 @@ int scr_apply_op(scr_handle h, const double* x, double* y) {
   return guarded([&] {
     apply_calA(h, x, y, nullptr, false);
     SCR_CUDA(cudaStreamSynchronize(h->s));
-    check_staged(h);
   });
 }
 
@@ -1827,7 +1819,6 @@ int scr_apply_pc(scr_handle h, const double* r, double* y) {
     reset_solve_stats(h);
     apply_pc_any(h, r, y);
     SCR_CUDA(cudaStreamSynchronize(h->s));
-    check_staged(h);
   });
 }
 
@@ -1849,7 +1840,6 @@ int scr_apply_schur(scr_handle h, const double* xp, double* yp) {
       apply_S<double>(h, v, xp, yp);
     }
     SCR_CUDA(cudaStreamSynchronize(h->s));
-    check_staged(h);
   });
 }
 
@@ -1886,7 +1876,6 @@ int scr_amg_apply(scr_handle h, int which, const double* b, double* x) {
       H->apply<double>(b, x, h->s);
     }
     SCR_CUDA(cudaStreamSynchronize(h->s));
-    check_staged(h);
   });
 }
 
@@ -1913,6 +1902,16 @@ int scr_export(scr_handle h, int which, int level, int kind, scr_bsr_out* out) {
       out->nnzb = L.agg ? L.A.nbr : 0;
       if (out->col_idx && L.agg)
         SCR_CUDA(cudaMemcpyAsync(out->col_idx, L.agg, sizeof(int) * L.A.nbr, cudaMemcpyDeviceToHost, h->s));
+      SCR_CUDA(cudaStreamSynchronize(h->s));
+      return;
+    }
+    if (kind == SCR_EXPORT_ROOTS) {
+      out->nb_rows = L.agg ? L.n_agg : 0;
+      out->nb_cols = L.A.nbr;
+      out->br = out->bc = 1;
+      out->nnzb = L.agg ? L.n_agg : 0;
+      if (out->col_idx && L.agg && L.n_agg)
+        SCR_CUDA(cudaMemcpyAsync(out->col_idx, L.roots, sizeof(int) * L.n_agg, cudaMemcpyDeviceToHost, h->s));
       SCR_CUDA(cudaStreamSynchronize(h->s));
       return;
     }
@@ -2109,7 +2108,6 @@ int corrector_run(scr_handle h, double* v, double* p, double* vdot, double* u, i
       SCR_CUDA(cudaMemcpyAsync(ale->uhat, h->d_uh, sizeof(double) * nf3,
                                dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     SCR_CUDA(cudaStreamSynchronize(s));
-    check_staged(h);
   });
   if (rc != SCR_OK) return rc;
   if (mesh_fail_it)
@@ -2301,3 +2299,11 @@ int scr_bsr_spmv(const scr_bsr* M, const double* x, double* y, void* stream) {
 }
 
 }  // extern "C"
+
+namespace scr {
+void check_bsr_indices(int nbr, int nbc, const int* rp, const int* col, long long nnzb, int* bad, cudaStream_t s) {
+  if (nbr <= 0) return;
+  k_check_cols<<<ceil_div(nbr, 256), 256, 0, s>>>(nbr, nbc, rp, col, nnzb, bad);
+  SCR_LAUNCH();
+}
+}  // namespace scr

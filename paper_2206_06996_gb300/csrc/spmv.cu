@@ -189,8 +189,7 @@ static void product(int G, const DBsr<VT>& M, const XT* x, XT* y, int nrhs, cons
       return;
     }
   }
-  if (!(code_of(M) >= 200 && !M.sell && spmv_staged<VT, XT>(G, M, x, y, nrhs, e, s)))
-    spmv_launch<VT, XT>(G, M, x, y, nrhs, e, s);
+  spmv_launch<VT, XT>(G, M, x, y, nrhs, e, s);
 }
 
 template <typename VT, typename XT>
@@ -258,17 +257,11 @@ int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s) {
   cudaEvent_t e0, e1;
   SCR_CUDA(cudaEventCreate(&e0));
   SCR_CUDA(cudaEventCreate(&e1));
-  // the scalar-row kernel with 1, 2, 4 or 8 lanes and, when M has a tile
-  // plan, the staged kernel with 2, 4 or 8 (the block-row and sliced-ELL
-  // variants measured slower on the tube operators)
+  // the scalar-row kernel with 1, 2, 4 or 8 lanes (the block-row and
+  // sliced-ELL variants measured slower on the tube operators)
   int cands[9] = {101, 102, 104, 108};
   int ncand = 4;
   if (M.nbr && (double)M.nnzb * M.bc / M.nbr >= 64) cands[ncand++] = 116;  // long rows
-  if (M.tiles && staged_shape_supported(M.br, M.bc, nrhs)) {
-    cands[ncand++] = 202;
-    cands[ncand++] = 204;
-    cands[ncand++] = 208;
-  }
   float best = 1e30f;
   int bestg = M.g;
   const int saved = M.g;
@@ -312,7 +305,7 @@ int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s) {
 }
 // text form of the cache: "nnzb nbr nbc br bc value_bytes nrhs code" per line
 static bool valid_code(int c) {
-  return (c >= 1 && c <= 16) || (c >= 101 && c <= 116) || c == 201 || c == 202 || c == 204 || c == 208;
+  return (c >= 1 && c <= 16) || (c >= 101 && c <= 116);
 }
 
 void tune_save(const char* path) {

@@ -278,10 +278,8 @@ inline void launch_spmv_e(const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& 
 
 // lanes per scalar row: FP64 keeps groups narrow (FP64 adds of the
 // reduction compete with the products), FP32 widens them for coalescing
-// M.g: lanes per block row (1..16, block-row kernel for BR > 1), 100 +
-// lanes per scalar row (scalar-row kernel) or 200 + lanes per scalar row
-// (staged kernel, spmv_staged.cu, when M has a tile plan); 0 selects by row
-// length
+// M.g: lanes per block row (1..16, block-row kernel for BR > 1) or 100 +
+// lanes per scalar row (scalar-row kernel); 0 selects by row length
 extern int g_forced;
 
 template <typename VT>
@@ -292,7 +290,6 @@ inline int code_of(const DBsr<VT>& M) {
 template <typename VT>
 inline int pick_group(const DBsr<VT>& M) {
   const int g = code_of(M);
-  if (g >= 200) return g - 200;
   if (g > 0) return g >= 100 ? g - 100 : g;
   // measured on the 616k-node tube: FP64 3x3 rows are fastest with 2 lanes
   // per scalar row (the FP64 pipe binds), FP32 with 4 (coalescing binds)

@@ -404,12 +404,12 @@ class BlockSolver:
         return n.value
 
     def export(self, which: int, level: int, kind: int):
-        """Copy a hierarchy operator / prolongator (block CSR, numpy) or the
-        aggregates (int array) to the host."""
-        from .abi import SCR_EXPORT_AGGREGATES
+        """Copy a hierarchy operator / prolongator (block CSR, numpy), the
+        aggregates or the aggregates' roots (int arrays) to the host."""
+        from .abi import SCR_EXPORT_AGGREGATES, SCR_EXPORT_ROOTS
         o = BsrOut()
         check(self.lib.scr_export(self.h, which, level, kind, C.byref(o)))
-        if kind == SCR_EXPORT_AGGREGATES:
+        if kind in (SCR_EXPORT_AGGREGATES, SCR_EXPORT_ROOTS):
             agg = np.empty(max(o.nb_rows, 1), dtype=np.int32)
             o2 = BsrOut()
             o2.col_idx = agg.ctypes.data

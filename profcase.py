@@ -1,6 +1,6 @@
 """Small, bounded cases for profiling single kernels of the path.
 
-    python -m paper_2206_06996_gb300.profcase --precision fp64 --n-ax 100 --reps 2
+    python profcase.py --precision fp64 --n-ax 100 --reps 2
 
 builds the 96 x (11 + 5) tube with `--n-ax` axial layers (100 layers:
 154,337 nodes, A about 170 MB in FP64, larger than L2), sets up the solver
@@ -17,7 +17,7 @@ import argparse
 import os
 import sys
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
