@@ -103,10 +103,16 @@ typedef struct {
   int amg_smoother;   /* 0: l1-Jacobi (amg_nu sweeps); 1: Chebyshev on D^{-1}A (default) */
   int amg_degree;     /* Chebyshev degree, 3 */
   int spmv_group;     /* 0: autotune/heuristic; 1..16: lanes per block row; 101..116: 100 + lanes per
-                         scalar row (forces the product kernel of every matrix) */
+                         scalar row; 301..316: 300 + lanes per block row of the 16-byte kernels on
+                         the padded copy (matrices without one use the scalar-row kernel with
+                         that many lanes) (forces the product kernel of every matrix) */
   int sell;           /* 0: slab products; W > 0: products with A, Shat and L use a sliced block-ELL
                          copy with rows sorted by length inside windows of W block rows
                          (W a multiple of 32, at most 1024); default 0 */
+  int vec;            /* 1 (default): A and Shat (and their FP32 copies) also keep a padded copy in
+                         which every block row's column indices and scalar rows start on 16-byte
+                         boundaries (zero padding), and the autotuner also times the kernels that
+                         read it with 16-byte vector loads; 0: slab products only */
   int l2_prefetch;    /* scalar-row products: each CTA prefetches into L2 the values and indices of
                          the CTA this many indices ahead (bulk L2 prefetch); 0 off; default 192 */
   int amg_coarse_bf16;/* mixed form only: 1 (default) stores the values of the coarse AMG levels
@@ -386,7 +392,8 @@ int scr_profile_end(scr_handle h, scr_kprof* out);
 
 /* The autotuner's kernel choices (scr_opts.autotune) live in a process-wide
    cache keyed by block shape, block rows and columns, stored blocks, value
-   precision and right-hand sides.  scr_tune_save writes every cached
+   precision (plus whether the matrix has the padded 16-byte copy of the
+   vec option) and right-hand sides.  scr_tune_save writes every cached
    decision to a text file, one per line; scr_tune_load adds the decisions of
    such a file to the cache for the current device, so later set-ups of
    matrices with those keys skip the timing and use the stored kernels.  Use:

@@ -42,6 +42,19 @@ struct DBsr {
   T* val = nullptr;
   int g = 0;                  // product kernel code (0: heuristic; see spmv.cu)
   const void* sell = nullptr; // host pointer to a DSell<T> copy used for products (optional)
+  // padded ("vector") copy for 16-byte loads (optional, built by build_vec):
+  // 3x3 blocks: vdesc holds one int4 per block row {column start, k, value
+  //   start, scalar-row length}; the row's k column indices sit at
+  //   vcol[column start ...], padded to a multiple of V = 16 / sizeof(T)
+  //   entries; its three scalar rows follow one another from value start,
+  //   each rl values long (k * 3 values, zero-padded to a multiple of V);
+  // 1x1 blocks: vdesc holds one int2 per row {start, k}; values and column
+  //   indices share the start, each row padded to a multiple of V entries.
+  // Every start is a multiple of V, so each lane's chunk of V blocks (3x3)
+  // or V entries (1x1) loads with 16-byte vector loads.
+  const void* vdesc = nullptr;
+  const int* vcol = nullptr;
+  const T* vval = nullptr;
   // BF16 copy of val (same slab layout): when set, FP32 products read these
   // values instead (coarse AMG levels of the mixed-precision form)
   const void* hval = nullptr;

@@ -89,8 +89,15 @@ void spmm_launch(int G, const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& e,
 template <typename VT>
 void build_sell(const DBsr<double>& M, DSell<VT>& S, DeviceArena& a, cudaStream_t s, int window);
 
+// padded copy of M for 16-byte loads (see DBsr::vdesc), for 3x3 and 1x1
+// blocks; sets M.vdesc / vcol / vval (arrays in a).  Leaves M unchanged for
+// other shapes or when a padded array would exceed int32 indexing.
+template <typename VT>
+void build_vec(DBsr<VT>& M, DeviceArena& a, cudaStream_t s);
+
 // forced kernel code for every product (0: per-matrix choice)
 void set_forced_group(int code);
+int forced_group();
 // CTAs ahead for the L2 prefetch of the scalar-row products (0: off)
 void set_l2_prefetch(int ctas);
 // print every autotune decision to stderr (0: quiet)

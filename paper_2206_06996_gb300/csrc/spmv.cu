@@ -143,6 +143,84 @@ void slab_to_float(const double* in, float* out, long long n, cudaStream_t s) {
   counters().launches++;
 }
 
+// ------------------------------------------------------------ padded copy
+// sizes of the padded copy per block row: column slots (k rounded up to a
+// multiple of V) and values (br scalar rows of bc k values each, rounded up
+// to a multiple of V)
+__global__ void k_vec_sizes(int nbr, const int* __restrict__ rp, int br, int bc, int V, int* __restrict__ csz,
+                            int* __restrict__ vsz) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbr) return;
+  const int k = rp[i + 1] - rp[i];
+  csz[i] = (k + V - 1) / V * V;
+  vsz[i] = br * ((bc * k + V - 1) / V * V);
+}
+
+// one warp per block row: column slots (padding repeats the row's last
+// column, or 0 in an empty row) and the padded scalar rows (zeros past bc k)
+template <typename T>
+__global__ void k_vec_fill(int nbr, const int* __restrict__ rp, const int* __restrict__ col,
+                           const T* __restrict__ slab, int br, int bc, int V, const int* __restrict__ cs,
+                           const int* __restrict__ vs, void* __restrict__ desc, int* __restrict__ vcol,
+                           T* __restrict__ vval) {
+  const int i = blockIdx.x * blockDim.y + threadIdx.y;
+  if (i >= nbr) return;
+  const int s = rp[i], k = rp[i + 1] - s;
+  const int c0 = cs[i], cn = cs[i + 1] - c0;
+  const int v0 = vs[i], rl = (vs[i + 1] - v0) / br;
+  if (threadIdx.x == 0) {
+    if (br == 3) static_cast<int4*>(desc)[i] = make_int4(c0, k, v0, rl);
+    else static_cast<int2*>(desc)[i] = make_int2(c0, k);
+  }
+  const int last = k > 0 ? col[s + k - 1] : 0;
+  for (int t = threadIdx.x; t < cn; t += blockDim.x) vcol[c0 + t] = t < k ? col[s + t] : last;
+  const long long src = (long long)s * br * bc;
+  for (int q = threadIdx.x; q < br * rl; q += blockDim.x) {
+    const int r = q / rl, e = q - r * rl;
+    vval[v0 + q] = e < bc * k ? slab[src + (long long)r * k * bc + e] : (T)0;
+  }
+}
+
+template <typename VT>
+void build_vec(DBsr<VT>& M, DeviceArena& a, cudaStream_t s) {
+  const bool sq3 = M.br == 3 && M.bc == 3, sq1 = M.br == 1 && M.bc == 1;
+  if (M.nbr == 0 || !(sq3 || sq1)) return;
+  constexpr int V = 16 / (int)sizeof(VT);
+  DeviceArena tmp(s);
+  int* csz = tmp.alloc<int>(M.nbr + 1);
+  int* vsz = tmp.alloc<int>(M.nbr + 1);
+  int* cs = a.alloc<int>(M.nbr + 1);
+  int* vs = tmp.alloc<int>(M.nbr + 1);
+  k_vec_sizes<<<ceil_div(M.nbr, 256), 256, 0, s>>>(M.nbr, M.rp, M.br, M.bc, V, csz, vsz);
+  SCR_LAUNCH();
+  long long nc = 0, nv = 0;
+  try {
+    nc = exclusive_scan(csz, cs, M.nbr, tmp, s);
+    nv = exclusive_scan(vsz, vs, M.nbr, tmp, s);
+  } catch (const CudaError&) {
+    return;  // padded arrays beyond int32 indexing: keep the slab kernels
+  }
+  void* desc = sq3 ? static_cast<void*>(a.alloc<int4>(M.nbr)) : static_cast<void*>(a.alloc<int2>(M.nbr));
+  // 16 entries of slack: a lane's last vector never leaves the allocation
+  int* vcol = a.alloc<int>(nc + 16);
+  VT* vval = sq1 ? nullptr : a.alloc<VT>(nv + 16);
+  if (sq1) {
+    // 1x1: values share the column slots' starts (both padded to V entries)
+    vval = a.alloc<VT>(nc + 16);
+  }
+  dim3 blk(32, 8);
+  k_vec_fill<VT><<<ceil_div(M.nbr, 8), blk, 0, s>>>(M.nbr, M.rp, M.col, M.val, M.br, M.bc, V, cs, sq1 ? cs : vs,
+                                                    desc, vcol, vval);
+  SCR_LAUNCH();
+  counters().launches += 2;
+  M.vdesc = desc;
+  M.vcol = vcol;
+  M.vval = vval;
+  (void)nv;
+}
+template void build_vec<double>(DBsr<double>&, DeviceArena&, cudaStream_t);
+template void build_vec<float>(DBsr<float>&, DeviceArena&, cudaStream_t);
+
 // ------------------------------------------------------------ SpMV
 // CTAs ahead for the L2 prefetch of the scalar-row kernel (0: off); set
 // from the options at scr_create.  Measured on the 616k-node tube: 128 to
@@ -156,6 +234,7 @@ void set_tune_verbose(int v) { g_tune_verbose = v; }
 // forced kernel code for every product (options.spmv_group)
 int g_forced = 0;
 void set_forced_group(int code) { g_forced = code; }
+int forced_group() { return g_forced; }
 
 template <typename VT, typename XT>
 static void spmv_launch(int G, const DBsr<VT>& M, const XT* x, XT* y, int nrhs, const EpiArgs& e, cudaStream_t s) {
@@ -239,7 +318,8 @@ int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s) {
   if (M.nbr == 0 || M.sell) return M.g;
   int dev = 0;
   cudaGetDevice(&dev);
-  const TuneKey key{M.nnzb, M.nbr, M.nbc, M.br, M.bc, (int)sizeof(VT), nrhs, dev};
+  // value bytes, plus 100 when M has the padded 16-byte copy (its candidates differ)
+  const TuneKey key{M.nnzb, M.nbr, M.nbc, M.br, M.bc, (int)sizeof(VT) + (M.vdesc ? 100 : 0), nrhs, dev};
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = tune_cache().find(key);
@@ -254,23 +334,46 @@ int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s) {
   SCR_CUDA(cudaMallocAsync(&x, nx * sizeof(XT), s));
   SCR_CUDA(cudaMallocAsync(&y, ny * sizeof(XT), s));
   SCR_CUDA(cudaMemsetAsync(x, 0, nx * sizeof(XT), s));
+  // square operators are timed with the epilogue they mostly run in a solve
+  // (the Chebyshev step of the V-cycle: three more vectors read, three
+  // written), the others with the plain product
+  EpiArgs ep;
+  XT* ev = nullptr;
+  if (M.br == M.bc && M.nbr == M.nbc) {
+    SCR_CUDA(cudaMallocAsync(&ev, 3 * ny * sizeof(XT), s));
+    SCR_CUDA(cudaMemsetAsync(ev, 0, 3 * ny * sizeof(XT), s));
+    ep.kind = Epi::ChebStep;
+    ep.alpha = 0.5;
+    ep.beta = 0.5;
+    ep.dinv = ev;
+    ep.r = ev + ny;
+    ep.xsol = ev + 2 * ny;
+    ep.dout = y;
+  }
   cudaEvent_t e0, e1;
   SCR_CUDA(cudaEventCreate(&e0));
   SCR_CUDA(cudaEventCreate(&e1));
   // the scalar-row kernel with 1, 2, 4 or 8 lanes (the block-row and
   // sliced-ELL variants measured slower on the tube operators)
-  int cands[9] = {101, 102, 104, 108};
+  int cands[12] = {101, 102, 104, 108};
   int ncand = 4;
   if (M.nbr && (double)M.nnzb * M.bc / M.nbr >= 64) cands[ncand++] = 116;  // long rows
+  // the 16-byte kernels on the padded copy (one right-hand side)
+  if (M.vdesc && nrhs == 1) {
+    cands[ncand++] = 302;
+    cands[ncand++] = 304;
+    cands[ncand++] = 308;
+    if (M.br == 1) cands[ncand++] = 316;
+  }
   float best = 1e30f;
   int bestg = M.g;
   const int saved = M.g;
-  float times[9] = {};
+  float times[12] = {};
   for (int q = 0; q < ncand; ++q) {
     const int code = cands[q];
     M.g = code;
     const int G = pick_group(M);
-    auto run = [&] { product<VT, XT>(G, M, x, y, nrhs, EpiArgs(), s); };
+    auto run = [&] { product<VT, XT>(G, M, x, y, nrhs, ep, s); };
     run();  // warm-up
     SCR_CUDA(cudaEventRecord(e0, s));
     for (int r = 0; r < 5; ++r) run();
@@ -290,6 +393,7 @@ int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s) {
   cudaEventDestroy(e1);
   SCR_CUDA(cudaFreeAsync(x, s));
   SCR_CUDA(cudaFreeAsync(y, s));
+  if (ev) SCR_CUDA(cudaFreeAsync(ev, s));
   M.g = bestg;
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -304,8 +408,9 @@ int autotune_spmv(DBsr<VT>& M, int nrhs, cudaStream_t s) {
   return bestg;
 }
 // text form of the cache: "nnzb nbr nbc br bc value_bytes nrhs code" per line
+// (value_bytes + 100 for matrices with the padded 16-byte copy)
 static bool valid_code(int c) {
-  return (c >= 1 && c <= 16) || (c >= 101 && c <= 116);
+  return (c >= 1 && c <= 16) || (c >= 101 && c <= 116) || (c >= 301 && c <= 316);
 }
 
 void tune_save(const char* path) {

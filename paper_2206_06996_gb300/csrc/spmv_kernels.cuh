@@ -180,6 +180,186 @@ __global__ void __launch_bounds__(256) k_spmv_brow(int nbr, const int* __restric
   }
 }
 
+// ------------------------------------------------------------ 16-byte products
+// Products on the padded copy of DBsr::vdesc.  Each lane takes a chunk of V
+// = 16 / sizeof(VT) blocks (3x3) or entries (1x1) at a time and loads it
+// with 16-byte vector loads: for a 3x3 chunk one index vector (V column
+// indices) and three value vectors per scalar row, against V column loads
+// and 3 V value loads per scalar row in the scalar-row kernel.
+// The stored values and indices are read once per product: their loads go
+// through the read-only path without allocating in L1 (which then keeps the
+// source-vector gathers) and ask L2 for 256-byte fills.
+template <typename VT>
+__device__ __forceinline__ void ldg16(const VT* p, VT* a) {
+  if constexpr (sizeof(VT) == 4) {
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    a[0] = v.x, a[1] = v.y, a[2] = v.z, a[3] = v.w;
+  } else {
+    double2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+    a[0] = v.x, a[1] = v.y;
+  }
+}
+template <int U>
+__device__ __forceinline__ void ldg_idx(const int* p, int* c) {
+  if constexpr (U == 4) {
+    int4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.s32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    c[0] = v.x, c[1] = v.y, c[2] = v.z, c[3] = v.w;
+  } else {
+    int2 v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v2.s32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    c[0] = v.x, c[1] = v.y;
+  }
+}
+
+// L2 prefetch (cp.async.bulk.prefetch.L2) of the padded values and column
+// slots of the block rows [i0, i1) of a padded copy (3x3: int4 descriptors;
+// 1x1: int2, values and slots sharing their starts).  Whole 16-byte lines
+// inside the allocations only.
+template <typename VT, bool SQ3>
+__device__ __forceinline__ void l2_prefetch_vec(const void* desc, const int* col, const VT* val, long long i0,
+                                                long long i1) {
+  long long c0, c1, v0, v1;
+  if constexpr (SQ3) {
+    const int4 a = __ldg(static_cast<const int4*>(desc) + i0), b = __ldg(static_cast<const int4*>(desc) + i1 - 1);
+    constexpr int V = 16 / (int)sizeof(VT);
+    c0 = a.x, c1 = b.x + (b.y + V - 1) / V * V;
+    v0 = a.z, v1 = b.z + 3LL * b.w;
+  } else {
+    constexpr int V = 16 / (int)sizeof(VT);
+    const int2 a = __ldg(static_cast<const int2*>(desc) + i0), b = __ldg(static_cast<const int2*>(desc) + i1 - 1);
+    c0 = v0 = a.x;
+    c1 = v1 = b.x + (b.y + V - 1) / V * V;
+  }
+  // runs start on 16-byte boundaries except FP64 column slots (8 bytes): round
+  // down the start and up the end (the arrays carry 16 entries of slack)
+  const unsigned long long vb = __cvta_generic_to_global(val + v0) & ~15ULL;
+  const unsigned long long ve = (__cvta_generic_to_global(val + v1) + 15) & ~15ULL;
+  const unsigned long long cb = __cvta_generic_to_global(col + c0) & ~15ULL;
+  const unsigned long long ce = (__cvta_generic_to_global(col + c1) + 15) & ~15ULL;
+  if (ve > vb)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(vb), "r"((unsigned)(ve - vb)) : "memory");
+  if (ce > cb)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(cb), "r"((unsigned)(ce - cb)) : "memory");
+}
+
+// 3x3 blocks, one right-hand side: G lanes per block row, each lane takes
+// chunks of U = V blocks (3 U values per scalar row, i.e. three 16-byte
+// loads) in turn and accumulates all three scalar rows, so a block's column
+// index and its three source values are loaded once for its 9 multiply-adds.
+// The three row sums are combined over the G lanes and written by lanes 0,
+// 1, 2 (mod G).
+template <int G, typename VT, typename XT, Epi E>
+__global__ void __launch_bounds__(256) k_spmv_vec33(int nbr, const int4* __restrict__ desc, const int* __restrict__ col,
+                                                    const VT* __restrict__ val, const XT* __restrict__ x,
+                                                    Epilogue<XT, E> epi, int pf) {
+  constexpr int V = 16 / (int)sizeof(VT);
+  constexpr int U = V;
+  const long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;
+  const int lane = threadIdx.x % G;
+  if (pf > 0 && threadIdx.x == 0) {
+    const long long i0 = (blockIdx.x + (long long)pf) * (256 / G);
+    if (i0 < nbr) l2_prefetch_vec<VT, true>(desc, col, val, i0, i0 + 256 / G < nbr ? i0 + 256 / G : nbr);
+  }
+  const bool active = i < nbr;  // inactive lanes still join the shuffles
+  XT acc[3] = {(XT)0, (XT)0, (XT)0};
+  if (active) {
+    const int4 d = __ldg(desc + i);
+    const int k = d.y, rl = d.w;
+    const int* __restrict__ cr = col + d.x;
+    const VT* __restrict__ v0 = val + d.z;
+    for (int j = lane * U; j < k; j += G * U) {
+      const int m = k - j < U ? k - j : U;  // blocks of this chunk
+      int c[U];
+      ldg_idx<U>(cr + j, c);
+      VT a[3][3 * U];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          if (q * V < 3 * m) {
+            ldg16<VT>(v0 + (long long)r * rl + 3 * j + q * V, &a[r][q * V]);
+          } else {
+#pragma unroll
+            for (int e = 0; e < V; ++e) a[r][q * V + e] = (VT)0;
+          }
+        }
+      XT xv[U][3];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const long long xb = 3LL * (u < m ? c[u] : 0);
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) xv[u][cc] = u < m ? (XT)__ldg(x + xb + cc) : (XT)0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc)
+#pragma unroll
+          for (int r = 0; r < 3; ++r)
+            if (u < m) acc[r] = fma((XT)a[r][3 * u + cc], xv[u][cc], acc[r]);
+    }
+  }
+  if constexpr (G > 1) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int off = G / 2; off > 0; off >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], off, G);
+  }
+  if (active) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      if (r % G == lane) epi(3 * i + r, 3 * i + r, acc[r]);
+  }
+}
+
+// 1x1 blocks, one right-hand side: G lanes per row, chunks of V entries
+// (one 16-byte value load and one index load of V column indices).
+template <int G, typename VT, typename XT, Epi E>
+__global__ void __launch_bounds__(256) k_spmv_vec11(int nbr, const int2* __restrict__ desc, const int* __restrict__ col,
+                                                    const VT* __restrict__ val, const XT* __restrict__ x,
+                                                    Epilogue<XT, E> epi, int pf) {
+  constexpr int V = 16 / (int)sizeof(VT);
+  const long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;
+  const int lane = threadIdx.x % G;
+  if (pf > 0 && threadIdx.x == 0) {
+    const long long i0 = (blockIdx.x + (long long)pf) * (256 / G);
+    if (i0 < nbr) l2_prefetch_vec<VT, false>(desc, col, val, i0, i0 + 256 / G < nbr ? i0 + 256 / G : nbr);
+  }
+  const bool active = i < nbr;
+  XT acc = (XT)0;
+  if (active) {
+    const int2 d = __ldg(desc + i);
+    const int k = d.y;
+    const int* __restrict__ cr = col + d.x;
+    const VT* __restrict__ vr = val + d.x;
+    for (int j = lane * V; j < k; j += G * V) {
+      const int m = k - j < V ? k - j : V;
+      int c[V];
+      VT a[V];
+      ldg_idx<V>(cr + j, c);
+      ldg16<VT>(vr + j, a);
+      XT xv[V];
+#pragma unroll
+      for (int u = 0; u < V; ++u) xv[u] = u < m ? (XT)__ldg(x + c[u]) : (XT)0;
+#pragma unroll
+      for (int u = 0; u < V; ++u)
+        if (u < m) acc = fma((XT)a[u], xv[u], acc);
+    }
+  }
+  if constexpr (G > 1) {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off, G);
+  }
+  if (active && lane == 0) epi(i, i, acc);
+}
+
 // sliced block-ELL product: one lane per block row, no cross-lane sums
 template <int BR, int BC, int NRHS, typename VT, typename XT, Epi E>
 __global__ void __launch_bounds__(256) k_sell_spmv(DSell<VT> S, const XT* __restrict__ x, Epilogue<XT, E> epi) {
@@ -234,8 +414,23 @@ inline void launch_spmv_g(const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& 
   const Epilogue<XT, E> epi = make_epilogue<XT, E>(x, y, e);
   const int blk = 256;
   bool done = false;
+  if constexpr (sizeof(VT) >= 4 && NRHS == 1 && ((BR == 3 && BC == 3) || (BR == 1 && BC == 1))) {
+    if (M.vdesc && code_of(M) >= 300) {
+      if constexpr (BR == 3) {
+        const long long threads = (long long)M.nbr * G;
+        k_spmv_vec33<G, VT, XT, E><<<ceil_div(threads, blk), blk, 0, s>>>(
+            M.nbr, static_cast<const int4*>(M.vdesc), M.vcol, M.vval, x, epi, g_l2_prefetch);
+      } else {
+        const long long threads = (long long)M.nbr * G;
+        k_spmv_vec11<G, VT, XT, E><<<ceil_div(threads, blk), blk, 0, s>>>(
+            M.nbr, static_cast<const int2*>(M.vdesc), M.vcol, M.vval, x, epi, g_l2_prefetch);
+      }
+      done = true;
+    }
+  }
   if constexpr (sizeof(VT) >= 4 && NRHS <= 3) {  // BF16 values, multi-column products: scalar-row kernel only
-    if (M.sell) {
+    if (done) {
+    } else if (M.sell) {
       const DSell<VT>& S = *static_cast<const DSell<VT>*>(M.sell);
       const long long threads = (long long)S.nchunk * kChunk;
       k_sell_spmv<BR, BC, NRHS, VT, XT, E><<<ceil_div(threads, blk), blk, 0, s>>>(S, x, epi);
@@ -278,8 +473,10 @@ inline void launch_spmv_e(const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& 
 
 // lanes per scalar row: FP64 keeps groups narrow (FP64 adds of the
 // reduction compete with the products), FP32 widens them for coalescing
-// M.g: lanes per block row (1..16, block-row kernel for BR > 1) or 100 +
-// lanes per scalar row (scalar-row kernel); 0 selects by row length
+// M.g: lanes per block row (1..16, block-row kernel for BR > 1), 100 +
+// lanes per scalar row (scalar-row kernel) or 300 + lanes per block row
+// (16-byte kernels on the padded copy, when M has one); 0 selects by row
+// length
 extern int g_forced;
 
 template <typename VT>
@@ -290,6 +487,7 @@ inline int code_of(const DBsr<VT>& M) {
 template <typename VT>
 inline int pick_group(const DBsr<VT>& M) {
   const int g = code_of(M);
+  if (g >= 300) return g - 300;
   if (g > 0) return g >= 100 ? g - 100 : g;
   // measured on the 616k-node tube: FP64 3x3 rows are fastest with 2 lanes
   // per scalar row (the FP64 pipe binds), FP32 with 4 (coalescing binds)

@@ -262,6 +262,60 @@ def test_vcycle_with_chebyshev_guard_matches_oracle():
     assert _rel(x, amg.vcycle(H, b)) < 1e-11
 
 
+@pytest.mark.parametrize("br,bc", [(3, 3), (1, 1)])
+@pytest.mark.parametrize("G", [1, 2, 4, 8])
+def test_vector_kernel_random_matrices(br, bc, G):
+    """The 16-byte kernels on the padded copy (forced with spmv_group = 300 +
+    G) equal the block product's definition on random matrices with empty
+    rows, one-block rows and ragged row lengths (the last chunk of a row
+    partly filled), over sizes spanning many CTAs."""
+    with pkg.BlockSolver(spmv_group=300 + G, autotune=0):
+        for nbr in (1, 37, 4099):
+            rng = np.random.default_rng(nbr * 11 + G + br)
+            M = _random_bsr(rng, nbr, max(nbr // 2, 3), br, bc, max_per_row=23)
+            x = rng.standard_normal(M.nb_cols * bc)
+            y = pkg.bsr_spmv(pkg.DeviceBSR.from_host(M), _dev(x)).cpu().numpy()
+            ref = bsr_matvec_by_definition(M, x)
+            assert np.allclose(y, ref, rtol=1e-13, atol=1e-13 * max(1.0, np.abs(ref).max()))
+            assert np.all(y[np.repeat(np.diff(M.row_ptr) == 0, br)] == 0.0)
+
+
+@pytest.mark.parametrize("which,bs", [(pkg.SCR_HIER_A, 3), (pkg.SCR_HIER_SHAT, 1)])
+@pytest.mark.parametrize("G", [1, 2, 4, 8])
+def test_vector_kernel_vcycle_matches_oracle(small, which, bs, G):
+    """V-cycles whose level-0 products run the 16-byte kernels (A 3x3, Shat
+    1x1, every smoother epilogue) equal the oracle's V-cycle on the exported
+    hierarchy (FP64)."""
+    with pkg.BlockSolver(spmv_group=300 + G, autotune=0) as sol:
+        sol.setup(small.A, small.B, small.C, small.D)
+        nl = sol.amg_levels(which)
+        As = [to_csr(sol.export(which, l, pkg.SCR_EXPORT_OPERATOR)) for l in range(nl)]
+        Ps = [to_csr(sol.export(which, l, pkg.SCR_EXPORT_PROLONGATOR)) for l in range(nl - 1)]
+        b = np.random.default_rng(31 + G).standard_normal(As[0].shape[0])
+        x = sol.amg_apply(which, _dev(b)).cpu().numpy()
+    H = amg.hierarchy_from_matrices(As, Ps, bs, 1, 1, "cheb", 3)
+    assert _rel(x, amg.vcycle(H, b)) < 1e-11
+
+
+@pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
+@pytest.mark.parametrize("G", [2, 4])
+def test_block_solve_with_vector_kernels_matches_direct(small, small_direct, precision, G):
+    """Whole solves with the 16-byte kernels forced (FP64 and mixed) meet the
+    direct solve; without the padded copy (vec = 0) the same forced code runs
+    the scalar-row kernel and the two answers agree to the solve tolerance."""
+    op = BlockOperator.from_system(small)
+    xs = []
+    for vec in (1, 0):
+        with pkg.BlockSolver(precision=precision, spmv_group=300 + G, autotune=0, vec=vec) as sol:
+            sol.setup(small.A, small.B, small.C, small.D)
+            x = sol.solve(small.b.copy())
+            st = sol.stats()
+        assert st["rel_res"] <= 1e-8 and rel_residual(op, x, small.b) <= 1e-8
+        assert _rel(x, small_direct) <= 1e-6
+        xs.append(x)
+    assert _rel(xs[0], xs[1]) <= 1e-6
+
+
 @pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
 def test_sliced_ell_products_match_slab_products(small, precision):
     """The sliced block-ELL copies of A, Shat and L give the same V-cycles as
