@@ -165,6 +165,8 @@ typedef struct {
   long long spmv_bytes;       /* modelled HBM bytes of the SpMV-type launches (process total) */
   int levels_A, levels_S, levels_M;
   int syncs;                  /* host waits on device scalars */
+  int kernel_A, kernel_Shat;  /* product kernel codes chosen for A and Shat in the solver
+                                 precision (see scr_opts.spmv_group; 0 = heuristic) */
 } scr_stats;
 
 /* Fill o with the defaults listed above.  Never fails for non-NULL o. */

@@ -67,6 +67,7 @@ class Stats(C.Structure):
         ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("mm_setup_ms", C.c_double),
         ("mm_solve_ms", C.c_double), ("kernel_launches", C.c_longlong), ("spmv_bytes", C.c_longlong),
         ("levels_A", C.c_int), ("levels_S", C.c_int), ("levels_M", C.c_int), ("syncs", C.c_int),
+        ("kernel_A", C.c_int), ("kernel_Shat", C.c_int),
     ]
 
     def as_dict(self) -> dict:

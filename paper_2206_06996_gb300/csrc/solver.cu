@@ -1639,6 +1639,10 @@ int scr_residual(scr_handle h, double* rel) {
 int scr_get_stats(scr_handle h, scr_stats* st) {
   if (!h || !st) return SCR_INVALID_ARG;
   *st = h->stats;
+  const bool f32 = h->o.precision == SCR_MIXED;
+  st->kernel_A = f32 ? h->Af.g : h->A.g;
+  st->kernel_Shat = h->hS.n_levels() ? (f32 ? h->hS.lv[0].Af.g : h->hS.lv[0].A.g) : 0;
+  if (forced_group() > 0) st->kernel_A = st->kernel_Shat = forced_group();
   st->kernel_launches = counters().launches;
   st->spmv_bytes = counters().spmv_bytes;
   st->levels_M = h->hM.n_levels();

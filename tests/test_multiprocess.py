@@ -67,7 +67,7 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     sys.path.insert(0, ROOT)
     import bench
     monkeypatch.setenv("RANK", "1")
-    monkeypatch.setattr(bench, "oracle_step_sample", lambda *a, **k: pytest.fail("rank 1 must not run the oracle"))
+    monkeypatch.setattr(bench, "_oracle_sample", lambda *a, **k: pytest.fail("rank 1 must not run the oracle"))
     bench.run_reference(type("A", (), {"workload": "tube_large", "warmup": 1, "steps": 1, "gpus": 2})())
     assert capsys.readouterr().out == ""
 
@@ -78,3 +78,19 @@ def test_bench_describes_each_workload_from_its_preset():
     assert bench.describe_workload("tube_large") == "straight tube 96x(11+5)x400"
     assert bench.describe_workload("stenosis") == "stenosed tube 160x(13+7)x600"
     assert bench.describe_workload("bifurcation").startswith("bifurcation, O-grid core 40x40, (24+5) rings")
+
+
+def test_member_split_is_balanced_and_complete():
+    """Independent problems split over ranks: every member on exactly one
+    rank, largest first to the least-loaded rank, so no rank carries more
+    than the lightest rank plus the largest member."""
+    import bench
+    sizes = [5, 80, 17, 17, 40, 3, 60, 22, 9, 31]
+    for world in (1, 2, 3, 4):
+        parts = bench.split_members(sizes, world)
+        assert sorted(i for p in parts for i in p) == list(range(len(sizes)))
+        loads = [sum(sizes[i] for i in p) for p in parts]
+        assert max(loads) - min(loads) <= max(sizes)
+        assert all(p == sorted(p) for p in parts)
+    assert bench.split_members([10, 10], 2) == [[0], [1]]
+    assert bench.split_members([4, 3, 3], 2) == [[0], [1, 2]]
