@@ -113,6 +113,12 @@ typedef struct {
                          which every block row's column indices and scalar rows start on 16-byte
                          boundaries (zero padding), and the autotuner also times the kernels that
                          read it with 16-byte vector loads; 0: slab products only */
+  int inner_vcycles;  /* 0 (default): Algorithm 2's inner A solve is GMRES + P_I to rtol_I (the paper);
+                         k in 1..64: k steps of Richardson's iteration preconditioned by one V-cycle
+                         (x_1 = M b, x_{i+1} = x_i + M (b - A x_i)): a fixed linear operator with no
+                         host synchronisation (the outer FGMRES is flexible) */
+  int inter_vcycles;  /* the same for the intermediate A solves of Algorithm 1 (steps 1 and 5) and of
+                         SIMPLE / SIMPLEC; 0 (default): GMRES + P_A to rtol_A */
   int l2_prefetch;    /* scalar-row products: each CTA prefetches into L2 the values and indices of
                          the CTA this many indices ahead (bulk L2 prefetch); 0 off; default 192 */
   int amg_coarse_bf16;/* mixed form only: 1 (default) stores the values of the coarse AMG levels

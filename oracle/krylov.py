@@ -146,3 +146,15 @@ def pcg(apply_op, b, apply_pc=None, tol=1e-8, maxit=500):
         p = z + (rz_new / rz) * p
         rz = rz_new
     return x, info
+
+
+def richardson(apply_op, b, apply_pc, k: int):
+    """k steps of Richardson's iteration preconditioned by M = apply_pc, from
+    x = 0: x_1 = M b, x_{i+1} = x_i + M (b - A x_i).  With M linear the
+    result is the fixed linear map sum_{i<k} (I - M A)^i M applied to b."""
+    b = np.asarray(b, dtype=np.float64)
+    x = apply_pc(b)
+    for _ in range(k - 1):
+        x = x + apply_pc(b - apply_op(x))
+    return x
+

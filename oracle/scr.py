@@ -24,6 +24,10 @@ infrastructure only; the CPU reference of the whole solver path).
   U_SIMPLE, by the diagonal lumped from the absolute values of A's entries,
   d_i = sum_j |a_ij|.
 * Mesh motion (Sec. 5.2.2): CG + AMG(L) on the harmonic extension.
+* Fixed-count A solves (options inner_vcycles, inter_vcycles): the paper's
+  inner and intermediate solves are GMRES to a tolerance; with k > 0 they are
+  k V-cycle-preconditioned Richardson steps instead, a fixed linear operator
+  (valid under the flexible outer FGMRES; the reading is stated in DESIGN).
 """
 from __future__ import annotations
 
@@ -32,7 +36,7 @@ import dataclasses
 import numpy as np
 
 from . import amg
-from .krylov import fgmres, gmres, pcg
+from .krylov import fgmres, gmres, pcg, richardson
 from .schur import schur_hat, simple_diagonal
 from .sparse import BlockOperator, rel_residual, to_csr
 
@@ -60,6 +64,8 @@ class SolverOptions:
     smoother: str = "cheb"
     cheb_degree: int = 3
     precond: str = "scr"       # "scr" (Algorithm 1), "simple" or "simplec"
+    inner_vcycles: int = 0     # Algorithm 2's A solve: 0 = GMRES to rtol_I, k = k Richardson steps
+    inter_vcycles: int = 0     # Algorithm 1's A solves (steps 1, 5) and SIMPLE's: 0 = GMRES to rtol_A
     mm_rtol: float = 1e-8
     mm_max_it: int = 500
 
@@ -92,9 +98,13 @@ class SCRSolver:
     def apply_S(self, xp: np.ndarray) -> np.ndarray:
         o, op = self.opts, self.op
         xbar = op.B @ xp
-        xt, info = gmres(lambda v: op.A @ v, xbar, lambda v: amg.vcycle(self.amg_A, v),
-                         tol=o.rtol_I, maxit=o.max_I, restart=o.restart_inner)
-        self.cnt.i_iters += info.iters
+        if o.inner_vcycles > 0:
+            xt = richardson(lambda v: op.A @ v, xbar, lambda v: amg.vcycle(self.amg_A, v), o.inner_vcycles)
+            self.cnt.i_iters += o.inner_vcycles
+        else:
+            xt, info = gmres(lambda v: op.A @ v, xbar, lambda v: amg.vcycle(self.amg_A, v),
+                             tol=o.rtol_I, maxit=o.max_I, restart=o.restart_inner)
+            self.cnt.i_iters += info.iters
         xbar = op.C @ xt
         xhat = op.D @ xp
         return xhat - xbar
@@ -102,9 +112,12 @@ class SCRSolver:
     # Algorithm 1 ------------------------------------------------------
     def solve_A(self, rv: np.ndarray) -> np.ndarray:
         o, op = self.opts, self.op
+        self.cnt.a_solves += 1
+        if o.inter_vcycles > 0:
+            self.cnt.a_iters += o.inter_vcycles
+            return richardson(lambda v: op.A @ v, rv, lambda v: amg.vcycle(self.amg_A, v), o.inter_vcycles)
         y, info = gmres(lambda v: op.A @ v, rv, lambda v: amg.vcycle(self.amg_A, v),
                         tol=o.rtol_A, maxit=o.max_A, restart=o.restart_inner)
-        self.cnt.a_solves += 1
         self.cnt.a_iters += info.iters
         return y
 

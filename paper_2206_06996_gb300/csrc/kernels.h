@@ -43,6 +43,11 @@ void slab_to_float(const double* in, float* out, long long n, cudaStream_t s);
 // slab float -> slab BF16 (round to nearest even); out holds n __nv_bfloat16
 void slab_to_bf16(const float* in, void* out, long long n, cudaStream_t s);
 
+// y_p = D x_p - C x_t in one pass (the last line of Algorithm 2); C 1x3
+// blocks, D 1x1, nrhs interleaved right-hand sides (1 or kSpmmCols)
+template <typename T>
+void schur_combine(const DBsr<T>& C, const DBsr<T>& D, const T* xt, const T* xp, T* yp, int nrhs, cudaStream_t s);
+
 // Validation of caller index arrays before any kernel indexes with them:
 // sets *bad (device int, not cleared here) when a row pointer is out of
 // [0, nnzb] or decreasing, or a column index is out of [0, nbc), unsorted or

@@ -742,6 +742,8 @@ struct scr_ctx {
   float* dAinvf = nullptr;
   float *pr = nullptr, *py = nullptr, *yhatf = nullptr, *rp2f = nullptr, *rv2f = nullptr, *xbarf = nullptr,
         *xtf = nullptr;
+  double *rr = nullptr, *rt = nullptr;  // fixed-count A solves (inner_vcycles, inter_vcycles)
+  float *rrf = nullptr, *rtf = nullptr;
   // mesh CG
   double *mb = nullptr, *mx = nullptr, *mr = nullptr, *mz = nullptr, *mp = nullptr, *mq = nullptr;
   CgState* cg = nullptr;
@@ -895,17 +897,18 @@ struct PcView {
   Hierarchy *hA, *hS;
   Gmres<T>*gA, *gS, *gI;
   T *yhat, *rp2, *rv2, *xbar, *xt;
+  T *rr, *rt;  // fixed-count A solves: residual and correction
   const T* dAinv;
   const T* out_a;  // outlet vectors in this precision (n_out x 3 n_v) or null
 };
 
 PcView<double> view64(scr_ctx* h) {
   return PcView<double>{&h->A, &h->B, &h->C, &h->D, &h->Shat, &h->hA, &h->hS, &h->gA, &h->gS, &h->gI,
-                        h->yhat, h->rp2, h->rv2, h->xbar, h->xt, h->dAinv, h->out_a};
+                        h->yhat, h->rp2, h->rv2, h->xbar, h->xt, h->rr, h->rt, h->dAinv, h->out_a};
 }
 PcView<float> view32(scr_ctx* h) {
   return PcView<float>{&h->Af, &h->Bf, &h->Cf, &h->Df, &h->hS.lv[0].Af, &h->hA, &h->hS, &h->gAf, &h->gSf, &h->gIf,
-                       h->yhatf, h->rp2f, h->rv2f, h->xbarf, h->xtf, h->dAinvf, h->out_af};
+                       h->yhatf, h->rp2f, h->rv2f, h->xbarf, h->xtf, h->rrf, h->rtf, h->dAinvf, h->out_af};
 }
 
 // y += sign * sum_j c_j a_j (a_j^T x) on the velocity rows (the outlets'
@@ -932,24 +935,57 @@ void apply_calA(scr_ctx* h, const double* x, double* y, const double* z, bool re
   if (h->n_out) outlet_terms<double>(h, h->out_a, x, y, resid ? -1.0 : 1.0);
 }
 
+// A^{-1} b approximated by k steps of Richardson's iteration preconditioned
+// by one V-cycle M, from x = 0: x_1 = M b, x_{i+1} = x_i + M (b - A x_i).
+// A fixed linear operator (the same for every b) without host
+// synchronisation; it replaces GMRES to a tolerance when the options ask for
+// a fixed count (the outer FGMRES is flexible, and a fixed linear inner
+// solve keeps the S operator of Algorithm 2 linear for the GMRES on S).
+template <typename T>
+void richardson_A(scr_ctx* h, PcView<T>& v, int k, const T* b, T* x) {
+  cudaStream_t s = h->s;
+  const long long n = 3LL * h->nv * h->k;
+  v.hA->template apply<T>(b, x, s);
+  for (int i = 1; i < k; ++i) {
+    if (h->n_out) {
+      apply_A<T>(h, v, x, v.rr);
+      axpby_t<T>(1.0, b, -1.0, v.rr, n, s);
+    } else {
+      EpiArgs res;
+      res.kind = Epi::Resid;
+      res.z = b;
+      spmv<T, T>(*v.A, x, v.rr, h->k, res, s);
+    }
+    v.hA->template apply<T>(v.rr, v.rt, s);
+    axpby_t<T>(1.0, v.rt, 1.0, x, n, s);
+  }
+}
+
+// an intermediate or inner A solve: GMRES + P_A to rtol (the paper), or k
+// fixed V-cycle Richardson steps when k > 0; returns the iterations
+template <typename T>
+int solve_A(scr_ctx* h, PcView<T>& v, Gmres<T>* g, int k, double rtol, int maxit, const T* b, T* x) {
+  if (k > 0) {
+    richardson_A<T>(h, v, k, b, x);
+    return k;
+  }
+  cudaStream_t s = h->s;
+  typename Gmres<T>::Op opA = [&](const T* xx, T* y) { apply_A<T>(h, v, xx, y); };
+  typename Gmres<T>::Op pcA = [&](const T* bb, T* xx) { v.hA->template apply<T>(bb, xx, s); };
+  int it = 0;
+  double rel = 0;
+  g->solve(opA, &pcA, b, x, rtol, maxit, h->red, s, &it, &rel);
+  return it;
+}
+
 // Algorithm 2: y_p = D x_p - C A^{-1} (B x_p), A^{-1} by inner GMRES + P_I
+// (or the fixed-count solve); D x_p - C x_t in one pass
 template <typename T>
 void apply_S(scr_ctx* h, PcView<T>& v, const T* xp, T* yp) {
   cudaStream_t s = h->s;
   spmv<T, T>(*v.B, xp, v.xbar, h->k, EpiArgs(), s);
-  typename Gmres<T>::Op opA = [&](const T* x, T* y) { apply_A<T>(h, v, x, y); };
-  typename Gmres<T>::Op pcA = [&](const T* b, T* x) { v.hA->template apply<T>(b, x, s); };
-  int it = 0;
-  double rel = 0;
-  v.gI->solve(opA, &pcA, v.xbar, v.xt, h->o.rtol_I, h->o.max_I, h->red, s, &it, &rel);
-  h->stats.i_iters += it;
-  spmv<T, T>(*v.D, xp, yp, h->k, EpiArgs(), s);
-  EpiArgs sub;
-  sub.kind = Epi::Axpby;
-  sub.alpha = -1.0;
-  sub.beta = 1.0;
-  sub.z = yp;
-  spmv<T, T>(*v.C, v.xt, yp, h->k, sub, s);
+  h->stats.i_iters += solve_A<T>(h, v, v.gI, h->o.inner_vcycles, h->o.rtol_I, h->o.max_I, v.xbar, v.xt);
+  schur_combine<T>(*v.C, *v.D, v.xt, xp, yp, h->k, s);
 }
 
 // Algorithm 1: y = P_SCR^{-1} r
@@ -961,16 +997,14 @@ void apply_pc(scr_ctx* h, PcView<T>& v, const T* r, T* y) {
   const T* rp = r + nv3;
   T* yv = y;
   T* yp = y + nv3;
-  typename Gmres<T>::Op opA = [&](const T* x, T* o) { apply_A<T>(h, v, x, o); };
-  typename Gmres<T>::Op pcA = [&](const T* b, T* x) { v.hA->template apply<T>(b, x, s); };
   typename Gmres<T>::Op opS = [&](const T* x, T* o) { apply_S<T>(h, v, x, o); };
   typename Gmres<T>::Op pcS = [&](const T* b, T* x) { v.hS->template apply<T>(b, x, s); };
   int it = 0;
   double rel = 0;
+  const int kA = h->o.inter_vcycles;
   // 1. A yhat_v = r_v
-  v.gA->solve(opA, &pcA, rv, v.yhat, h->o.rtol_A, h->o.max_A, h->red, s, &it, &rel);
+  h->stats.a_iters += solve_A<T>(h, v, v.gA, kA, h->o.rtol_A, h->o.max_A, rv, v.yhat);
   h->stats.a_solves++;
-  h->stats.a_iters += it;
   // 2. r_p <- r_p - C yhat_v
   EpiArgs e;
   e.kind = Epi::Axpby;
@@ -985,9 +1019,8 @@ void apply_pc(scr_ctx* h, PcView<T>& v, const T* r, T* y) {
   e.z = rv;
   spmv<T, T>(*v.B, yp, v.rv2, h->k, e, s);
   // 5. A y_v = r_v
-  v.gA->solve(opA, &pcA, v.rv2, yv, h->o.rtol_A, h->o.max_A, h->red, s, &it, &rel);
+  h->stats.a_iters += solve_A<T>(h, v, v.gA, kA, h->o.rtol_A, h->o.max_A, v.rv2, yv);
   h->stats.a_solves++;
-  h->stats.a_iters += it;
 }
 
 // P_SIMPLE^{-1} r = U_SIMPLE^{-1} diag(A, Shat)^{-1} L^{-1} r (Sec. 5.2.1):
@@ -1002,15 +1035,12 @@ void apply_simple(scr_ctx* h, PcView<T>& v, const T* r, T* y) {
   const T* rp = r + nv3;
   T* yv = y;
   T* yp = y + nv3;
-  typename Gmres<T>::Op opA = [&](const T* x, T* o) { apply_A<T>(h, v, x, o); };
-  typename Gmres<T>::Op pcA = [&](const T* b, T* x) { v.hA->template apply<T>(b, x, s); };
   typename Gmres<T>::Op opS = [&](const T* x, T* o) { spmv<T, T>(*v.Shat, x, o, h->k, EpiArgs(), s); };
   typename Gmres<T>::Op pcS = [&](const T* b, T* x) { v.hS->template apply<T>(b, x, s); };
   int it = 0;
   double rel = 0;
-  v.gA->solve(opA, &pcA, rv, v.yhat, h->o.rtol_A, h->o.max_A, h->red, s, &it, &rel);
+  h->stats.a_iters += solve_A<T>(h, v, v.gA, h->o.inter_vcycles, h->o.rtol_A, h->o.max_A, rv, v.yhat);
   h->stats.a_solves++;
-  h->stats.a_iters += it;
   EpiArgs e;
   e.kind = Epi::Axpby;
   e.alpha = -1.0;
@@ -1084,6 +1114,8 @@ int scr_default_opts(scr_opts* o) {
   o->amg_degree = 3;
   o->sell = 0;
   o->vec = 1;
+  o->inner_vcycles = 0;
+  o->inter_vcycles = 0;
   o->l2_prefetch = 192;
   o->amg_coarse_bf16 = 1;
   o->cuda_graphs = 1;
@@ -1114,6 +1146,8 @@ int scr_create(scr_handle* out, const scr_opts* o, void* stream) {
     if (op.amg_degree < 1 || op.amg_degree > 16) throw std::invalid_argument("Chebyshev degree must lie in [1, 16]");
     if (op.l2_prefetch < 0) throw std::invalid_argument("l2_prefetch must be >= 0");
     if (op.vec != 0 && op.vec != 1) throw std::invalid_argument("vec must be 0 or 1");
+    if (op.inner_vcycles < 0 || op.inner_vcycles > 64 || op.inter_vcycles < 0 || op.inter_vcycles > 64)
+      throw std::invalid_argument("inner_vcycles and inter_vcycles must lie in [0, 64]");
     if (op.nrhs != 1 && op.nrhs != kSpmmCols) throw std::invalid_argument("nrhs must be 1 or 8");
     if (op.amg_coarse_bf16 != 0 && op.amg_coarse_bf16 != 1) throw std::invalid_argument("amg_coarse_bf16 must be 0 or 1");
     std::unique_ptr<scr_ctx> h(new scr_ctx());
@@ -1278,6 +1312,8 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
       h->rv2f = w.alloc<float>(nv3 + 1);
       h->xbarf = w.alloc<float>(nv3 + 1);
       h->xtf = w.alloc<float>(nv3 + 1);
+      h->rrf = w.alloc<float>(nv3 + 1);
+      h->rtf = w.alloc<float>(nv3 + 1);
       h->rp2f = w.alloc<float>((long long)np * k + 1);
     } else {
       h->gA.init(w, nv3, h->o.restart_inner);
@@ -1287,6 +1323,8 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
       h->rv2 = w.alloc<double>(nv3 + 1);
       h->xbar = w.alloc<double>(nv3 + 1);
       h->xt = w.alloc<double>(nv3 + 1);
+      h->rr = w.alloc<double>(nv3 + 1);
+      h->rt = w.alloc<double>(nv3 + 1);
       h->rp2 = w.alloc<double>((long long)np * k + 1);
     }
     SCR_CUDA(cudaStreamSynchronize(s));

@@ -494,6 +494,59 @@ __global__ void __launch_bounds__(256) k_block_op(int nv, int np, DBsr<double> A
   }
 }
 
+// y_p = D x_p - C x_t, the last line of Algorithm 2 (App. B) in one pass:
+// one G-group per pressure row accumulates the row of C against x_t and the
+// row of D against x_p, so y_p is written once and never read back.
+template <int G, int NRHS, typename T>
+__global__ void __launch_bounds__(256) k_schur_combine(int np, DBsr<T> C, DBsr<T> D, const T* __restrict__ xt,
+                                                       const T* __restrict__ xp, T* __restrict__ yp) {
+  const long long o = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;
+  const int lane = threadIdx.x % G;
+  const bool active = o < np;  // inactive lanes still join the shuffles
+  T ac[NRHS], ad[NRHS];
+#pragma unroll
+  for (int h = 0; h < NRHS; ++h) ac[h] = ad[h] = (T)0;
+  if (active) {
+    scalar_row_accum<3, NRHS, G>(C.rp, C.col, C.val, xt, 1, (int)o, 0, lane, ac);
+    scalar_row_accum<1, NRHS, G>(D.rp, D.col, D.val, xp, 1, (int)o, 0, lane, ad);
+  }
+#pragma unroll
+  for (int h = 0; h < NRHS; ++h)
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+      ac[h] += __shfl_xor_sync(0xffffffffu, ac[h], off, G);
+      ad[h] += __shfl_xor_sync(0xffffffffu, ad[h], off, G);
+    }
+  if (active && lane == 0) {
+#pragma unroll
+    for (int h = 0; h < NRHS; ++h) yp[o * NRHS + h] = ad[h] - ac[h];
+  }
+}
+
+template <typename T>
+void schur_combine(const DBsr<T>& C, const DBsr<T>& D, const T* xt, const T* xp, T* yp, int nrhs,
+                   cudaStream_t s) {
+  const int np = D.nbr;
+  if (np == 0) return;
+  constexpr int G = 4;
+  const long long threads = (long long)np * G;
+  if (nrhs == 1)
+    k_schur_combine<G, 1, T><<<ceil_div(threads, 256), 256, 0, s>>>(np, C, D, xt, xp, yp);
+  else if (nrhs == kSpmmCols)
+    k_schur_combine<G, kSpmmCols, T><<<ceil_div(threads, 256), 256, 0, s>>>(np, C, D, xt, xp, yp);
+  else
+    throw CudaError{cudaErrorInvalidValue, "schur_combine: unsupported number of right-hand sides"};
+  SCR_LAUNCH();
+  counters().launches++;
+  counters().spmv_bytes += (long long)((double)C.nnzb * (3 * sizeof(T) + 4) + (double)D.nnzb * (sizeof(T) + 4) +
+                                       (2.0 * np + 2) * 4 + (double)C.nbc * 3 * nrhs * sizeof(T) +
+                                       2.0 * np * nrhs * sizeof(T));
+}
+template void schur_combine<double>(const DBsr<double>&, const DBsr<double>&, const double*, const double*, double*,
+                                    int, cudaStream_t);
+template void schur_combine<float>(const DBsr<float>&, const DBsr<float>&, const float*, const float*, float*, int,
+                                   cudaStream_t);
+
 template <int NRHS>
 static void launch_block_op(int nv, int np, const DBsr<double>& A, const DBsr<double>& B, const DBsr<double>& C,
                             const DBsr<double>& D, const double* x, double* y, const double* z, bool resid,

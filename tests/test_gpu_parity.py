@@ -409,6 +409,51 @@ def test_algorithm2_tight_inner_equals_schur(mini):
     assert _rel(y, S @ xp) < 1e-8
 
 
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_algorithm2_fixed_count_inner_matches_oracle(small, k):
+    """Algorithm 2 with the inner A solve as k V-cycle Richardson steps: the
+    GPU's S x_p equals D x_p - C R_k B x_p with R_k the oracle's Richardson
+    map on the exported hierarchy of A (FP64)."""
+    op = BlockOperator.from_system(small)
+    xp = np.random.default_rng(40 + k).standard_normal(op.np)
+    with pkg.BlockSolver(inner_vcycles=k) as sol:
+        sol.setup(small.A, small.B, small.C, small.D)
+        y = sol.apply_schur(_dev(xp)).cpu().numpy()
+        nl = sol.amg_levels(pkg.SCR_HIER_A)
+        As = [to_csr(sol.export(pkg.SCR_HIER_A, l, pkg.SCR_EXPORT_OPERATOR)) for l in range(nl)]
+        Ps = [to_csr(sol.export(pkg.SCR_HIER_A, l, pkg.SCR_EXPORT_PROLONGATOR)) for l in range(nl - 1)]
+    from oracle import krylov
+    H = amg.hierarchy_from_matrices(As, Ps, 3, 1, 1, "cheb", 3)
+    A = to_csr(small.A)
+    xt = krylov.richardson(lambda v: A @ v, op.B @ xp, lambda v: amg.vcycle(H, v), k)
+    ref = op.D @ xp - op.C @ xt
+    assert _rel(y, ref) < 1e-11
+
+
+@pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
+@pytest.mark.parametrize("inner,inter", [(2, 0), (3, 2)])
+def test_block_solve_with_fixed_count_a_solves_matches_direct(small, small_direct, precision, inner, inter):
+    """Whole SCR solves with fixed-count inner (and intermediate) A solves
+    meet 1e-8 and the direct solution to 1e-6; the inner count is exactly k
+    per application of S."""
+    op = BlockOperator.from_system(small)
+    with pkg.BlockSolver(precision=precision, inner_vcycles=inner, inter_vcycles=inter) as sol:
+        sol.setup(small.A, small.B, small.C, small.D)
+        x = sol.solve(small.b.copy())
+        st = sol.stats()
+    assert st["rel_res"] <= 1e-8 and rel_residual(op, x, small.b) <= 1e-8
+    assert _rel(x, small_direct) <= 1e-6
+    assert st["i_iters"] == inner * st["s_iters"] or st["i_iters"] % inner == 0
+    if inter:
+        assert st["a_iters"] == inter * st["a_solves"]
+
+
+def test_fixed_count_options_are_validated():
+    for bad in ({"inner_vcycles": -1}, {"inter_vcycles": 65}):
+        with pytest.raises(pkg.ScrError):
+            pkg.BlockSolver(**bad)
+
+
 def test_algorithm1_tight_solves_equals_inverse(mini, mini_x):
     op = BlockOperator.from_system(mini)
     with pkg.BlockSolver(rtol_A=1e-13, rtol_S=1e-12, rtol_I=1e-14, max_A=2000, max_S=2000, max_I=2000,

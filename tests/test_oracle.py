@@ -790,3 +790,40 @@ def test_bifurcation_scr_and_mesh_cg_match_direct():
     u, minfo = m.solve(s.mesh_b)
     ud = direct.solve_mesh(s)
     assert minfo.converged and np.linalg.norm(u - ud) <= 1e-9 * np.linalg.norm(ud)
+
+
+# ---------------------------------------------------------------- fixed-count A solves
+def test_richardson_closed_form():
+    """k Richardson steps with a linear preconditioner M = omega I equal the
+    closed form x_k = V diag((1 - (1 - omega lam)^k) / lam) V^T b from the
+    eigen-decomposition of an SPD A (the truncated Neumann series of A^{-1})."""
+    rng = np.random.default_rng(7)
+    Q, _ = np.linalg.qr(rng.standard_normal((12, 12)))
+    lam = np.linspace(0.5, 3.0, 12)
+    A = (Q * lam) @ Q.T
+    b = rng.standard_normal(12)
+    omega = 0.4
+    for k in (1, 2, 5):
+        x = krylov.richardson(lambda v: A @ v, b, lambda v: omega * v, k)
+        ref = Q @ (((1.0 - (1.0 - omega * lam) ** k) / lam) * (Q.T @ b))
+        assert np.allclose(x, ref, rtol=1e-12, atol=1e-14)
+    # an exact preconditioner solves in one step, and further steps keep it
+    Ainv = np.linalg.inv(A)
+    for k in (1, 3):
+        x = krylov.richardson(lambda v: A @ v, b, lambda v: Ainv @ v, k)
+        assert np.allclose(A @ x, b, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("inner,inter", [(2, 0), (3, 2), (1, 1)])
+def test_scr_with_fixed_count_a_solves_matches_direct(mini_system, mini_direct, inner, inter):
+    """With Algorithm 2's inner A solve (and Algorithm 1's A solves) replaced
+    by a few V-cycle Richardson steps, the flexible outer FGMRES still meets
+    1e-8 and the direct solution to 1e-6."""
+    s = mini_system
+    out = scr.solve_system(s, scr.SolverOptions(inner_vcycles=inner, inter_vcycles=inter))
+    op = BlockOperator.from_system(s)
+    assert out["info"].converged
+    assert rel_residual(op, out["x"], s.b) <= 1e-8
+    assert np.linalg.norm(out["x"] - mini_direct) <= 1e-6 * np.linalg.norm(mini_direct)
+    assert out["counters"].i_iters % inner == 0
+
