@@ -77,6 +77,9 @@ extern "C" {
 #define SCR_EXPORT_AGGREGATES 2  /* aggregate id per block row of level l (-1: none), into col_idx */
 #define SCR_EXPORT_ROOTS 3       /* root block row of each aggregate of level l (the distance-2
                                     independent node that seeded it), n_agg entries into col_idx */
+#define SCR_EXPORT_BLOCK_B 4     /* the set-up B, C, D blocks of the block system (level 0; which is */
+#define SCR_EXPORT_BLOCK_C 5     /* ignored); with SCR_EXPORT_OPERATOR of SCR_HIER_A level 0 (A) they */
+#define SCR_EXPORT_BLOCK_D 6     /* give back the whole Jacobian the solver holds */
 
 typedef struct scr_ctx* scr_handle;
 
@@ -119,6 +122,10 @@ typedef struct {
                          host synchronisation (the outer FGMRES is flexible) */
   int inter_vcycles;  /* the same for the intermediate A solves of Algorithm 1 (steps 1 and 5) and of
                          SIMPLE / SIMPLEC; 0 (default): GMRES + P_A to rtol_A */
+  int newton;         /* scr_corrector / scr_corrector_ale: 0 (default) hold the tangent of the last
+                         scr_setup fixed (modified Newton); 1 re-assemble it on the GPU at every
+                         iteration's state (scr_assemble_tangent) before that iteration's solve, as
+                         the paper's multi-corrector does */
   int l2_prefetch;    /* scalar-row products: each CTA prefetches into L2 the values and indices of
                          the CTA this many indices ahead (bulk L2 prefetch); 0 off; default 192 */
   int amg_coarse_bf16;/* mixed form only: 1 (default) stores the values of the coarse AMG levels
@@ -288,8 +295,32 @@ int scr_assembly_setup(scr_handle h, const scr_mesh* m, const scr_physics* ph);
 int scr_assemble_residual(scr_handle h, const double* v, const double* vhat, const double* p,
                           const double* vdot, const double* u, double* R, int dev);
 
+/* Tangent assembly on the GPU (Sec. 3.5: the consistent tangent K =
+   alpha_m dR/d(ydot) + alpha_f gamma dt dR/dy of the element residuals of
+   scr_assemble_residual, with tau_M and tau_C evaluated at the state and held
+   fixed; generalized-alpha weights from scr_physics.rho_inf and dt).  At the
+   state v, p (at t_{n+alpha_f}), vhat (mesh velocity; may be NULL: zero) and
+   vdot (at t_{n+alpha_m}; may be NULL: zero), host pointers when dev == 0,
+   device pointers otherwise, it writes the blocks A, B, C, D into the
+   sparsity pattern of the matrices of the last scr_setup, with the velocity
+   Dirichlet nodes of scr_assembly_setup as identity rows of A (the input
+   convention: the pattern holds no other block in a Dirichlet row or column
+   of A, B, C), and then runs the set-up of the block solve on them (Shat,
+   AMG hierarchies, lower-precision copies), so the next scr_solve solves
+   with this Jacobian.  The element tangents are formed one thread per
+   (element, column vertex) and summed per stored block in increasing
+   element order, so every run gives the same values.  The pattern is
+   captured at the first call after a caller's scr_setup; the solid
+   displacement does not enter (the solid is linearised at the reference
+   state).  SCR_INVALID_ARG without scr_setup (not batched) and
+   scr_assembly_setup on the same mesh, or for NULL v, p. */
+int scr_assemble_tangent(scr_handle h, const double* v, const double* vhat, const double* p, const double* vdot,
+                         int dev);
+
 /* Segregated multi-corrector iterations (Sec. 3.5) on the GPU: with the
-   tangent of the last scr_setup held fixed (modified Newton) and the mesh
+   tangent of the last scr_setup held fixed (modified Newton; with the option
+   newton = 1 the tangent is re-assembled at every iteration's state by
+   scr_assemble_tangent before that iteration's solve) and the mesh
    of scr_assembly_setup held fixed (no mesh-motion update inside the loop),
    n_iter times: R = scr_assemble_residual at the state (plus the outlet
    tractions m_j (a_j^T v) a_j of scr_set_outlets, with m_j = c_j / (alpha_f

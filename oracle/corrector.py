@@ -20,13 +20,22 @@ solid displacement at t_{n+1} on the fluid-solid interface (zero on the other
 Dirichlet mesh nodes), the mesh velocity at t_{n+1} follows from it, and the
 residual sees the mesh velocity at t_{n+alpha_f} in its convective velocity.
 The element geometry stays the reference configuration.
+
+``tangent`` is the block Jacobian at an arbitrary state: the generator's
+element loop with the consistent tangent (tau frozen at the state) and the
+boundary conditions of the input convention (Dirichlet velocity nodes:
+identity rows of A, their rows of B and their columns of A and C dropped).
+With ``newton=True`` the loops re-assemble it at every iteration's state
+before that iteration's solve (the paper's multi-corrector re-assembles the
+left-hand side at each iteration), instead of holding the initial one.
 """
 from __future__ import annotations
 
 import numpy as np
+import scipy.sparse as sp
 import scipy.sparse.linalg as spl
 
-from .sparse import BlockOperator
+from .sparse import BlockOperator, to_csr
 
 
 def genalpha_weights(rho_inf: float, dt: float):
@@ -66,15 +75,33 @@ def mesh_velocity(uhat_n1, uhat_n, vhat_n, rho_inf: float, dt: float):
     return v1, vhat_n + af * (v1 - vhat_n)
 
 
-def corrector(system, assembler, v, p, vdot, u, n_iter: int):
+def tangent(system, assembler, v, p, vdot=None, vhat=None):
+    """(A, B, C, D) as scalar CSR matrices: the raw consistent tangent of the
+    element loop at the state, K = alpha_m dR/dvdot + alpha_f gamma dt dR/dy
+    (the solid displacement moving by (alpha_f gamma dt)^2 / alpha_m), with
+    the Dirichlet velocity nodes' rows of A replaced by identity rows and
+    their rows of B and columns of A and C removed."""
+    am, cf, cu = genalpha_weights(system.params["rho_inf"], system.params["dt"])
+    raw = assembler.evaluate(v, p, vd=vdot, vhat=vhat, cm=am, cf=cf, cu=cu, want_mat=True)
+    dv = np.repeat(np.asarray(system.mesh.dir_v, dtype=bool), 3)
+    keep = sp.diags((~dv).astype(np.float64))
+    A = (keep @ to_csr(raw["A"]) @ keep + sp.diags(dv.astype(np.float64))).tocsr()
+    B = (keep @ to_csr(raw["B"])).tocsr()
+    C = (to_csr(raw["C"]) @ keep).tocsr()
+    D = to_csr(raw["D"]).tocsr()
+    return A, B, C, D
+
+
+def corrector(system, assembler, v, p, vdot, u, n_iter: int, newton: bool = False):
     """n_iter corrector iterations; returns the final (v, p, vdot, u) and the
-    right-hand-side norms before each solve and after the last update."""
-    v, p, vdot, u, _, norms = _loop(system, assembler, v, p, vdot, u, n_iter, None)
+    right-hand-side norms before each solve and after the last update.  With
+    newton=True the tangent is re-assembled at every iteration's state."""
+    v, p, vdot, u, _, norms = _loop(system, assembler, v, p, vdot, u, n_iter, None, newton)
     return v, p, vdot, u, norms
 
 
 def corrector_ale(system, assembler, v, p, vdot, u, n_iter: int, L_raw, fluid_id, dir_m, follow,
-                  uhat_n, vhat_n):
+                  uhat_n, vhat_n, newton: bool = False):
     """As ``corrector`` with the mesh moving inside the loop.  The state
     enters at the same-Y predictor (Sec. 3.5), so u at entry is u_n; each
     iteration takes u_{n+1} = u_n + (u - u_n) / alpha_f, the Dirichlet data
@@ -86,12 +113,12 @@ def corrector_ale(system, assembler, v, p, vdot, u, n_iter: int, L_raw, fluid_id
     mesh = dict(L=L_raw, fid=np.asarray(fluid_id), dir_m=np.asarray(dir_m, dtype=bool),
                 follow=np.asarray(follow, dtype=bool), uhat_n=np.asarray(uhat_n, dtype=np.float64),
                 vhat_n=np.asarray(vhat_n, dtype=np.float64))
-    return _loop(system, assembler, v, p, vdot, u, n_iter, mesh)
+    return _loop(system, assembler, v, p, vdot, u, n_iter, mesh, newton)
 
 
-def _loop(system, assembler, v, p, vdot, u, n_iter, mesh):
+def _loop(system, assembler, v, p, vdot, u, n_iter, mesh, newton=False):
     op = BlockOperator.from_system(system)
-    lu = spl.splu(op.full().tocsc(), permc_spec="MMD_ATA")
+    lu = None if newton else spl.splu(op.full().tocsc(), permc_spec="MMD_ATA")
     rho_inf, dt = system.params["rho_inf"], system.params["dt"]
     am, cf, cu = genalpha_weights(rho_inf, dt)
     af = 1.0 / (1.0 + rho_inf)
@@ -129,6 +156,12 @@ def _loop(system, assembler, v, p, vdot, u, n_iter, mesh):
         norms.append(float(np.linalg.norm(b)))
         if it == n_iter:
             break
+        if newton:
+            A, B, C, D = tangent(system, assembler, v, p, vdot, vhat)
+            for a, c in zip(a_out, c_out):
+                a = sp.csr_matrix(np.asarray(a, dtype=np.float64).reshape(-1, 1))
+                A = (A + c * (a @ a.T)).tocsr()
+            lu = spl.splu(sp.bmat([[A, B], [C, D]], format="csc"), permc_spec="MMD_ATA")
         x = lu.solve(b)
         vdot += am * x[:nv3]
         v += cf * x[:nv3]

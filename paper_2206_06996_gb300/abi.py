@@ -11,6 +11,7 @@ SCR_FP64, SCR_MIXED = 0, 1
 SCR_PC_SCR, SCR_PC_SIMPLE, SCR_PC_SIMPLEC = 0, 1, 2
 SCR_HIER_A, SCR_HIER_SHAT, SCR_HIER_MESH = 0, 1, 2
 SCR_EXPORT_OPERATOR, SCR_EXPORT_PROLONGATOR, SCR_EXPORT_AGGREGATES, SCR_EXPORT_ROOTS = 0, 1, 2, 3
+SCR_EXPORT_BLOCK_B, SCR_EXPORT_BLOCK_C, SCR_EXPORT_BLOCK_D = 4, 5, 6
 
 STATUS_NAMES = {0: "SCR_OK", 1: "SCR_INVALID_ARG", 2: "SCR_CUDA_ERROR", 3: "SCR_NOT_CONVERGED",
                 4: "SCR_DEVICE_TIMEOUT", 5: "SCR_SINGULAR"}
@@ -32,6 +33,7 @@ class Opts(C.Structure):
         ("amg_nu", C.c_int), ("amg_trunc", C.c_double), ("amg_pmax", C.c_int), ("autotune", C.c_int),
         ("amg_smoother", C.c_int), ("amg_degree", C.c_int), ("spmv_group", C.c_int),
         ("sell", C.c_int), ("vec", C.c_int), ("inner_vcycles", C.c_int), ("inter_vcycles", C.c_int),
+        ("newton", C.c_int),
         ("l2_prefetch", C.c_int), ("amg_coarse_bf16", C.c_int), ("cuda_graphs", C.c_int),
         ("nrhs", C.c_int),
         ("mm_rtol", C.c_double), ("mm_max_it", C.c_int), ("verbose", C.c_int),
@@ -88,7 +90,7 @@ EXPORTED = [
     "scr_export", "scr_bsr_spmv", "scr_profile_begin", "scr_profile_end", "scr_bsr_spmv_noalloc",
     "scr_setup_batch", "scr_solve_batch", "scr_batch_residuals", "scr_tune_save", "scr_tune_load",
     "scr_solve_multi", "scr_set_outlets", "scr_assembly_setup", "scr_assemble_residual",
-    "scr_corrector", "scr_mesh_coupling", "scr_corrector_ale",
+    "scr_corrector", "scr_mesh_coupling", "scr_corrector_ale", "scr_assemble_tangent",
 ]
 
 _lib = None

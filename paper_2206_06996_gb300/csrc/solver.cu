@@ -766,6 +766,11 @@ struct scr_ctx {
   // residual assembly (scr_assembly_setup)
   ResidualAssembler ra;
   std::unique_ptr<DeviceArena> rmats;
+  // tangent assembly (scr_assemble_tangent): patterns of the block system
+  // captured from the set-up it first ran after, and its own re-set-ups
+  TangentAssembler ta;
+  std::unique_ptr<DeviceArena> tmats;
+  bool tangent_setup = false;  // scr_setup called by scr_assemble_tangent
   bool have_residual = false;
   std::vector<unsigned char> dir_v;  // velocity Dirichlet flag per node (empty: none)
   scr_physics phys{};
@@ -1116,6 +1121,7 @@ int scr_default_opts(scr_opts* o) {
   o->vec = 1;
   o->inner_vcycles = 0;
   o->inter_vcycles = 0;
+  o->newton = 0;
   o->l2_prefetch = 192;
   o->amg_coarse_bf16 = 1;
   o->cuda_graphs = 1;
@@ -1148,6 +1154,7 @@ int scr_create(scr_handle* out, const scr_opts* o, void* stream) {
     if (op.vec != 0 && op.vec != 1) throw std::invalid_argument("vec must be 0 or 1");
     if (op.inner_vcycles < 0 || op.inner_vcycles > 64 || op.inter_vcycles < 0 || op.inter_vcycles > 64)
       throw std::invalid_argument("inner_vcycles and inter_vcycles must lie in [0, 64]");
+    if (op.newton != 0 && op.newton != 1) throw std::invalid_argument("newton must be 0 or 1");
     if (op.nrhs != 1 && op.nrhs != kSpmmCols) throw std::invalid_argument("nrhs must be 1 or 8");
     if (op.amg_coarse_bf16 != 0 && op.amg_coarse_bf16 != 1) throw std::invalid_argument("amg_coarse_bf16 must be 0 or 1");
     std::unique_ptr<scr_ctx> h(new scr_ctx());
@@ -1190,6 +1197,7 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
     SCR_CUDA(cudaStreamSynchronize(s));
     h->have_block = false;
     h->nbatch = 0;
+    if (!h->tangent_setup) h->ta.ready = false;  // new matrices: a new pattern for the tangent
     h->hA = Hierarchy();
     h->hS = Hierarchy();
     h->work.reset();
@@ -1969,7 +1977,10 @@ int scr_export(scr_handle h, int which, int level, int kind, scr_bsr_out* out) {
     const DBsr<double>* M = nullptr;
     if (kind == SCR_EXPORT_OPERATOR) M = &L.A;
     else if (kind == SCR_EXPORT_PROLONGATOR) M = &L.P;
-    else throw std::invalid_argument("scr_export: unknown kind");
+    else if (kind == SCR_EXPORT_BLOCK_B && level == 0 && h->have_block) M = &h->B;
+    else if (kind == SCR_EXPORT_BLOCK_C && level == 0 && h->have_block) M = &h->C;
+    else if (kind == SCR_EXPORT_BLOCK_D && level == 0 && h->have_block) M = &h->D;
+    else throw std::invalid_argument("scr_export: unknown kind (B, C, D: level 0 of a set-up block system)");
     out->nb_rows = M->nbr;
     out->nb_cols = M->nbc;
     out->br = M->br;
@@ -2000,6 +2011,7 @@ int scr_assembly_setup(scr_handle h, const scr_mesh* m, const scr_physics* ph) {
     cudaStream_t s = h->s;
     h->have_residual = false;
     h->have_coupling = false;  // a mesh coupling belongs to the previous mesh
+    h->ta.ready = false;
     h->rmats.reset(new DeviceArena(s));
     ResidualPhysics rp{ph->rho_f, ph->mu_f, ph->rho_s, ph->E_s / (2.0 * (1.0 + ph->nu_s)), ph->dt,
                        ph->c_m_solid, ph->c_c_solid};
@@ -2058,6 +2070,30 @@ int scr_assemble_residual(scr_handle h, const double* v, const double* vhat, con
 
 namespace {
 
+// Tangent at the state (device pointers) into the captured patterns, then
+// the set-up of the block solve on it (Shat, hierarchies, copies)
+void assemble_tangent_dev(scr_ctx* h, const double* v, const double* vhat, const double* p, const double* vd) {
+  cudaStream_t s = h->s;
+  if (!h->ta.ready) {
+    h->tmats.reset(new DeviceArena(s));
+    const DBsr<double>* mats[4] = {&h->A, &h->B, &h->C, &h->D};
+    h->ta.setup(h->ra, mats, *h->tmats, s);
+  }
+  const double rho = h->phys.rho_inf;
+  const double am = 0.5 * (3.0 - rho) / (1.0 + rho), af = 1.0 / (1.0 + rho), ga = af;
+  const double cf = af * ga * h->phys.dt, cu = cf * cf / am;
+  h->ta.evaluate(h->ra, h->d_dir, v, vhat, p, vd, am, cf, cu, s);
+  scr_bsr d[4];
+  for (int m = 0; m < 4; ++m) {
+    const TangentAssembler::Pattern& P = h->ta.pat[m];
+    d[m] = scr_bsr{P.nbr, P.nbc, P.br, P.bc, (int)P.nnzb, P.rp, P.col, P.val};
+  }
+  h->tangent_setup = true;
+  const int rc = scr_setup(h, &d[0], &d[1], &d[2], &d[3], 1);
+  h->tangent_setup = false;
+  if (rc != SCR_OK) throw std::runtime_error(std::string("set-up on the assembled tangent: ") + scr_last_error());
+}
+
 // mesh-motion arguments of scr_corrector_ale (null: the mesh stays fixed)
 struct AleArgs {
   const double* uhat_n;
@@ -2107,7 +2143,6 @@ int corrector_run(scr_handle h, double* v, double* p, double* vdot, double* u, i
       else fill<double>(h->d_vhn, 0.0, nf3, s);
     }
     double* R = h->r_in + 4 * nv3 + np;  // 3 n_nodes + n_p
-    ArnoldiState* st = h->gOuter.st;
     EpiArgs plain;
     for (int it = 0; it <= n_iter; ++it) {
       if (ale) {
@@ -2128,6 +2163,10 @@ int corrector_run(scr_handle h, double* v, double* p, double* vdot, double* u, i
         h->stats.mm_iters = mit;
         mesh_velocity(h->d_node_of_f, h->d_uh, h->d_uhn, h->d_vhn, af, ga, h->phys.dt, h->d_vhat, h->cpl_nf, s);
       }
+      // full Newton (options.newton): the tangent at this iteration's state
+      // and the set-up of the solve on it, before its right-hand side
+      if (h->o.newton && it < n_iter) assemble_tangent_dev(h, dv, ale ? h->d_vhat : nullptr, dp, dvd);
+      ArnoldiState* st = h->gOuter.st;
       h->ra.evaluate(dv, ale ? h->d_vhat : nullptr, dp, dvd, du, R, s);
       // resistance outlets: the traction P_j a_j with P_j = m_j (a_j^T v)
       // (the term whose derivative is the rank-1 tangent c_j a_j a_j^T,
@@ -2168,6 +2207,37 @@ int corrector_run(scr_handle h, double* v, double* p, double* vdot, double* u, i
 }
 
 }  // namespace
+
+int scr_assemble_tangent(scr_handle h, const double* v, const double* vhat, const double* p, const double* vdot,
+                         int dev) {
+  if (!h || !v || !p) return SCR_INVALID_ARG;
+  if (!h->have_block || !h->have_residual || h->nbatch || h->ra.nn != h->nv || h->ra.np != h->np) {
+    set_last_error("scr_assemble_tangent: needs scr_setup (not batched) and scr_assembly_setup on the same mesh");
+    return SCR_INVALID_ARG;
+  }
+  return guarded([&] {
+    cudaStream_t s = h->s;
+    const long long nv3 = 3LL * h->nv, np = h->np;
+    const double *dv = v, *dvh = vhat, *dp = p, *dvd = vdot;
+    if (!dev) {
+      double* b = h->r_in;
+      SCR_CUDA(cudaMemcpyAsync(b, v, sizeof(double) * nv3, cudaMemcpyHostToDevice, s));
+      dv = b;
+      if (vhat) {
+        SCR_CUDA(cudaMemcpyAsync(b + nv3, vhat, sizeof(double) * nv3, cudaMemcpyHostToDevice, s));
+        dvh = b + nv3;
+      }
+      if (vdot) {
+        SCR_CUDA(cudaMemcpyAsync(b + 2 * nv3, vdot, sizeof(double) * nv3, cudaMemcpyHostToDevice, s));
+        dvd = b + 2 * nv3;
+      }
+      SCR_CUDA(cudaMemcpyAsync(b + 4 * nv3, p, sizeof(double) * np, cudaMemcpyHostToDevice, s));
+      dp = b + 4 * nv3;
+    }
+    assemble_tangent_dev(h, dv, dvh, dp, dvd);
+    SCR_CUDA(cudaStreamSynchronize(s));
+  });
+}
 
 int scr_corrector(scr_handle h, double* v, double* p, double* vdot, double* u, int n_iter, double* res_norms,
                   int dev) {

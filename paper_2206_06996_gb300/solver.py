@@ -234,6 +234,17 @@ class BlockSolver:
         check(self.lib.scr_assemble_residual(self.h, vp(pv), vp(opt[0]), vp(pp), vp(opt[1]), vp(opt[2]), vp(pr), dev))
         return R
 
+    def assemble_tangent(self, v, p, vhat=None, vdot=None):
+        """Assemble the tangent blocks A, B, C, D on the GPU at the state and
+        set the block solve up on them (scr_assemble_tangent); numpy arrays or
+        CUDA tensors."""
+        keep: list = []
+        pv, dev = _ptr(v, keep)
+        pp, _ = _ptr(p, keep)
+        opt = [(_ptr(a, keep)[0] if a is not None else None) for a in (vhat, vdot)]
+        vp = lambda a: None if a is None else C.c_void_p(a)
+        check(self.lib.scr_assemble_tangent(self.h, vp(pv), vp(opt[0]), vp(pp), vp(opt[1]), dev))
+
     def corrector(self, v, p, vdot, u, n_iter: int):
         """n_iter multi-corrector iterations on the state (updated in place:
         numpy arrays or CUDA tensors); returns the residual norms."""
@@ -406,7 +417,7 @@ class BlockSolver:
     def export(self, which: int, level: int, kind: int):
         """Copy a hierarchy operator / prolongator (block CSR, numpy), the
         aggregates or the aggregates' roots (int arrays) to the host."""
-        from .abi import SCR_EXPORT_AGGREGATES, SCR_EXPORT_ROOTS
+        from .abi import SCR_EXPORT_AGGREGATES, SCR_EXPORT_ROOTS  # noqa: F401
         o = BsrOut()
         check(self.lib.scr_export(self.h, which, level, kind, C.byref(o)))
         if kind in (SCR_EXPORT_AGGREGATES, SCR_EXPORT_ROOTS):

@@ -12,6 +12,7 @@ Every call goes through the C ABI (the thin binding).  Tolerances:
 import numpy as np
 import pytest
 import scipy.sparse as sp
+import scipy.sparse.linalg as spl
 
 import fsi_inputs as F
 from mis2_check import check_mis2_aggregation
@@ -975,6 +976,137 @@ def test_gpu_corrector_ale_matches_the_oracle_loop(small, precision):
     assert np.abs(uh).max() > 1e-6
     np.testing.assert_array_equal(norms, norms_d)
     np.testing.assert_array_equal(uh, uh_d.cpu().numpy())
+
+
+def _gpu_blocks(sol):
+    A = to_csr(sol.export(pkg.SCR_HIER_A, 0, pkg.SCR_EXPORT_OPERATOR))
+    B, C, D = (to_csr(sol.export(pkg.SCR_HIER_A, 0, k))
+               for k in (pkg.SCR_EXPORT_BLOCK_B, pkg.SCR_EXPORT_BLOCK_C, pkg.SCR_EXPORT_BLOCK_D))
+    return A, B, C, D
+
+
+def _moved_state(s, asm, seed):
+    v0, p0 = asm.initial_state()
+    rng = np.random.default_rng(seed)
+    nn = s.mesh.n_nodes
+    v = v0 + 2.0 * rng.standard_normal(v0.size)
+    p = p0 + 10.0 * rng.standard_normal(p0.size)
+    vd = 50.0 * rng.standard_normal(3 * nn)
+    vh = rng.standard_normal(3 * nn)
+    return v, p, vd, vh
+
+
+@pytest.mark.parametrize("preset", ["tube_mini", "tube_small", "bif_mini"])
+def test_gpu_tangent_matches_the_oracle_at_a_moved_state(preset):
+    """The GPU's tangent assembly (one thread per element column, summed per
+    stored block in element order) at a state away from the assembly state
+    (perturbed velocity, pressure, mesh velocity and rates) equals the
+    oracle's Jacobian there (the generator's element tangent with tau frozen,
+    the Dirichlet convention applied) to FP64 rounding, block by block; the
+    solve on it meets the direct solve of that Jacobian."""
+    from oracle import corrector
+    s = F.tube_system(preset, keep_mesh=True)
+    asm = F.Assembler(F.make_params(**F.PRESETS[preset]))
+    v, p, vd, vh = _moved_state(s, asm, 17)
+    want = corrector.tangent(s, asm, v, p, vd, vh)
+    with pkg.BlockSolver() as sol:
+        sol.setup(s.A, s.B, s.C, s.D)
+        sol.assembly_setup(s.mesh, s.params)
+        sol.assemble_tangent(v, p, vhat=vh, vdot=vd)
+        got = _gpu_blocks(sol)
+        x = sol.solve(s.b.copy())
+        # the same from device pointers
+        sol.assemble_tangent(_dev(v), _dev(p), vhat=_dev(vh), vdot=_dev(vd))
+        got_d = _gpu_blocks(sol)
+    for g, w, gd in zip(got, want, got_d):
+        assert g.shape == w.shape
+        assert abs(g - w).max() <= 1e-12 * abs(w).max()
+        assert abs(g - gd).max() == 0
+    K = sp.bmat([[want[0], want[1]], [want[2], want[3]]], format="csc")
+    xd = spl.spsolve(K, s.b)
+    assert np.linalg.norm(K @ x - s.b) <= 1e-8 * np.linalg.norm(s.b)
+    assert _rel(x, xd) <= 1e-6
+
+
+def test_gpu_tangent_at_the_assembly_state_is_the_input_system(small):
+    """At the generator's assembly state the GPU's tangent is the input block
+    system itself (the patterns kept, Dirichlet rows identity)."""
+    asm = F.Assembler(F.make_params(**F.PRESETS["tube_small"]))
+    v0, p0 = asm.initial_state()
+    with pkg.BlockSolver() as sol:
+        sol.setup(small.A, small.B, small.C, small.D)
+        sol.assembly_setup(small.mesh, small.params)
+        sol.assemble_tangent(v0, p0)
+        got = _gpu_blocks(sol)
+    for g, w in zip(got, (small.A, small.B, small.C, small.D)):
+        w = to_csr(w)
+        assert abs(g - w).max() <= 1e-12 * abs(w).max()
+
+
+@pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
+def test_gpu_newton_corrector_matches_the_oracle_loop(small, precision):
+    """The multi-corrector with the tangent re-assembled on the GPU at every
+    iteration (option newton) follows the oracle's loop that re-assembles
+    the generator's tangent and solves directly: same starting residual, same
+    residuals up to the solves' tolerance, the same final state."""
+    from oracle import corrector
+    s = small
+    asm = F.Assembler(F.make_params(**F.PRESETS["tube_small"]))
+    v0, p0 = asm.initial_state()
+    z = np.zeros(3 * s.mesh.n_nodes)
+    vr, pr, vdr, ur, nr = corrector.corrector(s, asm, v0, p0, z, z, 3, newton=True)
+    with pkg.BlockSolver(precision=precision, newton=1) as sol:
+        sol.setup(s.A, s.B, s.C, s.D)
+        sol.assembly_setup(s.mesh, s.params)
+        v, p, vd, u = v0.copy(), p0.copy(), z.copy(), z.copy()
+        norms = sol.corrector(v, p, vd, u, 3)
+        dv, dp, dvd, du = (_dev(a) for a in (v0, p0, z, z))
+        norms_d = sol.corrector(dv, dp, dvd, du, 3)
+    assert norms[0] == pytest.approx(nr[0], rel=1e-12)
+    assert norms[1] == pytest.approx(nr[1], rel=1e-3)
+    assert norms[2] < 1e-2 * norms[1]
+    for a, b in ((v, vr), (p, pr), (vd, vdr), (u, ur)):
+        assert _rel(a, b) < 1e-7
+    np.testing.assert_array_equal(norms, norms_d)
+
+
+@pytest.mark.parametrize("precision", [pkg.SCR_FP64])
+def test_gpu_newton_corrector_ale_matches_the_oracle_loop(small, precision):
+    """The same with the mesh moving inside the loop: the tangent at each
+    iteration sees that iteration's mesh velocity."""
+    from oracle import corrector
+    from oracle.sparse import to_csr as tc
+    s = small
+    m = s.mesh
+    asm = F.Assembler(F.make_params(**F.PRESETS["tube_small"]))
+    L_raw = asm.mesh_laplacian()
+    follow = F.interface_follow(m)
+    v0, p0 = asm.initial_state()
+    z, zf = np.zeros(3 * m.n_nodes), np.zeros(3 * m.n_fluid)
+    vn = 0.01 * np.random.default_rng(4).standard_normal(3 * m.n_fluid)
+    vr, pr, vdr, ur, uhr, nr = corrector.corrector_ale(s, asm, v0, p0, z, z, 3, tc(L_raw), m.fluid_id,
+                                                       m.dir_m, follow, zf, vn, newton=True)
+    with pkg.BlockSolver(precision=precision, newton=1) as sol:
+        sol.setup(s.A, s.B, s.C, s.D)
+        sol.assembly_setup(m, s.params)
+        sol.mesh_setup(s.L)
+        sol.mesh_coupling(L_raw, m.fluid_id, m.dir_m, follow)
+        v, p, vd, u = v0.copy(), p0.copy(), z.copy(), z.copy()
+        norms, uh = sol.corrector_ale(v, p, vd, u, zf, 3, vhat_n=vn)
+    assert norms[0] == pytest.approx(nr[0], rel=1e-12)
+    assert norms[1] == pytest.approx(nr[1], rel=1e-3)
+    for a, b in ((v, vr), (p, pr), (vd, vdr), (u, ur), (uh, uhr)):
+        assert _rel(a, b) < 1e-7
+
+
+def test_gpu_tangent_needs_both_set_ups(small):
+    with pkg.BlockSolver() as sol:
+        sol.setup(small.A, small.B, small.C, small.D)
+        v, p = np.zeros(3 * small.n_v), np.zeros(small.n_p)
+        with pytest.raises(pkg.ScrError, match="scr_assembly_setup"):
+            sol.assemble_tangent(v, p)
+    with pytest.raises(pkg.ScrError):
+        pkg.BlockSolver(newton=2)
 
 
 def test_gpu_corrector_ale_rejects_a_missing_coupling(small):

@@ -827,3 +827,76 @@ def test_scr_with_fixed_count_a_solves_matches_direct(mini_system, mini_direct, 
     assert np.linalg.norm(out["x"] - mini_direct) <= 1e-6 * np.linalg.norm(mini_direct)
     assert out["counters"].i_iters % inner == 0
 
+
+# ---------------------------------------------------------------- tangent at a state
+def test_tangent_at_the_initial_state_is_the_input_system():
+    """The oracle's Jacobian at a state, at the generator's assembly state,
+    equals the block system the input module builds (the same element loop
+    and the same Dirichlet convention: identity rows of A, rows of B and
+    columns of A and C removed at Dirichlet velocity nodes)."""
+    from oracle import corrector
+    s = F.tube_system("tube_mini", keep_mesh=True)
+    asm = F.Assembler(F.make_params(**F.PRESETS["tube_mini"]))
+    v, p = asm.initial_state()
+    A, B, C, D = corrector.tangent(s, asm, v, p)
+    for got, want in ((A, s.A), (B, s.B), (C, s.C), (D, s.D)):
+        w = to_csr(want)
+        assert abs(got - w).max() <= 1e-14 * abs(w).max()
+    dv = np.repeat(s.mesh.dir_v, 3)
+    assert np.all(A.diagonal()[dv] == 1.0)
+    assert abs(A[dv][:, ~dv]).max() == 0 and abs(A[~dv][:, dv]).max() == 0
+    assert abs(B[dv]).max() == 0 and abs(C[:, dv]).max() == 0
+
+
+def test_tangent_is_the_derivative_of_the_residual_at_a_moved_state():
+    """At a state away from the assembly state (perturbed velocity, pressure,
+    mesh velocity, rates and solid displacement), the tangent's action on an
+    increment equals the central difference of the residual along the
+    generalized-alpha update of that increment (rates by alpha_m, values by
+    alpha_f gamma dt, the displacement by (alpha_f gamma dt)^2 / alpha_m),
+    with tau frozen at the state: free rows of the momentum and mass
+    residuals."""
+    from oracle import corrector
+    s = F.tube_system("tube_mini", keep_mesh=True)
+    asm = F.Assembler(F.make_params(**F.PRESETS["tube_mini"]))
+    v0, p0 = asm.initial_state()
+    rng = np.random.default_rng(11)
+    nn = s.mesh.n_nodes
+    v = v0 + 2.0 * rng.standard_normal(v0.size)
+    p = p0 + 10.0 * rng.standard_normal(p0.size)
+    vd = 50.0 * rng.standard_normal(3 * nn)
+    vh = 1.0 * rng.standard_normal(3 * nn)
+    A, B, C, D = corrector.tangent(s, asm, v, p, vd, vh)
+    am, cf, cu = corrector.genalpha_weights(s.params["rho_inf"], s.params["dt"])
+    dv = np.repeat(s.mesh.dir_v, 3)
+    xv = rng.standard_normal(3 * nn)
+    xv[dv] = 0.0
+    xp = rng.standard_normal(p.size)
+    tau = np.zeros(8 * s.mesh.n_elem)
+    asm.evaluate(v, p, vd=vd, vhat=vh, tau=tau, tau_mode=1, want_mat=False)
+    h = 1e-4  # the increments are scaled by alpha_f gamma dt: the state moves by about 1e-8
+    u = 1e-3 * rng.standard_normal(3 * nn)
+    R = [asm.evaluate(v + sg * h * cf * xv, p + sg * h * cf * xp, vd=vd + sg * h * am * xv,
+                      u=u + sg * h * cu * xv, vhat=vh, tau=tau, tau_mode=2, want_mat=False) for sg in (1.0, -1.0)]
+    dRm = (R[0]["Rm"] - R[1]["Rm"]) / (2 * h)
+    dRp = (R[0]["Rp"] - R[1]["Rp"]) / (2 * h)
+    Km = A @ xv + B @ xp
+    Kp = C @ xv + D @ xp
+    assert np.linalg.norm(Km[~dv] - dRm[~dv]) <= 1e-6 * np.linalg.norm(dRm[~dv])
+    assert np.linalg.norm(Kp - dRp) <= 1e-6 * np.linalg.norm(dRp)
+
+
+def test_newton_corrector_first_step_is_the_frozen_one_and_it_contracts():
+    """Re-assembling the tangent at every iteration: the first iteration
+    uses the tangent at the initial state, so it matches the frozen-tangent
+    loop; later iterations keep contracting the residual."""
+    from oracle import corrector
+    s = F.tube_system("tube_mini", keep_mesh=True)
+    asm = F.Assembler(F.make_params(**F.PRESETS["tube_mini"]))
+    v, p = asm.initial_state()
+    z = np.zeros(3 * s.mesh.n_nodes)
+    *_, nf = corrector.corrector(s, asm, v, p, z, z, 1)
+    *_, nn_ = corrector.corrector(s, asm, v, p, z, z, 3, newton=True)
+    assert nn_[0] == pytest.approx(nf[0], rel=1e-14) and nn_[1] == pytest.approx(nf[1], rel=1e-9)
+    assert nn_[2] < 1e-2 * nn_[1] and nn_[3] < nn_[2]
+
