@@ -528,7 +528,7 @@ def main(argv=None):
     # ---------------------------------------------------------- optional legs on the headline tube
     batched = None
     if args.batched:
-        batched = batched_leg(args, pkg, F, torch, dev, timed)
+        batched = batched_leg(args, pkg, F, torch, dev, timed, pg, world, rank)
     assembly = None
     if args.assembly:
         assembly = assembly_leg(args, pkg, F, torch, dev, stream, s)
@@ -648,19 +648,46 @@ def bifurcation_leg(args, pkg, F, torch, np, dev, stream, events, barrier, pg, a
     return out
 
 
-def batched_leg(args, pkg, F, torch, dev, timed):
+def gather_members(pg, world: int, mine: list[int], values: list, n: int) -> list:
+    """Per-member results of every rank, in member order: rank r holds the
+    members `mine` (its part of split_members) with `values`; returns the n
+    values on every rank (all_gather of the (index, value) pairs)."""
+    pairs = list(zip(mine, values))
+    if pg is None or world == 1:
+        got = [pairs]
+    else:
+        got = [None] * world
+        pg.all_gather_object(got, pairs)
+    out = [None] * n
+    for part in got:
+        for i, v in part:
+            out[i] = v
+    return out
+
+
+def batched_leg(args, pkg, F, torch, dev, timed, pg=None, world=1, rank=0):
     """The 64-tube batch: one block-diagonal set-up + solve of all members
     against the same members set up and solved one after another, in the
     same precision (FP64 and mixed).  The one-by-one runs reuse the
     autotuner's decisions of a first pass (the members' shapes are
     distinct, so without the cache every member would time its kernels),
-    with set-up and solve times reported apart."""
+    with set-up and solve times reported apart.  With N ranks the members
+    are split by unknowns (split_members) and each rank solves its own part
+    as one union; the per-member residuals are gathered in member order and
+    the job time is the slowest rank's (no collective on the data path)."""
     import numpy as np
-    members = [F.tube_system("batch", **F.batch_member_params(i)) for i in range(64)]
+    params = [F.batch_member_params(i) for i in range(64)]
+    # nodes of a member: a centre node plus n_circ x (lumen + wall rings) per
+    # section, n_ax + 1 sections (the unknowns grow in proportion)
+    sizes = [(1 + p["n_circ"] * (p["n_rad_f"] + p["n_rad_s"])) * (p["n_ax"] + 1) for p in params]
+    mine = split_members(sizes, world)[rank]
+    members = [F.tube_system("batch", **params[i]) for i in mine]
     devm = [tuple(pkg.DeviceBSR.from_host(M, device=dev) for M in (m.A, m.B, m.C, m.D)) for m in members]
     bsd = [torch.as_tensor(m.b, device=dev) for m in members]
     xsd = [torch.empty_like(b) for b in bsd]
-    out = {"members": 64, "nodes": int(sum(m.n_v for m in members)), "unknowns": int(sum(m.n for m in members))}
+    out = {"members": 64, "members_this_rank": len(mine), "split": "by unknowns over ranks" if world > 1 else "none",
+           "nodes_this_rank": int(sum(m.n_v for m in members)),
+           "unknowns_this_rank": int(sum(m.n for m in members))}
     for name, prec in (("fp64", pkg.SCR_FP64), ("mixed", pkg.SCR_MIXED)):
         solb = pkg.BlockSolver(precision=prec)
 
@@ -670,7 +697,7 @@ def batched_leg(args, pkg, F, torch, dev, timed):
 
         step_batch(solb)
         msb, _ = timed(solb, step_batch, max(1, min(args.steps, 3)))
-        relb = solb.batch_residuals()
+        relb = gather_members(pg, world, mine, [float(r) for r in solb.batch_residuals()], 64)
         solb.close()
         sols = pkg.BlockSolver(precision=prec)
         setup_ms = solve_ms = 0.0
@@ -688,7 +715,8 @@ def batched_leg(args, pkg, F, torch, dev, timed):
         step_seq(sols)  # first pass: the autotuner times each member's shapes once
         mss, _ = timed(sols, step_seq, 1)
         sols.close()
-        out[name] = {"batched_ms": msb, "members_per_s": 64 * 1000.0 / msb, "one_by_one_ms": mss,
+        msb_job = allmax(pg, msb, dev)
+        out[name] = {"batched_ms": msb_job, "members_per_s": 64 * 1000.0 / msb_job, "one_by_one_ms": allmax(pg, mss, dev),
                      "one_by_one_setup_ms": setup_ms, "one_by_one_solve_ms": solve_ms,
                      "speedup_vs_one_by_one": mss / msb, "max_member_rel_res": float(np.max(relb))}
     return out
@@ -734,7 +762,31 @@ def assembly_leg(args, pkg, F, torch, dev, stream, s_head):
     torch.cuda.synchronize(dev)
     mesh_it, _ = sola.mesh_iters()
     sola.close()
+    # the tangent on the GPU (element tangents + per-block sums) followed by
+    # the set-up of the solve on it, and one full-Newton corrector iteration
+    # (tangent re-assembled at the iteration's state)
+    solt = pkg.BlockSolver(newton=1)
+    solt.setup(Ad, Bd, Cd, Dd)
+    solt.assembly_setup(sm.mesh, sm.params)
+    solt.assemble_tangent(vt, pt)
+    torch.cuda.synchronize(dev)
+    ea.record(stream)
+    solt.assemble_tangent(vt, pt)
+    eb.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_tan = ea.elapsed_time(eb)
+    setup_tan = solt.stats()["setup_ms"]
+    vc, pc, vdc, uc = vt.clone(), pt.clone(), vd0.clone(), vd0.clone()
+    torch.cuda.synchronize(dev)
+    ea.record(stream)
+    norms_nt = solt.corrector(vc, pc, vdc, uc, 2)
+    eb.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_nt = ea.elapsed_time(eb) / 2
+    solt.close()
     return {"elements": int(sm.mesh.n_elem), "residual_ms": ms_res, "elements_per_s": sm.mesh.n_elem * 1000.0 / ms_res,
+            "tangent_and_setup_ms": ms_tan, "tangent_ms": ms_tan - setup_tan,
+            "newton_iteration_ms": ms_nt, "newton_residuals": [float(x) for x in norms_nt],
             "corrector_iteration_ms": ms_corr, "corrector_residual_drop": float(norms[1] / norms[0]),
             "corrector_ale_iteration_ms": ea.elapsed_time(eb),
             "corrector_ale_residual_drop": float(norms_ale[1] / norms_ale[0]),

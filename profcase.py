@@ -7,7 +7,9 @@ builds the 96 x (11 + 5) tube with `--n-ax` axial layers (100 layers:
 with the autotuner off (every product with the kernel `--group`, default
 the scalar-row kernel with 2 lanes per row) and applies `--reps` V-cycles of
 the A hierarchy; `--what solve` runs one full block solve instead, `--what
-residual` evaluates the GPU residual assembly (element loop) `--reps` times.  A
+residual` evaluates the GPU residual assembly (element loop) `--reps` times,
+`--what tangent` the GPU tangent assembly (element tangents, per-block sums
+and the set-up of the solve on them) `--reps` times.  A
 profiler capture of one kernel family (for example `k_spmv<3, 3, 1, 2,
 double`) then sees only launches of that family on this moderate case.
 """
@@ -27,7 +29,7 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--n-ax", type=int, default=100)
     ap.add_argument("--reps", type=int, default=2)
-    ap.add_argument("--what", choices=["vcycle", "solve", "residual"], default="vcycle")
+    ap.add_argument("--what", choices=["vcycle", "solve", "residual", "tangent"], default="vcycle")
     ap.add_argument("--group", type=int, default=102,
                     help="product kernel code for every matrix (102: scalar-row kernel, 2 lanes per row)")
     args = ap.parse_args()
@@ -36,6 +38,20 @@ def main():
     import fsi_inputs as F
     import paper_2206_06996_gb300 as pkg
 
+    if args.what == "tangent":
+        s = F.tube_system("tube_large", n_ax=args.n_ax, keep_mesh=True)
+        asm = F.Assembler(F.make_params(**{**F.PRESETS["tube_large"], "n_ax": args.n_ax}))
+        v0, p0 = asm.initial_state()
+        asm.close()
+        with pkg.BlockSolver() as sol:
+            sol.setup(s.A, s.B, s.C, s.D)
+            sol.assembly_setup(s.mesh, s.params)
+            v, p = torch.as_tensor(v0, device="cuda"), torch.as_tensor(p0, device="cuda")
+            for _ in range(args.reps):
+                sol.assemble_tangent(v, p)
+            torch.cuda.synchronize()
+        print("ok", s.mesh.n_elem)
+        return
     if args.what == "residual":
         # the element loop on the same mesh: --reps residual evaluations
         s = F.tube_system("tube_large", n_ax=args.n_ax, keep_mesh=True)

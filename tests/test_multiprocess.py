@@ -20,6 +20,47 @@ def _free_port() -> int:
         return s.getsockname()[1]
 
 
+def _members_rank(rank: int, world: int, port: int, out):
+    """A rank of the batched workload's split: solves nothing, but returns
+    per-member values computed from the member index, which the gather must
+    put back in member order on every rank."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import bench
+    w, r, local, pg = bench.dist_init("gloo")
+    try:
+        sizes = [(i * 37) % 11 + 1 for i in range(20)]
+        parts = bench.split_members(sizes, w)
+        mine = parts[r]
+        vals = [1e-9 * (i + 1) for i in mine]
+        full = bench.gather_members(pg, w, mine, vals, len(sizes))
+        out.put((r, mine, full))
+    finally:
+        pg.destroy_process_group()
+
+
+def test_two_ranks_split_the_members_and_gather_their_residuals():
+    """World size 2 on gloo: the two ranks take disjoint parts of the members
+    that together cover all of them, and both reassemble the per-member
+    values in member order."""
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_members_rank, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(out.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, m0, f0), (r1, m1, f1) = res
+    assert (r0, r1) == (0, 1)
+    assert sorted(m0 + m1) == list(range(20)) and not set(m0) & set(m1)
+    want = [1e-9 * (i + 1) for i in range(20)]
+    assert f0 == want and f1 == want
+
+
 def _rank(rank: int, world: int, port: int, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
                       LOCAL_RANK=str(rank))
