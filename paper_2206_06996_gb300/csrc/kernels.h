@@ -105,6 +105,8 @@ void set_forced_group(int code);
 int forced_group();
 // CTAs ahead for the L2 prefetch of the scalar-row products (0: off)
 void set_l2_prefetch(int ctas);
+// programmatic dependent launch of the product kernels (0: off)
+void set_pdl(int on);
 // print every autotune decision to stderr (0: quiet)
 void set_tune_verbose(int v);
 // write / read the autotune cache as text (throw std::invalid_argument)

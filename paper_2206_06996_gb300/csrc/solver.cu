@@ -1122,6 +1122,7 @@ int scr_default_opts(scr_opts* o) {
   o->inner_vcycles = 0;
   o->inter_vcycles = 0;
   o->newton = 0;
+  o->pdl = 1;
   o->l2_prefetch = 192;
   o->amg_coarse_bf16 = 1;
   o->cuda_graphs = 1;
@@ -1155,12 +1156,14 @@ int scr_create(scr_handle* out, const scr_opts* o, void* stream) {
     if (op.inner_vcycles < 0 || op.inner_vcycles > 64 || op.inter_vcycles < 0 || op.inter_vcycles > 64)
       throw std::invalid_argument("inner_vcycles and inter_vcycles must lie in [0, 64]");
     if (op.newton != 0 && op.newton != 1) throw std::invalid_argument("newton must be 0 or 1");
+    if (op.pdl != 0 && op.pdl != 1) throw std::invalid_argument("pdl must be 0 or 1");
     if (op.nrhs != 1 && op.nrhs != kSpmmCols) throw std::invalid_argument("nrhs must be 1 or 8");
     if (op.amg_coarse_bf16 != 0 && op.amg_coarse_bf16 != 1) throw std::invalid_argument("amg_coarse_bf16 must be 0 or 1");
     std::unique_ptr<scr_ctx> h(new scr_ctx());
     h->o = op;
     set_forced_group(op.spmv_group);
     set_l2_prefetch(op.l2_prefetch);
+    set_pdl(op.pdl);
     set_tune_verbose(op.verbose);
     h->s = static_cast<cudaStream_t>(stream);
     SCR_CUDA(cudaGetDevice(&h->device));

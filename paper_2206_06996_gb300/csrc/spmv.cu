@@ -228,6 +228,9 @@ template void build_vec<float>(DBsr<float>&, DeviceArena&, cudaStream_t);
 // FP64 241 -> 229 us); 1536 and more were slower than none.
 int g_l2_prefetch = 192;
 void set_l2_prefetch(int ctas) { g_l2_prefetch = ctas; }
+// programmatic dependent launch of the product kernels (options.pdl)
+int g_pdl = 1;
+void set_pdl(int on) { g_pdl = on; }
 // print every autotune decision with the candidates' times (options.verbose)
 static int g_tune_verbose = 0;
 void set_tune_verbose(int v) { g_tune_verbose = v; }

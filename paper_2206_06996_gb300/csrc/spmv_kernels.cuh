@@ -18,6 +18,17 @@
 
 namespace scr {
 
+// Programmatic dependent launch (option pdl): a product kernel lets the next
+// kernel of the stream start as soon as all of its CTAs are running
+// (griddepcontrol.launch_dependents), and, before it reads anything an
+// earlier kernel wrote, waits for that kernel to complete with its memory
+// visible (griddepcontrol.wait).  Between the two it only prefetches its own
+// rows of the stored matrix into L2 (read-only data), so the matrix stream
+// of one product overlaps the tail of the previous one.  Launched without
+// the attribute, both instructions return at once.
+__device__ __forceinline__ void pdl_allow_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ------------------------------------------------------------ SpMV
 // accumulate one scalar row r of block row i of M into acc[h]; the lanes of
 // a G-group take the row's blocks in turn (BC values each, contiguous in the
@@ -99,7 +110,11 @@ __global__ void __launch_bounds__(256, SCR_SPMV_MINBLOCKS) k_spmv(int nbr, const
   const long long o = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;  // scalar row
   const int lane = threadIdx.x % G;
   const long long nrows = (long long)nbr * BR;
-  if (pf > 0 && threadIdx.x == 0) l2_prefetch_rows<BR, BC, G, VT>(rp, col, val, nbr, blockIdx.x + (long long)pf);
+  const int ahead = pf < 0 ? -pf - 1 : pf;
+  pdl_allow_next();
+  if (pf < 0 && threadIdx.x == 0) l2_prefetch_rows<BR, BC, G, VT>(rp, col, val, nbr, blockIdx.x);
+  pdl_wait_prev();
+  if (ahead > 0 && threadIdx.x == 0) l2_prefetch_rows<BR, BC, G, VT>(rp, col, val, nbr, blockIdx.x + (long long)ahead);
   const bool active = o < nrows;  // inactive lanes still join the shuffles
   AT acc[NRHS];
 #pragma unroll
@@ -263,8 +278,15 @@ __global__ void __launch_bounds__(256) k_spmv_vec33(int nbr, const int4* __restr
   constexpr int U = V;
   const long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;
   const int lane = threadIdx.x % G;
-  if (pf > 0 && threadIdx.x == 0) {
-    const long long i0 = (blockIdx.x + (long long)pf) * (256 / G);
+  const int ahead = pf < 0 ? -pf - 1 : pf;
+  pdl_allow_next();
+  if (pf < 0 && threadIdx.x == 0) {
+    const long long i0 = blockIdx.x * (long long)(256 / G);
+    if (i0 < nbr) l2_prefetch_vec<VT, true>(desc, col, val, i0, i0 + 256 / G < nbr ? i0 + 256 / G : nbr);
+  }
+  pdl_wait_prev();
+  if (ahead > 0 && threadIdx.x == 0) {
+    const long long i0 = (blockIdx.x + (long long)ahead) * (256 / G);
     if (i0 < nbr) l2_prefetch_vec<VT, true>(desc, col, val, i0, i0 + 256 / G < nbr ? i0 + 256 / G : nbr);
   }
   const bool active = i < nbr;  // inactive lanes still join the shuffles
@@ -328,8 +350,15 @@ __global__ void __launch_bounds__(256) k_spmv_vec11(int nbr, const int2* __restr
   constexpr int V = 16 / (int)sizeof(VT);
   const long long i = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / G;
   const int lane = threadIdx.x % G;
-  if (pf > 0 && threadIdx.x == 0) {
-    const long long i0 = (blockIdx.x + (long long)pf) * (256 / G);
+  const int ahead = pf < 0 ? -pf - 1 : pf;
+  pdl_allow_next();
+  if (pf < 0 && threadIdx.x == 0) {
+    const long long i0 = blockIdx.x * (long long)(256 / G);
+    if (i0 < nbr) l2_prefetch_vec<VT, false>(desc, col, val, i0, i0 + 256 / G < nbr ? i0 + 256 / G : nbr);
+  }
+  pdl_wait_prev();
+  if (ahead > 0 && threadIdx.x == 0) {
+    const long long i0 = (blockIdx.x + (long long)ahead) * (256 / G);
     if (i0 < nbr) l2_prefetch_vec<VT, false>(desc, col, val, i0, i0 + 256 / G < nbr ? i0 + 256 / G : nbr);
   }
   const bool active = i < nbr;
@@ -408,6 +437,35 @@ __global__ void __launch_bounds__(256) k_sell_spmv(DSell<VT> S, const XT* __rest
 // CTAs ahead for the L2 prefetch of the scalar-row kernel (0: off) and the
 // forced kernel code of every product (0: per matrix); defined in spmv.cu
 extern int g_l2_prefetch;
+// launch the product kernels with programmatic stream serialization (option pdl)
+extern int g_pdl;
+
+// kern<<<grid, blk, 0, s>>>(args...), with the programmatic-serialization
+// attribute when g_pdl is set (the kernel then starts before its
+// predecessor completes and waits for it in griddepcontrol.wait); the
+// prefetch argument pf is passed negated under PDL, which makes the kernel
+// prefetch its own rows before it waits
+template <typename... KArgs, typename... Args>
+inline void launch_product(void (*kern)(KArgs...), long long grid, int blk, cudaStream_t s, Args... args) {
+  if (g_pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)blk);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SCR_CUDA(cudaLaunchKernelEx(&cfg, kern, args...));
+  } else {
+    kern<<<(unsigned)grid, blk, 0, s>>>(args...);
+  }
+}
+// the kernels' prefetch argument: pf >= 0: pf CTAs ahead; pf < 0 (PDL): the
+// CTA's own rows before the wait, then -pf - 1 CTAs ahead
+inline int pf_arg() { return g_pdl ? -g_l2_prefetch - 1 : g_l2_prefetch; }
 
 template <int BR, int BC, int NRHS, int G, typename VT, typename XT, typename AT, Epi E>
 inline void launch_spmv_g(const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& e, cudaStream_t s) {
@@ -418,12 +476,12 @@ inline void launch_spmv_g(const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& 
     if (M.vdesc && code_of(M) >= 300) {
       if constexpr (BR == 3) {
         const long long threads = (long long)M.nbr * G;
-        k_spmv_vec33<G, VT, XT, E><<<ceil_div(threads, blk), blk, 0, s>>>(
-            M.nbr, static_cast<const int4*>(M.vdesc), M.vcol, M.vval, x, epi, g_l2_prefetch);
+        launch_product(k_spmv_vec33<G, VT, XT, E>, ceil_div(threads, blk), blk, s, M.nbr,
+                       static_cast<const int4*>(M.vdesc), (const int*)M.vcol, (const VT*)M.vval, x, epi, pf_arg());
       } else {
         const long long threads = (long long)M.nbr * G;
-        k_spmv_vec11<G, VT, XT, E><<<ceil_div(threads, blk), blk, 0, s>>>(
-            M.nbr, static_cast<const int2*>(M.vdesc), M.vcol, M.vval, x, epi, g_l2_prefetch);
+        launch_product(k_spmv_vec11<G, VT, XT, E>, ceil_div(threads, blk), blk, s, M.nbr,
+                       static_cast<const int2*>(M.vdesc), (const int*)M.vcol, (const VT*)M.vval, x, epi, pf_arg());
       }
       done = true;
     }
@@ -444,8 +502,8 @@ inline void launch_spmv_g(const DBsr<VT>& M, const XT* x, XT* y, const EpiArgs& 
   }
   if (!done) {
     const long long threads = (long long)M.nbr * BR * G;
-    k_spmv<BR, BC, NRHS, G, VT, XT, AT, E><<<ceil_div(threads, blk), blk, 0, s>>>(M.nbr, M.rp, M.col, M.val, x, epi,
-                                                                                  g_l2_prefetch);
+    launch_product(k_spmv<BR, BC, NRHS, G, VT, XT, AT, E>, ceil_div(threads, blk), blk, s, M.nbr, (const int*)M.rp,
+                   (const int*)M.col, (const VT*)M.val, x, epi, pf_arg());
   }
   SCR_LAUNCH();
 }

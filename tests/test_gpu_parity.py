@@ -376,6 +376,30 @@ def test_cuda_graph_vcycles_equal_eager_vcycles(small, precision):
 
 
 @pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
+@pytest.mark.parametrize("graphs", [0, 1])
+def test_programmatic_dependent_launch_changes_no_result(small, precision, graphs):
+    """With the product kernels launched under programmatic stream
+    serialization (each waits for its predecessor before reading a vector,
+    after prefetching its own matrix rows), V-cycles of A, Shat and L and a
+    whole solve are bit-identical to ordinary launches, eager and from CUDA
+    graphs, with the scalar-row and the 16-byte kernels."""
+    for code in (0, 304):
+        res = []
+        for pdl in (0, 1):
+            with pkg.BlockSolver(pdl=pdl, cuda_graphs=graphs, precision=precision, spmv_group=code,
+                                 autotune=0) as sol:
+                sol.setup(small.A, small.B, small.C, small.D)
+                sol.mesh_setup(small.L)
+                out = _three_vcycles(sol, small) + _three_vcycles(sol, small)
+                x = sol.solve(small.b.copy())
+                res.append((out, x, sol.iters()))
+        for a, b in zip(res[0][0], res[1][0]):
+            np.testing.assert_array_equal(a, b)
+        np.testing.assert_array_equal(res[0][1], res[1][1])
+        assert res[0][2] == res[1][2]
+
+
+@pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
 def test_l2_prefetch_changes_no_result(small, precision):
     """The bulk L2 prefetch of the scalar-row products only moves data into
     L2: V-cycles are bit-identical with it off, 1 CTA ahead and 192 ahead
