@@ -266,9 +266,10 @@ CPU_SAMPLE_SMALL = ("tube_large", {"n_ax": 10})
 _BLAS_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
 
 
-def _oracle_sample(name: str, overrides: dict):
+def _oracle_sample(name: str, overrides: dict, want_x: bool = False):
     """One full oracle step (set-up, SCR-FGMRES, mesh AMG-CG) on a generator
-    preset; returns (seconds, unknowns, outer, inner iterations)."""
+    preset; returns (seconds, unknowns, outer, inner iterations) and, with
+    want_x, the oracle's block solution."""
     import fsi_inputs as F
     from oracle import scr as oscr
     s = F.tube_system(name, **overrides)
@@ -277,7 +278,8 @@ def _oracle_sample(name: str, overrides: dict):
     dt = time.perf_counter() - t0
     assert out["info"].converged
     c = out["counters"]
-    return dt, s.n, out["info"].iters, c.a_iters + c.s_iters + c.i_iters
+    res = (dt, s.n, out["info"].iters, c.a_iters + c.s_iters + c.i_iters)
+    return res + (out["x"],) if want_x else res
 
 
 def _pool_sample(args):
@@ -316,7 +318,7 @@ def cpu_baseline(n_full: int) -> dict:
     `value` = the single-thread full-workload rate x that aggregate speed-up
     (independent problems on every core, as the GPU runs replicas)."""
     cores = os.cpu_count() or 1
-    t1, n1, o1, i1 = _oracle_in_processes(CPU_SAMPLE, 1)[0]
+    t1, n1, o1, i1, x1 = _oracle_in_processes(CPU_SAMPLE + (True,), 1)[0]
     t_full = t1 * n_full / n1
     ts, ns, _, _ = _oracle_in_processes(CPU_SAMPLE_SMALL, 1)[0]
     t0 = time.perf_counter()
@@ -335,6 +337,7 @@ def cpu_baseline(n_full: int) -> dict:
         "extrapolated": True,
         "single_thread": {"value": 1.0 / t_full, "unit": UNIT, "cores": 1, "seconds_per_solve": t_full},
         "all_core_speedup": speedup,
+        "_x_sample": x1,
     }
 
 
@@ -358,6 +361,7 @@ def run_reference(args):
     for _ in range(args.steps):
         times.append(_oracle_sample(*small)[0])
     cb = cpu_baseline(n_full)
+    cb.pop("_x_sample", None)
     line = {
         "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / cb["value"],
@@ -567,11 +571,26 @@ def main(argv=None):
     if rank != 0:
         return
     cpu = None
+    oracle_check = None
     if not args.no_cpu_baseline and world == 1:
         try:
             cpu = cpu_baseline(n_head)
         except Exception as e:  # pragma: no cover
             cpu = {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle", "sample": f"failed: {e}"}
+        x_or = cpu.pop("_x_sample", None)
+        if x_or is not None:
+            # the GPU's FP64 and mixed answers on the oracle's timed sample,
+            # against the oracle's own SCR-FGMRES answer (both at 1e-8)
+            so = F.tube_system(CPU_SAMPLE[0], **CPU_SAMPLE[1])
+            oracle_check = {"workload": f"{CPU_SAMPLE[0]} with {CPU_SAMPLE[1]}, {so.n} unknowns",
+                            "reference": "the oracle's SCR-FGMRES at rel-res 1e-8 (the cpu_baseline sample)"}
+            for nm, pr in (("fp64", pkg.SCR_FP64), ("mixed", pkg.SCR_MIXED)):
+                with pkg.BlockSolver(precision=pr) as so_sol:
+                    so_sol.setup(so.A, so.B, so.C, so.D)
+                    xg = so_sol.solve(so.b.copy())
+                    rr = so_sol.residual()
+                oracle_check[nm] = {"rel_difference": float(np.linalg.norm(xg - x_or) / np.linalg.norm(x_or)),
+                                    "rel_res": rr}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -588,7 +607,7 @@ def main(argv=None):
         "solve_ms": head["solve_ms"], "dofs_iters_per_s": head["dofs_iters_per_s"],
         "mm_setup_ms": head["mm_setup_ms"], "mm_solve_ms": head["mm_solve_ms"],
         "gpu_launches": head["gpu_launches"], "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": e2e,
-        "mixed": mixed, "stenosis": sten, "bifurcation": bif,
+        "mixed": mixed, "oracle_check": oracle_check, "stenosis": sten, "bifurcation": bif,
         "batched": batched, "multi_rhs": multi, "assembly": assembly,
         "clocks": head["clocks"], "inputs_build_s": t_in,
     }
