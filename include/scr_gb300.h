@@ -133,6 +133,10 @@ typedef struct {
                          Results are the same either way (measured: FP64 step 1084 -> 1069 ms,
                          mixed 626 -> 615 ms on the 616k-node tube).
                          Like spmv_group and l2_prefetch it is process-wide: the last scr_create sets it */
+  int tangent_resetup;/* how scr_assemble_tangent (and the Newton corrector) set the solve up on the
+                         new tangent: 1 (default) scr_update_values (the aggregates, truncation
+                         positions and product patterns of the first set-up kept); 0 a full
+                         scr_setup */
   int l2_prefetch;    /* scalar-row products: each CTA prefetches into L2 the values and indices of
                          the CTA this many indices ahead (bulk L2 prefetch); 0 off; default 192 */
   int amg_coarse_bf16;/* mixed form only: 1 (default) stores the values of the coarse AMG levels
@@ -208,6 +212,21 @@ int scr_destroy(scr_handle h);
    entry of A; SCR_CUDA_ERROR on device failure. */
 int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C,
               const scr_bsr* D, int ptr_is_device);
+
+/* New values for the block system of the last scr_setup, with the same
+   sizes and the same sparsity patterns (row_ptr and col_idx equal to the
+   set-up's; checked on the device, SCR_INVALID_ARG when they differ): the
+   numeric re-set-up of a Newton step whose Jacobian keeps its pattern.  The
+   values are copied in, Shat = D - C diag(A)^{-1} B is recomputed on its
+   stored pattern (Sec. 5.2.1), and both AMG hierarchies are recomputed on
+   their stored patterns: the aggregates of the first set-up are kept, the
+   smoothed prolongators are recomputed from the new operators and
+   truncated to the positions the first set-up kept (rescaled to the new
+   row sums), and the Galerkin operators, smoother data (Chebyshev interval,
+   guard), coarsest inverse and lower-precision copies follow.  Ownership,
+   pointers and errors as scr_setup; not for batched handles. */
+int scr_update_values(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C, const scr_bsr* D,
+                      int ptr_is_device);
 
 /* Solve calA x = b to the outer tolerance (FGMRES + P_SCR, x_0 = 0).
    b, x: length 3 n_v + n_p.  Returns SCR_NOT_CONVERGED if the outer cap is

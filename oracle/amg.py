@@ -152,6 +152,31 @@ def tentative_prolongator(agg: np.ndarray, bs: int) -> sp.csr_matrix:
     return sp.csr_matrix((vals, (rows, cols)), shape=(n * bs, na * bs))
 
 
+def truncate_to_pattern(P: sp.csr_matrix, bs: int, indptr: np.ndarray, indices: np.ndarray) -> sp.csr_matrix:
+    """The truncation of step 4 with its kept block positions given (the
+    block pattern indptr / indices, a subset of P's blocks in every row), as
+    a numeric re-set-up keeps them: the kept blocks of each scalar row are
+    rescaled by (sum of the row) / (sum of its kept entries)."""
+    B = sp.bsr_matrix(P, blocksize=(bs, bs))
+    B.sort_indices()
+    nbr = B.shape[0] // bs
+    rows = np.repeat(np.arange(nbr), np.diff(B.indptr))
+    keep_set = set(zip(np.repeat(np.arange(nbr), np.diff(indptr)).tolist(), np.asarray(indices).tolist()))
+    keep = np.array([(r, c) in keep_set for r, c in zip(rows.tolist(), B.indices.tolist())], dtype=bool)
+    data = B.data.copy()
+    s_all = np.zeros((nbr, bs))
+    s_kept = np.zeros((nbr, bs))
+    np.add.at(s_all, rows, data.sum(axis=2))
+    np.add.at(s_kept, rows, (data * keep[:, None, None]).sum(axis=2))
+    scale = np.where(s_kept != 0.0, s_all / np.where(s_kept != 0.0, s_kept, 1.0), 1.0)
+    data = data * scale[rows][:, :, None]
+    k = np.nonzero(keep)[0]
+    ip = np.concatenate([[0], np.cumsum(np.bincount(rows[k], minlength=nbr))])
+    out = sp.bsr_matrix((data[k], B.indices[k], ip), shape=P.shape).tocsr()
+    out.sort_indices()
+    return out
+
+
 def gershgorin_dinv_a(A: sp.csr_matrix) -> float:
     """max_i sum_j |a_ij| / |a_ii| (an upper bound of rho(D^{-1} A))."""
     absrow = np.asarray(abs(A).sum(axis=1)).ravel()

@@ -33,7 +33,7 @@ class Opts(C.Structure):
         ("amg_nu", C.c_int), ("amg_trunc", C.c_double), ("amg_pmax", C.c_int), ("autotune", C.c_int),
         ("amg_smoother", C.c_int), ("amg_degree", C.c_int), ("spmv_group", C.c_int),
         ("sell", C.c_int), ("vec", C.c_int), ("inner_vcycles", C.c_int), ("inter_vcycles", C.c_int),
-        ("newton", C.c_int), ("pdl", C.c_int),
+        ("newton", C.c_int), ("pdl", C.c_int), ("tangent_resetup", C.c_int),
         ("l2_prefetch", C.c_int), ("amg_coarse_bf16", C.c_int), ("cuda_graphs", C.c_int),
         ("nrhs", C.c_int),
         ("mm_rtol", C.c_double), ("mm_max_it", C.c_int), ("verbose", C.c_int),
@@ -90,7 +90,7 @@ EXPORTED = [
     "scr_export", "scr_bsr_spmv", "scr_profile_begin", "scr_profile_end", "scr_bsr_spmv_noalloc",
     "scr_setup_batch", "scr_solve_batch", "scr_batch_residuals", "scr_tune_save", "scr_tune_load",
     "scr_solve_multi", "scr_set_outlets", "scr_assembly_setup", "scr_assemble_residual",
-    "scr_corrector", "scr_mesh_coupling", "scr_corrector_ale", "scr_assemble_tangent",
+    "scr_corrector", "scr_mesh_coupling", "scr_corrector_ale", "scr_assemble_tangent", "scr_update_values",
 ]
 
 _lib = None
@@ -115,6 +115,7 @@ def load_library(build_if_missing: bool = False):
     L.scr_create.argtypes = [P(V), P(Opts), V]
     L.scr_destroy.argtypes = [V]
     L.scr_setup.argtypes = [V, P(Bsr), P(Bsr), P(Bsr), P(Bsr), C.c_int]
+    L.scr_update_values.argtypes = [V, P(Bsr), P(Bsr), P(Bsr), P(Bsr), C.c_int]
     L.scr_solve.argtypes = [V, V, V, C.c_int]
     L.scr_iters.argtypes = [V, P(C.c_int), P(C.c_int)]
     L.scr_residual.argtypes = [V, P(C.c_double)]

@@ -1285,3 +1285,109 @@ void dense_apply_f(const float* inv, const float* b, float* x, int n, int nrhs, 
 }
 
 }  // namespace scr
+
+// ------------------------------------------------------------ numeric re-set-up
+// The values of a set-up's products for new operator values on unchanged
+// patterns (scr_update_values): every output keeps the sparsity pattern of
+// the first set-up, only its values are recomputed.
+namespace scr {
+
+void spgemm_numeric(const DBsr<double>& A, const DBsr<double>& B, DBsr<double>& C, cudaStream_t s) {
+  if (A.nbr == 0 || C.nnzb == 0) return;
+  const int grid = ceil_div(A.nbr, kSpgemmWarps);
+  const int br = A.br, bk = A.bc, bc = B.bc;
+  if (br == 3 && bk == 3 && bc == 3) k_spgemm_numeric<3, 3, 3><<<grid, 32 * kSpgemmWarps, 0, s>>>(A, B, C);
+  else if (br == 1 && bk == 3 && bc == 1) k_spgemm_numeric<1, 3, 1><<<grid, 32 * kSpgemmWarps, 0, s>>>(A, B, C);
+  else if (br == 1 && bk == 1 && bc == 1) k_spgemm_numeric<1, 1, 1><<<grid, 32 * kSpgemmWarps, 0, s>>>(A, B, C);
+  else throw CudaError{cudaErrorInvalidValue, "spgemm_numeric: unsupported block shape"};
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
+void spadd_numeric(const DBsr<double>& A, double alpha, const DBsr<double>& B, const double* rowscale,
+                   DBsr<double>& C, cudaStream_t s) {
+  if (A.nbr == 0) return;
+  // the fill pass of spadd: the union pattern is rewritten with the same columns
+  k_spadd_fill<<<ceil_div(A.nbr, 256), 256, 0, s>>>(A, alpha, B, rowscale ? 1.0 : -1.0, rowscale, C);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
+void scale_rows_inv_values(const DBsr<double>& M, const double* d, double* out, cudaStream_t s) {
+  const long long n = (long long)M.nbr * M.br;
+  if (n == 0) return;
+  k_scale_rows_inv<<<ceil_div(n, 256), 256, 0, s>>>(M, d, out);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
+// O keeps its kept columns (a subset of P's row, both sorted); per scalar row
+// r its values are P's at those columns times sum_all / sum_kept of P's row
+// r, the row-sum preserving rescaling of the truncation
+__global__ void k_trunc_refill(DBsr<double> P, DBsr<double> O) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P.nbr) return;
+  const int BR = P.br, BC = P.bc;
+  const int s = P.rp[i], k = P.rp[i + 1] - s;
+  const int os = O.rp[i], ok = O.rp[i + 1] - os;
+  for (int r = 0; r < BR; ++r) {
+    double sall = 0.0, skept = 0.0;
+    int o = 0;
+    for (int t = 0; t < k; ++t) {
+      const bool kp = o < ok && O.col[os + o] == P.col[s + t];
+      for (int c = 0; c < BC; ++c) {
+        const double v = P.val[slab_index(s, k, t, r, c, BR, BC)];
+        sall += v;
+        if (kp) skept += v;
+      }
+      if (kp) ++o;
+    }
+    const double sc = skept != 0.0 ? sall / skept : 1.0;
+    o = 0;
+    for (int t = 0; t < k && o < ok; ++t) {
+      if (O.col[os + o] != P.col[s + t]) continue;
+      for (int c = 0; c < BC; ++c)
+        O.val[slab_index(os, ok, o, r, c, BR, BC)] = P.val[slab_index(s, k, t, r, c, BR, BC)] * sc;
+      ++o;
+    }
+  }
+}
+
+void truncate_refill(const DBsr<double>& P, DBsr<double>& O, cudaStream_t s) {
+  if (P.nbr == 0) return;
+  k_trunc_refill<<<ceil_div(P.nbr, 256), 256, 0, s>>>(P, O);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
+// T = A^T on T's existing pattern: every stored block (i, j) of A is found in
+// row j of T by binary search and written transposed
+__global__ void k_transpose_values(DBsr<double> A, DBsr<double> T) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= A.nbr) return;
+  const int BR = A.br, BC = A.bc;
+  const int s = A.rp[i], k = A.rp[i + 1] - s;
+  for (int t = 0; t < k; ++t) {
+    const int j = A.col[s + t];
+    int lo = T.rp[j], hi = T.rp[j + 1] - 1;
+    const int ts = lo, tk = hi + 1 - lo;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (T.col[mid] < i) lo = mid + 1;
+      else hi = mid;
+    }
+    if (lo > hi || T.col[lo] != i) continue;  // not in the pattern (cannot happen for a transpose)
+    for (int r = 0; r < BR; ++r)
+      for (int c = 0; c < BC; ++c)
+        T.val[slab_index(ts, tk, lo - ts, c, r, BC, BR)] = A.val[slab_index(s, k, t, r, c, BR, BC)];
+  }
+}
+
+void transpose_numeric(const DBsr<double>& A, DBsr<double>& T, cudaStream_t s) {
+  if (A.nbr == 0) return;
+  k_transpose_values<<<ceil_div(A.nbr, 256), 256, 0, s>>>(A, T);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+
+}  // namespace scr

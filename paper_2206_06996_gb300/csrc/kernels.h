@@ -314,6 +314,20 @@ struct Aggregation {
 // strength graph + MIS-2 aggregation of the block rows of A
 Aggregation aggregate(const DBsr<double>& A, double theta, DeviceArena& arena, DeviceArena& tmp,
                       cudaStream_t s, int* mis_rounds);
+// numeric re-set-up on unchanged patterns (amg_setup.cu): C = A B, C = alpha
+// A + beta diag(rowscale) B (beta = 1, or -1 without rowscale), out =
+// diag(d)^{-1} M values, O = the row-sum preserving truncation of P to O's
+// kept columns, T = A^T; each writes the values of an output whose pattern
+// a full set-up built
+void spgemm_numeric(const DBsr<double>& A, const DBsr<double>& B, DBsr<double>& C, cudaStream_t s);
+void spadd_numeric(const DBsr<double>& A, double alpha, const DBsr<double>& B, const double* rowscale,
+                   DBsr<double>& C, cudaStream_t s);
+void scale_rows_inv_values(const DBsr<double>& M, const double* d, double* out, cudaStream_t s);
+void truncate_refill(const DBsr<double>& P, DBsr<double>& O, cudaStream_t s);
+void transpose_numeric(const DBsr<double>& A, DBsr<double>& T, cudaStream_t s);
+// the padded copy's values from M's slab values (same pattern)
+template <typename VT>
+void refresh_vec(DBsr<VT>& M, cudaStream_t s);
 // tentative prolongator I_bs / sqrt(|a|)
 void tentative(const int* agg, int nbr, int n_agg, int bs, DBsr<double>& P, DeviceArena& arena,
                DeviceArena& tmp, cudaStream_t s);

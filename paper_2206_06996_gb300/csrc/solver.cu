@@ -69,6 +69,10 @@ struct HostScalars {
 // ------------------------------------------------------------ AMG hierarchy
 struct Level {
   DBsr<double> A, P, R;
+  // products of the build kept for a numeric re-set-up (refresh): the
+  // tentative prolongator, A P_tent, the untruncated smoothed prolongator
+  // and A P (their patterns are reused, their values recomputed)
+  DBsr<double> Pt, T, Ps, AP;
   DBsr<float> Af, Pf, Rf;
   double* dinv = nullptr;   // l1-Jacobi: 1 / sum_j |a_ij|
   float* dinvf = nullptr;
@@ -194,9 +198,8 @@ struct Hierarchy {
           L.roots = ag.roots;
           L.n_agg = ag.n_agg;
           DBsr<double> Pt, T, AP, Ac;
-          DeviceArena tmp2(s);
           t0 = Clock::now();
-          tentative(ag.agg, Al.nbr, ag.n_agg, bs, Pt, tmp2, tmp, s);
+          tentative(ag.agg, Al.nbr, ag.n_agg, bs, Pt, ar, tmp, s);
           double* d = tmp.alloc<double>(L.n + 1);
           int* bad = tmp.alloc<int>(1);
           SCR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
@@ -205,11 +208,14 @@ struct Hierarchy {
           gershgorin(Al, d, lam, s);
           double* rs = tmp.alloc<double>(L.n + 1);
           prolong_rowscale(d, lam, rs, (int)L.n, s);
-          spgemm(Al, Pt, T, tmp2, s);
+          spgemm(Al, Pt, T, ar, s);
+          L.Pt = Pt;
+          L.T = T;
           if (o.amg_trunc > 0.0 || o.amg_pmax > 0) {
             DBsr<double> Ps;
-            spadd(Pt, 1.0, T, rs, Ps, tmp2, s);
+            spadd(Pt, 1.0, T, rs, Ps, ar, s);
             truncate_rows(Ps, o.amg_trunc, o.amg_pmax, L.P, ar, s);
+            L.Ps = Ps;
           } else {
             spadd(Pt, 1.0, T, rs, L.P, ar, s);
           }
@@ -220,7 +226,8 @@ struct Hierarchy {
           SCR_CUDA(cudaStreamSynchronize(s));
           const double t_tr = ms_since(t0);
           t0 = Clock::now();
-          spgemm(Al, L.P, AP, tmp2, s);
+          spgemm(Al, L.P, AP, ar, s);
+          L.AP = AP;
           SCR_CUDA(cudaStreamSynchronize(s));
           const double t_ap = ms_since(t0);
           t0 = Clock::now();
@@ -335,6 +342,88 @@ struct Hierarchy {
         }
       }
     }
+    SCR_CUDA(cudaStreamSynchronize(s));
+  }
+
+  // New values on the patterns of the last build: A0 has the pattern of the
+  // build's level-0 operator (its values may differ).  Every level's
+  // operator, prolongator, restriction and smoother data are recomputed on
+  // the stored patterns: the aggregates, the truncation's kept positions and
+  // the sparse products' patterns are those of the build (a numeric
+  // re-set-up); the V-cycle graph is recorded again at its next use.
+  void refresh(const DBsr<double>& A0, const scr_opts& o, cudaStream_t s, const DBsr<float>* A0f = nullptr) {
+    gexec.reset();
+    graph_failed = false;
+    gin = gout = nullptr;
+    gsize = 0;
+    const int nl = n_levels();
+    if (nl == 0) return;
+    lv[0].A.val = A0.val;
+    lv[0].A.vdesc = A0.vdesc;
+    lv[0].A.vval = A0.vval;
+    for (int l = 0; l < nl; ++l) {
+      Level& L = lv[l];
+      l1_inv(L.A, L.dinv, s);
+      if (l + 1 >= nl) break;
+      DeviceArena tmp(s);
+      double* d = tmp.alloc<double>(L.n + 1);
+      int* bad = tmp.alloc<int>(1);
+      SCR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+      diag_scalar(L.A, d, bad, s);
+      double* lam = tmp.alloc<double>(1);
+      gershgorin(L.A, d, lam, s);
+      double* rs = tmp.alloc<double>(L.n + 1);
+      prolong_rowscale(d, lam, rs, (int)L.n, s);
+      spgemm_numeric(L.A, L.Pt, L.T, s);
+      if (L.Ps.nbr) {
+        spadd_numeric(L.Pt, 1.0, L.T, rs, L.Ps, s);
+        truncate_refill(L.Ps, L.P, s);
+      } else {
+        spadd_numeric(L.Pt, 1.0, L.T, rs, L.P, s);
+      }
+      transpose_numeric(L.P, L.R, s);
+      spgemm_numeric(L.A, L.P, L.AP, s);
+      spgemm_numeric(L.R, L.AP, lv[l + 1].A, s);
+      SCR_CUDA(cudaStreamSynchronize(s));
+    }
+    // coarsest level: dense inverse
+    {
+      DeviceArena tmp(s);
+      double* M = tmp.alloc<double>((size_t)nc * nc + 1);
+      int* sing = tmp.alloc<int>(1);
+      SCR_CUDA(cudaMemsetAsync(sing, 0, sizeof(int), s));
+      to_dense(lv.back().A, M, s);
+      dense_inverse(M, cinv, nc, sing, s);
+      int hs = 0;
+      SCR_CUDA(cudaMemcpyAsync(&hs, sing, sizeof(int), cudaMemcpyDeviceToHost, s));
+      SCR_CUDA(cudaStreamSynchronize(s));
+      if (hs) throw CudaError{cudaErrorInvalidValue, "singular coarsest AMG operator"};
+    }
+    // smoother data and lower-precision copies, as in build
+    for (int l = 0; l < nl; ++l) {
+      Level& L = lv[l];
+      if (smoother == SCR_SMOOTH_CHEB && l + 1 < nl) {
+        inv_diag(L.A, L.dd, s);
+        L.lam = power_lambda(L.A, L.dd, 20, s);
+        L.cheb_off = cheb_guard_growth(L, s) > kChebGuardGrowth;
+        if (f32) cast_d2f(L.dd, L.ddf, L.n, s);
+      }
+      if (f32) {
+        if (!(l == 0 && A0f)) {
+          slab_to_float(L.A.val, L.Af.val, L.A.nnzb * L.A.br * L.A.bc, s);
+          if (L.Af.vdesc) refresh_vec<float>(L.Af, s);
+        }
+        if (L.P.nbr) {
+          slab_to_float(L.P.val, L.Pf.val, L.P.nnzb * L.P.br * L.P.bc, s);
+          slab_to_float(L.R.val, L.Rf.val, L.R.nnzb * L.R.br * L.R.bc, s);
+        }
+        if (L.Af.hval) slab_to_bf16(L.Af.val, const_cast<void*>(L.Af.hval), L.Af.nnzb * L.Af.br * L.Af.bc, s);
+        if (L.Pf.hval) slab_to_bf16(L.Pf.val, const_cast<void*>(L.Pf.hval), L.Pf.nnzb * L.Pf.br * L.Pf.bc, s);
+        if (L.Rf.hval) slab_to_bf16(L.Rf.val, const_cast<void*>(L.Rf.hval), L.Rf.nnzb * L.Rf.br * L.Rf.bc, s);
+        cast_d2f(L.dinv, L.dinvf, L.n, s);
+      }
+    }
+    if (f32) cast_d2f(cinv, cinvf, (long long)nc * nc, s);
     SCR_CUDA(cudaStreamSynchronize(s));
   }
 
@@ -725,6 +814,7 @@ struct scr_ctx {
   std::unique_ptr<DeviceArena> mwork;  // mesh workspaces
   std::unique_ptr<DeviceArena> mmats;
   DBsr<double> A, B, C, D, Shat, L;
+  DBsr<double> Bs, CBs;  // diag(A)^{-1} B and C diag(A)^{-1} B of Shat's set-up (kept for scr_update_values)
   DBsr<float> Af, Bf, Cf, Df;
   DSell<double> A_sell, Shat_sell, L_sell;
   DSell<float> Af_sell, Shatf_sell;
@@ -1123,6 +1213,7 @@ int scr_default_opts(scr_opts* o) {
   o->inter_vcycles = 0;
   o->newton = 0;
   o->pdl = 1;
+  o->tangent_resetup = 1;
   o->l2_prefetch = 192;
   o->amg_coarse_bf16 = 1;
   o->cuda_graphs = 1;
@@ -1157,6 +1248,8 @@ int scr_create(scr_handle* out, const scr_opts* o, void* stream) {
       throw std::invalid_argument("inner_vcycles and inter_vcycles must lie in [0, 64]");
     if (op.newton != 0 && op.newton != 1) throw std::invalid_argument("newton must be 0 or 1");
     if (op.pdl != 0 && op.pdl != 1) throw std::invalid_argument("pdl must be 0 or 1");
+    if (op.tangent_resetup != 0 && op.tangent_resetup != 1)
+      throw std::invalid_argument("tangent_resetup must be 0 or 1");
     if (op.nrhs != 1 && op.nrhs != kSpmmCols) throw std::invalid_argument("nrhs must be 1 or 8");
     if (op.amg_coarse_bf16 != 0 && op.amg_coarse_bf16 != 1) throw std::invalid_argument("amg_coarse_bf16 must be 0 or 1");
     std::unique_ptr<scr_ctx> h(new scr_ctx());
@@ -1182,6 +1275,109 @@ int scr_destroy(scr_handle h) {
   return guarded([&] {
     cudaStreamSynchronize(h->s);
     delete h;
+  });
+}
+
+namespace {
+// flag when the caller's pattern (rp, col) differs from the stored one
+__global__ void k_pattern_differs(int nbr, long long nnzb, const int* __restrict__ rp, const int* __restrict__ col,
+                                  const int* __restrict__ rp0, const int* __restrict__ col0, int* __restrict__ diff) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t <= nbr && rp[t] != rp0[t]) atomicExch(diff, 1);
+  if (t < nnzb && col[t] != col0[t]) atomicExch(diff, 1);
+}
+
+// new values of a stored matrix with an unchanged pattern: checks the
+// pattern against the stored one (SCR_INVALID_ARG when it differs) and
+// writes the values into the stored slab array
+void update_values(const scr_bsr* M, DBsr<double>& D, int dev, cudaStream_t s, const char* name) {
+  if (M->nb_rows != D.nbr || M->nb_cols != D.nbc || M->br != D.br || M->bc != D.bc || M->nnzb != D.nnzb)
+    throw std::invalid_argument(std::string(name) + ": sizes differ from the set-up's; call scr_setup");
+  DeviceArena tmp(s);
+  const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const int* rp = M->row_ptr;
+  const int* col = M->col_idx;
+  const double* val = M->val;
+  const size_t nv = (size_t)M->nnzb * M->br * M->bc;
+  if (!dev) {
+    int* r = tmp.alloc<int>(M->nb_rows + 1);
+    int* c = tmp.alloc<int>(M->nnzb + 1);
+    double* v = tmp.alloc<double>(nv + 1);
+    SCR_CUDA(cudaMemcpyAsync(r, M->row_ptr, sizeof(int) * (M->nb_rows + 1), k, s));
+    if (M->nnzb) SCR_CUDA(cudaMemcpyAsync(c, M->col_idx, sizeof(int) * M->nnzb, k, s));
+    if (nv) SCR_CUDA(cudaMemcpyAsync(v, M->val, sizeof(double) * nv, k, s));
+    rp = r;
+    col = c;
+    val = v;
+  }
+  int* diff = tmp.alloc<int>(1);
+  SCR_CUDA(cudaMemsetAsync(diff, 0, sizeof(int), s));
+  const long long n = std::max<long long>(M->nb_rows + 1, M->nnzb);
+  k_pattern_differs<<<ceil_div(n, 256), 256, 0, s>>>(M->nb_rows, M->nnzb, rp, col, D.rp, D.col, diff);
+  SCR_LAUNCH();
+  int hd = 0;
+  SCR_CUDA(cudaMemcpyAsync(&hd, diff, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SCR_CUDA(cudaStreamSynchronize(s));
+  if (hd) throw std::invalid_argument(std::string(name) + ": pattern differs from the set-up's; call scr_setup");
+  if (nv) to_slab<double>(D.rp, val, D.val, D.nbr, D.br, D.bc, D.nnzb, s);
+  SCR_CUDA(cudaStreamSynchronize(s));
+}
+}  // namespace
+
+int scr_update_values(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C, const scr_bsr* D,
+                      int dev) {
+  if (!h || !A || !B || !C || !D) return SCR_INVALID_ARG;
+  if (!h->have_block || h->nbatch) {
+    set_last_error("scr_update_values: needs a block set-up (scr_setup, not batched)");
+    return SCR_INVALID_ARG;
+  }
+  return guarded([&] {
+    auto t0 = Clock::now();
+    cudaStream_t s = h->s;
+    SCR_CUDA(cudaStreamSynchronize(s));
+    update_values(A, h->A, dev, s, "A");
+    update_values(B, h->B, dev, s, "B");
+    update_values(C, h->C, dev, s, "C");
+    update_values(D, h->D, dev, s, "D");
+    const int nv = h->nv;
+    {
+      // Shat = D - C diag(A)^{-1} B on its stored patterns (Sec. 5.2.1)
+      DeviceArena tmp(s);
+      double* d = tmp.alloc<double>(3LL * nv + 1);
+      int* bad = tmp.alloc<int>(1);
+      SCR_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+      diag_scalar(h->A, d, bad, s);
+      int hb = 0;
+      SCR_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+      SCR_CUDA(cudaStreamSynchronize(s));
+      if (hb) throw std::invalid_argument("A has a missing or zero diagonal entry");
+      if (h->o.precond == SCR_PC_SIMPLEC) abs_rowsum(h->A, d, s);
+      for (int j = 0; j < h->n_out; ++j) add_scaled_squares(d, h->out_a + 3LL * nv * j, h->out_c[j], 3LL * nv, s);
+      if (h->n_out) reciprocal(d, h->dAinv, 3LL * nv, s);
+      scale_rows_inv_values(h->B, d, h->Bs.val, s);
+      spgemm_numeric(h->C, h->Bs, h->CBs, s);
+      spadd_numeric(h->D, 1.0, h->CBs, nullptr, h->Shat, s);
+      SCR_CUDA(cudaStreamSynchronize(s));
+    }
+    if (!h->n_out) {
+      if (h->o.precond == SCR_PC_SIMPLEC) l1_inv(h->A, h->dAinv, s);
+      else inv_diag(h->A, h->dAinv, s);
+    }
+    refresh_vec<double>(h->A, s);
+    refresh_vec<double>(h->Shat, s);
+    const bool f32 = h->o.precision == SCR_MIXED;
+    if (f32) {
+      slab_to_float(h->A.val, h->Af.val, h->A.nnzb * 9, s);
+      slab_to_float(h->B.val, h->Bf.val, h->B.nnzb * 3, s);
+      slab_to_float(h->C.val, h->Cf.val, h->C.nnzb * 3, s);
+      slab_to_float(h->D.val, h->Df.val, h->D.nnzb, s);
+      refresh_vec<float>(h->Af, s);
+      cast_d2f(h->dAinv, h->dAinvf, 3LL * nv, s);
+    }
+    h->hA.refresh(h->A, h->o, s, f32 ? &h->Af : nullptr);
+    h->hS.refresh(h->Shat, h->o, s);
+    SCR_CUDA(cudaStreamSynchronize(s));
+    h->stats.setup_ms = ms_since(t0);
   });
 }
 
@@ -1251,10 +1447,9 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
         h->dAinv = a.alloc<double>(3LL * nv + 1);
         reciprocal(d, h->dAinv, 3LL * nv, s);
       }
-      DBsr<double> Bs, T;
-      scale_rows_inv(h->B, d, Bs, tmp, s);
-      spgemm(h->C, Bs, T, tmp, s);
-      spadd(h->D, 1.0, T, nullptr, h->Shat, a, s);
+      scale_rows_inv(h->B, d, h->Bs, a, s);
+      spgemm(h->C, h->Bs, h->CBs, a, s);
+      spadd(h->D, 1.0, h->CBs, nullptr, h->Shat, a, s);
       SCR_CUDA(cudaStreamSynchronize(s));
     }
     if (h->o.verbose) fprintf(stderr, "[setup] Shat %.2f ms (%lld entries)\n", ms_since(t1), h->Shat.nnzb);
@@ -2092,7 +2287,8 @@ void assemble_tangent_dev(scr_ctx* h, const double* v, const double* vhat, const
     d[m] = scr_bsr{P.nbr, P.nbc, P.br, P.bc, (int)P.nnzb, P.rp, P.col, P.val};
   }
   h->tangent_setup = true;
-  const int rc = scr_setup(h, &d[0], &d[1], &d[2], &d[3], 1);
+  const int rc = h->o.tangent_resetup ? scr_update_values(h, &d[0], &d[1], &d[2], &d[3], 1)
+                                      : scr_setup(h, &d[0], &d[1], &d[2], &d[3], 1);
   h->tangent_setup = false;
   if (rc != SCR_OK) throw std::runtime_error(std::string("set-up on the assembled tangent: ") + scr_last_error());
 }

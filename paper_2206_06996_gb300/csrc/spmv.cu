@@ -218,6 +218,44 @@ void build_vec(DBsr<VT>& M, DeviceArena& a, cudaStream_t s) {
   M.vval = vval;
   (void)nv;
 }
+// the padded values of block row i from its descriptor (the column slots
+// are unchanged)
+template <typename T>
+__global__ void k_vec_refill(int nbr, const int* __restrict__ rp, const T* __restrict__ slab, int br, int bc, int V,
+                             const void* __restrict__ desc, T* __restrict__ vval) {
+  const int i = blockIdx.x * blockDim.y + threadIdx.y;
+  if (i >= nbr) return;
+  const int s = rp[i], k = rp[i + 1] - s;
+  int v0, rl;
+  if (br == 3) {
+    const int4 d = static_cast<const int4*>(desc)[i];
+    v0 = d.z;
+    rl = d.w;
+  } else {
+    const int2 d = static_cast<const int2*>(desc)[i];
+    v0 = d.x;
+    rl = (k + V - 1) / V * V;
+  }
+  const long long src = (long long)s * br * bc;
+  for (int q = threadIdx.x; q < br * rl; q += blockDim.x) {
+    const int r = q / rl, e = q - r * rl;
+    vval[v0 + q] = e < bc * k ? slab[src + (long long)r * k * bc + e] : (T)0;
+  }
+}
+
+template <typename VT>
+void refresh_vec(DBsr<VT>& M, cudaStream_t s) {
+  if (!M.vdesc || M.nbr == 0) return;
+  constexpr int V = 16 / (int)sizeof(VT);
+  dim3 blk(32, 8);
+  k_vec_refill<VT><<<ceil_div(M.nbr, 8), blk, 0, s>>>(M.nbr, M.rp, M.val, M.br, M.bc, V, M.vdesc,
+                                                      const_cast<VT*>(M.vval));
+  SCR_LAUNCH();
+  counters().launches++;
+}
+template void refresh_vec<double>(DBsr<double>&, cudaStream_t);
+template void refresh_vec<float>(DBsr<float>&, cudaStream_t);
+
 template void build_vec<double>(DBsr<double>&, DeviceArena&, cudaStream_t);
 template void build_vec<float>(DBsr<float>&, DeviceArena&, cudaStream_t);
 

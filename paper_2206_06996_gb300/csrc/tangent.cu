@@ -13,7 +13,9 @@
 //     element's 16 x 16 tangent at the 4-point Gauss rule (momentum rows
 //     against velocity columns: A, against the pressure column: B; mass rows
 //     against velocity columns: C, against the pressure column: D) and
-//     writes it to a per-element scratch;
+//     writes it to a per-element scratch; four of an element's threads first
+//     form the element's geometry and its Gauss-point quantities (one point
+//     each) in shared memory for all sixteen;
 //  2. one thread per stored block of A, B, C and D (the pattern the solver
 //     was set up with) adds the contributions of the elements that couple
 //     its row and column, in increasing element order.
@@ -98,77 +100,155 @@ __device__ double circum_diameter(const double (&x)[4][3]) {
   return 2.0 * sqrt(r2);
 }
 
+// Per-element quantities shared by the element's 16 column threads (one
+// CTA holds kTanElems elements): geometry, the velocity gradient, and for
+// each Gauss point q the stabilisation parameters, the fine-scale velocity
+// and the two directional derivatives of the shape functions.
+constexpr int kTanElems = 8;
+struct TanGeom {
+  double dN[4][3];
+  double gv[3][3];
+  double w;
+  int kind;  // -1: degenerate or no element, 0: fluid, 1: solid
+};
+struct TanGauss {
+  double tauM, tauC, vp[3], dNu[4], dNvp[4];
+};
+
 // column (b, c) of element e's tangent, c = 0..2 the velocity component k =
 // c of vertex b, c = 3 its pressure: the 12 momentum rows and 4 mass rows
-// (A and C entries, or B and D entries), accumulated over the Gauss points
-__global__ void __launch_bounds__(128) k_element_tangent(TangentArgs T) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const int e = (int)(t >> 4), b = (int)((t >> 2) & 3), c = (int)(t & 3);
-  if (e >= T.n_elem) return;
-  double x[4][3], v[4][3], p[4];
-  for (int a = 0; a < 4; ++a) {
-    const int n = T.ien[4 * e + a];
-    for (int i = 0; i < 3; ++i) {
-      x[a][i] = T.xyz[3 * n + i];
-      v[a][i] = T.v[3 * n + i];
-    }
-    p[a] = T.p[T.pien[4 * e + a]];
-  }
-  double Km[4][3] = {}, Kq[4] = {};  // momentum rows (a, i) and mass rows a of this column
-  double dN[4][3], dxi[3][3], V = 0.0;
-  const bool ok = tet_geometry(x, dN, dxi, V);
+// (A and C entries, or B and D entries), accumulated over the Gauss points.
+// Phase 1: the element's threads c16 = q < 4 form the element's geometry
+// (each) and the quantities of Gauss point q; phase 2: every thread its
+// column from those shared values.
+__global__ void __launch_bounds__(16 * kTanElems) k_element_tangent(TangentArgs T) {
+  __shared__ TanGeom sg[kTanElems];
+  __shared__ TanGauss sq[kTanElems][4];
+  const int el = threadIdx.x >> 4, c16 = threadIdx.x & 15;
+  const int e = blockIdx.x * kTanElems + el;
+  const int b = c16 >> 2, c = c16 & 3;
   const double ga = (5.0 + 3.0 * sqrt(5.0)) / 20.0, gb = (5.0 - sqrt(5.0)) / 20.0;
   const double cm = T.cm, cf = T.cf, cu = T.cu;
-  if (ok && T.etype[e] == 0) {
-    // ---- fluid (Sec. 3.2) ----
-    const double rho = T.rho_f, mu = T.mu_f, w = V / 4.0;
-    double G[3][3];
-    const double cM = 0.5 * cbrt(2.0);
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) {
-        double s = 0.0;
-        for (int k = 0; k < 3; ++k)
-          for (int l = 0; l < 3; ++l) s += dxi[k][i] * (k == l ? 2.0 * cM : cM) * dxi[l][j];
-        G[i][j] = s;
+  if (c16 < 4) {
+    const int q = c16;
+    int kind = -1;
+    if (e < T.n_elem) {
+      double x[4][3], v[4][3], p[4], dN[4][3], dxi[3][3], V = 0.0;
+      for (int a = 0; a < 4; ++a) {
+        const int n = T.ien[4 * e + a];
+        for (int i = 0; i < 3; ++i) {
+          x[a][i] = T.xyz[3 * n + i];
+          v[a][i] = T.v[3 * n + i];
+        }
+        p[a] = T.p[T.pien[4 * e + a]];
       }
-    double GG = 0.0;
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) GG += G[i][j] * G[i][j];
-    const double trG = G[0][0] + G[1][1] + G[2][2], nu = mu / rho;
-    double gv[3][3], gp[3];
-    for (int i = 0; i < 3; ++i) {
-      gp[i] = 0.0;
-      for (int j = 0; j < 3; ++j) {
-        double s = 0.0;
-        for (int a = 0; a < 4; ++a) s += v[a][i] * dN[a][j];
-        gv[i][j] = s;
+      if (tet_geometry(x, dN, dxi, V)) {
+        kind = T.etype[e] == 0 ? 0 : 1;
+        double gv[3][3] = {};
+        if (kind == 0) {
+          // ---- fluid (Sec. 3.2): tau_M, tau_C and the fine scales at q ----
+          const double rho = T.rho_f, mu = T.mu_f, nu = mu / rho;
+          double G[3][3];
+          const double cM = 0.5 * cbrt(2.0);
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+              double s = 0.0;
+              for (int k = 0; k < 3; ++k)
+                for (int l = 0; l < 3; ++l) s += dxi[k][i] * (k == l ? 2.0 * cM : cM) * dxi[l][j];
+              G[i][j] = s;
+            }
+          double GG = 0.0;
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) GG += G[i][j] * G[i][j];
+          const double trG = G[0][0] + G[1][1] + G[2][2];
+          double gp[3];
+          for (int i = 0; i < 3; ++i) {
+            gp[i] = 0.0;
+            for (int j = 0; j < 3; ++j) {
+              double s = 0.0;
+              for (int a = 0; a < 4; ++a) s += v[a][i] * dN[a][j];
+              gv[i][j] = s;
+            }
+            for (int a = 0; a < 4; ++a) gp[i] += p[a] * dN[a][i];
+          }
+          double N[4];
+          for (int a = 0; a < 4; ++a) N[a] = a == q ? ga : gb;
+          double uq[3], vdq[3];
+          for (int i = 0; i < 3; ++i) {
+            uq[i] = vdq[i] = 0.0;
+            for (int a = 0; a < 4; ++a) {
+              const int n = T.ien[4 * e + a];
+              uq[i] += N[a] * (v[a][i] - (T.vhat ? T.vhat[3 * n + i] : 0.0));
+              vdq[i] += N[a] * (T.vd ? T.vd[3 * n + i] : 0.0);
+            }
+          }
+          double uGu = 0.0;
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) uGu += uq[i] * G[i][j] * uq[j];
+          TanGauss& g = sq[el][q];
+          g.tauM = 1.0 / (rho * sqrt(4.0 / (T.dt * T.dt) + uGu + 36.0 * nu * nu * GG));
+          g.tauC = 1.0 / (g.tauM * trG);
+          for (int i = 0; i < 3; ++i)
+            g.vp[i] = -g.tauM * (rho * (vdq[i] + gv[i][0] * uq[0] + gv[i][1] * uq[1] + gv[i][2] * uq[2]) + gp[i]);
+          for (int a = 0; a < 4; ++a) {
+            g.dNu[a] = dN[a][0] * uq[0] + dN[a][1] * uq[1] + dN[a][2] * uq[2];
+            g.dNvp[a] = dN[a][0] * g.vp[0] + dN[a][1] * g.vp[1] + dN[a][2] * g.vp[2];
+          }
+        } else if (q == 0) {
+          // ---- solid: its stabilisation from the circumsphere diameter ----
+          const double rho = T.rho_s, mu = T.mu_s;
+          const double cs = sqrt(mu / rho), dx = circum_diameter(x);
+          sq[el][0].tauM = T.c_m_solid * dx / (cs * rho);
+          sq[el][0].tauC = T.c_c_solid * cs * dx * rho;
+        }
+        if (q == 0) {
+          for (int a = 0; a < 4; ++a)
+            for (int i = 0; i < 3; ++i) sg[el].dN[a][i] = dN[a][i];
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) sg[el].gv[i][j] = gv[i][j];
+          sg[el].w = V / 4.0;
+        }
       }
-      for (int a = 0; a < 4; ++a) gp[i] += p[a] * dN[a][i];
     }
+    if (q == 0) sg[el].kind = kind;
+  }
+  __syncthreads();
+  const int kind = sg[el].kind;
+  if (kind < 0) {
+    if (e < T.n_elem) {  // degenerate element: zero column
+      double* out = T.E + (long long)e * kTanVals;
+      for (int a = 0; a < 4; ++a) {
+        if (c < 3) {
+          for (int i = 0; i < 3; ++i) out[offA(a, b, i, c)] = 0.0;
+          out[offC(a, b, c)] = 0.0;
+        } else {
+          for (int i = 0; i < 3; ++i) out[offB(a, b, i)] = 0.0;
+          out[offD(a, b)] = 0.0;
+        }
+      }
+    }
+    return;
+  }
+  double dN[4][3];
+  for (int a = 0; a < 4; ++a)
+    for (int i = 0; i < 3; ++i) dN[a][i] = sg[el].dN[a][i];
+  const double w = sg[el].w;
+  double Km[4][3] = {}, Kq[4] = {};  // momentum rows (a, i) and mass rows a of this column
+  if (kind == 0) {
+    const double rho = T.rho_f, mu = T.mu_f;
+    double gv[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) gv[i][j] = sg[el].gv[i][j];
     for (int q = 0; q < 4; ++q) {
       double N[4];
       for (int a = 0; a < 4; ++a) N[a] = a == q ? ga : gb;
-      double uq[3], vdq[3];
-      for (int i = 0; i < 3; ++i) {
-        uq[i] = vdq[i] = 0.0;
-        for (int a = 0; a < 4; ++a) {
-          const int n = T.ien[4 * e + a];
-          uq[i] += N[a] * (v[a][i] - (T.vhat ? T.vhat[3 * n + i] : 0.0));
-          vdq[i] += N[a] * (T.vd ? T.vd[3 * n + i] : 0.0);
-        }
-      }
-      double uGu = 0.0;
-      for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) uGu += uq[i] * G[i][j] * uq[j];
-      const double tauM = 1.0 / (rho * sqrt(4.0 / (T.dt * T.dt) + uGu + 36.0 * nu * nu * GG));
-      const double tauC = 1.0 / (tauM * trG);
-      double vp[3];
-      for (int i = 0; i < 3; ++i)
-        vp[i] = -tauM * (rho * (vdq[i] + gv[i][0] * uq[0] + gv[i][1] * uq[1] + gv[i][2] * uq[2]) + gp[i]);
+      const TanGauss& g = sq[el][q];
+      const double tauM = g.tauM, tauC = g.tauC;
+      const double vp[3] = {g.vp[0], g.vp[1], g.vp[2]};
       double dNu[4], dNvp[4];
       for (int a = 0; a < 4; ++a) {
-        dNu[a] = dN[a][0] * uq[0] + dN[a][1] * uq[1] + dN[a][2] * uq[2];
-        dNvp[a] = dN[a][0] * vp[0] + dN[a][1] * vp[1] + dN[a][2] * vp[2];
+        dNu[a] = g.dNu[a];
+        dNvp[a] = g.dNvp[a];
       }
       if (c < 3) {
         // velocity column (b, k): the strong residual rM moves by drM through
@@ -214,11 +294,10 @@ __global__ void __launch_bounds__(128) k_element_tangent(TangentArgs T) {
         }
       }
     }
-  } else if (ok) {
+  } else {
     // ---- solid (Sec. 3.5, small-strain deviatoric elasticity, incompressible) ----
-    const double rho = T.rho_s, mu = T.mu_s, w = V / 4.0;
-    const double cs = sqrt(mu / rho), dx = circum_diameter(x);
-    const double tauM = T.c_m_solid * dx / (cs * rho), tauC = T.c_c_solid * cs * dx * rho;
+    const double rho = T.rho_s, mu = T.mu_s;
+    const double tauM = sq[el][0].tauM, tauC = sq[el][0].tauC;
     for (int q = 0; q < 4; ++q) {
       double N[4];
       for (int a = 0; a < 4; ++a) N[a] = a == q ? ga : gb;
@@ -339,8 +418,7 @@ void TangentAssembler::evaluate(const ResidualAssembler& ra, const unsigned char
     TangentArgs T{ne,          ra.d_xyz,    ra.d_ien, ra.d_pien, ra.d_etype, v,    vhat, p, vd,
                   ra.ph.rho_f, ra.ph.mu_f,  ra.ph.rho_s, ra.ph.mu_s, ra.ph.dt, ra.ph.c_m_solid, ra.ph.c_c_solid,
                   cm,          cf,          cu,       E};
-    const long long threads = 16LL * ne;
-    k_element_tangent<<<ceil_div(threads, 128), 128, 0, s>>>(T);
+    k_element_tangent<<<ceil_div(ne, kTanElems), 16 * kTanElems, 0, s>>>(T);
     SCR_LAUNCH();
     counters().launches++;
   }

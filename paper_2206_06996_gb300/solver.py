@@ -135,6 +135,19 @@ class BlockSolver:
         self.n_v, self.n_p = A.nb_rows, D.nb_rows
         return self
 
+    def update_values(self, A, B, Cm, D):
+        """New values for the set-up's block system (same patterns):
+        scr_update_values, the numeric re-set-up."""
+        keep: list = []
+        sa, da = _as_bsr(A, keep)
+        sb, db = _as_bsr(B, keep)
+        sc, dc = _as_bsr(Cm, keep)
+        sd, dd = _as_bsr(D, keep)
+        if len({da, db, dc, dd}) != 1:
+            raise ValueError("A, B, C, D must all be on the host or all on the device")
+        check(self.lib.scr_update_values(self.h, C.byref(sa), C.byref(sb), C.byref(sc), C.byref(sd), da))
+        return self
+
     def solve(self, b, x=None, raise_on_nonconvergence: bool = True):
         """x with calA x = b.  numpy in -> numpy out (host pointers);
         CUDA tensor in -> CUDA tensor out (device pointers)."""

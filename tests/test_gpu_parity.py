@@ -1068,7 +1068,8 @@ def test_gpu_tangent_at_the_assembly_state_is_the_input_system(small):
 
 
 @pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
-def test_gpu_newton_corrector_matches_the_oracle_loop(small, precision):
+@pytest.mark.parametrize("resetup", [0, 1])
+def test_gpu_newton_corrector_matches_the_oracle_loop(small, precision, resetup):
     """The multi-corrector with the tangent re-assembled on the GPU at every
     iteration (option newton) follows the oracle's loop that re-assembles
     the generator's tangent and solves directly: same starting residual, same
@@ -1079,7 +1080,7 @@ def test_gpu_newton_corrector_matches_the_oracle_loop(small, precision):
     v0, p0 = asm.initial_state()
     z = np.zeros(3 * s.mesh.n_nodes)
     vr, pr, vdr, ur, nr = corrector.corrector(s, asm, v0, p0, z, z, 3, newton=True)
-    with pkg.BlockSolver(precision=precision, newton=1) as sol:
+    with pkg.BlockSolver(precision=precision, newton=1, tangent_resetup=resetup) as sol:
         sol.setup(s.A, s.B, s.C, s.D)
         sol.assembly_setup(s.mesh, s.params)
         v, p, vd, u = v0.copy(), p0.copy(), z.copy(), z.copy()
@@ -1131,6 +1132,101 @@ def test_gpu_tangent_needs_both_set_ups(small):
             sol.assemble_tangent(v, p)
     with pytest.raises(pkg.ScrError):
         pkg.BlockSolver(newton=2)
+
+
+def _exported_blocks(sol):
+    """The solver's A, B, C, D as block matrices in the set-up's patterns."""
+    return (sol.export(pkg.SCR_HIER_A, 0, pkg.SCR_EXPORT_OPERATOR),
+            *(sol.export(pkg.SCR_HIER_A, 0, k) for k in (pkg.SCR_EXPORT_BLOCK_B, pkg.SCR_EXPORT_BLOCK_C,
+                                                         pkg.SCR_EXPORT_BLOCK_D)))
+
+
+@pytest.mark.parametrize("precision", [pkg.SCR_FP64, pkg.SCR_MIXED])
+def test_numeric_resetup_with_the_same_values_changes_nothing(small, precision):
+    """scr_update_values with the set-up's own values reproduces the set-up:
+    V-cycles of both hierarchies and a whole solve are bit-identical."""
+    with pkg.BlockSolver(precision=precision) as sol:
+        sol.setup(small.A, small.B, small.C, small.D)
+        sol.mesh_setup(small.L)
+        v0 = _three_vcycles(sol, small)
+        x0 = sol.solve(small.b.copy())
+        sol.update_values(small.A, small.B, small.C, small.D)
+        v1 = _three_vcycles(sol, small)
+        x1 = sol.solve(small.b.copy())
+    for a, b in zip(v0, v1):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(x0, x1)
+
+
+def test_numeric_resetup_matches_the_oracle_on_the_kept_patterns(small):
+    """New values on the set-up's patterns (the Jacobian at a moved state,
+    assembled on the GPU): the solver's A, B, C, D are the new ones, Shat is
+    the oracle's D - C diag(A)^{-1} B of them, the aggregates are the set-up's,
+    every prolongator is the oracle's smoothed prolongator of the new level
+    operator truncated to the set-up's kept positions, every coarse operator
+    is P^T A P, and the solve meets the direct solve of the new system."""
+    s = small
+    asm = F.Assembler(F.make_params(**F.PRESETS["tube_small"]))
+    v, p, vd, vh = _moved_state(s, asm, 23)
+    with pkg.BlockSolver(tangent_resetup=0) as tsol:
+        tsol.setup(s.A, s.B, s.C, s.D)
+        tsol.assembly_setup(s.mesh, s.params)
+        tsol.assemble_tangent(v, p, vhat=vh, vdot=vd)
+        new = _exported_blocks(tsol)
+    with pkg.BlockSolver() as sol:
+        sol.setup(s.A, s.B, s.C, s.D)
+        before = {}
+        for which in (pkg.SCR_HIER_A, pkg.SCR_HIER_SHAT):
+            nl = sol.amg_levels(which)
+            before[which] = [(sol.export(which, l, pkg.SCR_EXPORT_AGGREGATES),
+                              sol.export(which, l, pkg.SCR_EXPORT_PROLONGATOR)) for l in range(nl - 1)]
+        sol.update_values(*new)
+        got = _exported_blocks(sol)
+        after = {}
+        for which in (pkg.SCR_HIER_A, pkg.SCR_HIER_SHAT):
+            nl = sol.amg_levels(which)
+            after[which] = ([to_csr(sol.export(which, l, pkg.SCR_EXPORT_OPERATOR)) for l in range(nl)],
+                            [sol.export(which, l, pkg.SCR_EXPORT_PROLONGATOR) for l in range(nl - 1)],
+                            [sol.export(which, l, pkg.SCR_EXPORT_AGGREGATES) for l in range(nl - 1)])
+        b = np.random.default_rng(5).standard_normal(s.n)
+        x = sol.solve(b.copy())
+    for g, w in zip(got, new):
+        assert np.array_equal(g.row_ptr, w.row_ptr) and np.array_equal(g.col, w.col)
+        assert np.array_equal(g.val, w.val)
+    op = BlockOperator(*new)
+    Shat = schur.schur_hat(op)
+    As, Ps, aggs = after[pkg.SCR_HIER_SHAT]
+    assert abs(As[0] - Shat).max() <= 1e-12 * abs(Shat).max()
+    for which, bs in ((pkg.SCR_HIER_A, 3), (pkg.SCR_HIER_SHAT, 1)):
+        As, Ps, aggs = after[which]
+        for l, ((agg0, P0), P, agg) in enumerate(zip(before[which], Ps, aggs)):
+            np.testing.assert_array_equal(agg, agg0)
+            assert np.array_equal(P.row_ptr, P0.row_ptr) and np.array_equal(P.col, P0.col)
+            Pt = amg.tentative_prolongator(agg.astype(np.int64), bs)
+            Psm, _ = amg.smoothed_prolongator(As[l], Pt)
+            Pref = amg.truncate_to_pattern(Psm, bs, P0.row_ptr, P0.col)
+            Pg = to_csr(P)
+            assert abs(Pg - Pref).max() <= 1e-12 * abs(Pref).max()
+            Aref = (Pref.T @ As[l] @ Pref).tocsr()
+            assert abs(As[l + 1] - Aref).max() <= 1e-11 * abs(Aref).max()
+    K = op.full().tocsc()
+    xd = spl.spsolve(K, b)
+    assert np.linalg.norm(K @ x - b) <= 1e-8 * np.linalg.norm(b)
+    assert _rel(x, xd) <= 1e-6
+
+
+def test_numeric_resetup_rejects_another_pattern(small, mini):
+    with pkg.BlockSolver() as sol:
+        sol.setup(small.A, small.B, small.C, small.D)
+        with pytest.raises(pkg.ScrError, match="differ"):
+            sol.update_values(mini.A, mini.B, mini.C, mini.D)
+        A = F.BSR(small.A.br, small.A.bc, small.A.nb_rows, small.A.nb_cols, small.A.row_ptr.copy(),
+                  small.A.col.copy(), small.A.val.copy())
+        r = 5
+        a, b = A.row_ptr[r], A.row_ptr[r + 1]
+        A.col[a:b] = np.roll(A.col[a:b], 1)  # same sizes, another pattern
+        with pytest.raises(pkg.ScrError, match="pattern"):
+            sol.update_values(A, small.B, small.C, small.D)
 
 
 def test_gpu_corrector_ale_rejects_a_missing_coupling(small):

@@ -900,3 +900,27 @@ def test_newton_corrector_first_step_is_the_frozen_one_and_it_contracts():
     assert nn_[0] == pytest.approx(nf[0], rel=1e-14) and nn_[1] == pytest.approx(nf[1], rel=1e-9)
     assert nn_[2] < 1e-2 * nn_[1] and nn_[3] < nn_[2]
 
+
+def test_truncation_to_a_given_pattern():
+    """Truncating to the pattern the truncation itself selects reproduces
+    it exactly; on another matrix with the same block pattern it keeps those
+    positions and every scalar row sum (the rescaling of step 4)."""
+    s = F.tube_system("tube_mini")
+    A = to_csr(s.A)
+    S = amg.strength_graph(A, 3, 0.08)
+    agg = amg.aggregate_greedy(S)
+    Pt = amg.tentative_prolongator(agg, 3)
+    P, _ = amg.smoothed_prolongator(A, Pt)
+    Pk = amg.truncate_prolongator(P, 3, 0.3, 5)
+    Bk = sp.bsr_matrix(Pk, blocksize=(3, 3))
+    Bk.sort_indices()
+    got = amg.truncate_to_pattern(P, 3, Bk.indptr, Bk.indices)
+    assert abs(got - Pk).max() <= 1e-15 * abs(Pk).max()
+    A2 = (A + sp.diags(0.1 * np.abs(A.diagonal()))).tocsr()
+    P2, _ = amg.smoothed_prolongator(A2, Pt)
+    got2 = amg.truncate_to_pattern(P2, 3, Bk.indptr, Bk.indices)
+    B2 = sp.bsr_matrix(got2, blocksize=(3, 3))
+    B2.sort_indices()
+    assert np.array_equal(B2.indptr, Bk.indptr) and np.array_equal(B2.indices, Bk.indices)
+    assert np.allclose(np.asarray(got2.sum(axis=1)).ravel(), np.asarray(P2.sum(axis=1)).ravel(), rtol=1e-12, atol=1e-14)
+
