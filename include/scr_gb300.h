@@ -137,6 +137,10 @@ typedef struct {
                          new tangent: 1 (default) scr_update_values (the aggregates, truncation
                          positions and product patterns of the first set-up kept); 0 a full
                          scr_setup */
+  int mapped_scalars; /* how the Krylov residual estimates reach the host after each iteration:
+                         1 (default) kernels write mapped pinned host memory; 0 a device buffer
+                         and one 16-byte copy to pinned memory before the stream synchronisation
+                         (measured 0.4 % slower) */
   int l2_prefetch;    /* scalar-row products: each CTA prefetches into L2 the values and indices of
                          the CTA this many indices ahead (bulk L2 prefetch); 0 off; default 192 */
   int amg_coarse_bf16;/* mixed form only: 1 (default) stores the values of the coarse AMG levels

@@ -34,6 +34,7 @@ class Opts(C.Structure):
         ("amg_smoother", C.c_int), ("amg_degree", C.c_int), ("spmv_group", C.c_int),
         ("sell", C.c_int), ("vec", C.c_int), ("inner_vcycles", C.c_int), ("inter_vcycles", C.c_int),
         ("newton", C.c_int), ("pdl", C.c_int), ("tangent_resetup", C.c_int),
+        ("mapped_scalars", C.c_int),
         ("l2_prefetch", C.c_int), ("amg_coarse_bf16", C.c_int), ("cuda_graphs", C.c_int),
         ("nrhs", C.c_int),
         ("mm_rtol", C.c_double), ("mm_max_it", C.c_int), ("verbose", C.c_int),

@@ -52,15 +52,33 @@ static double ms_since(Clock::time_point t0) {
 // ------------------------------------------------------------ host scalars
 // Two doubles of mapped pinned memory per solver: the device writes the
 // residual estimate there and the host reads it after a stream sync.
+// Scalars the host reads after a stream synchronisation (Krylov residual
+// estimates).  Mapped mode (default): the kernels write them straight into
+// mapped pinned host memory.  Copy mode: the kernels write a device buffer,
+// and fetch() queues a 16-byte copy into pinned host memory before the
+// synchronisation.  Measured on the 616k-node tube: mapped 1070 ms per FP64
+// step, copy 1074 ms.
+int g_mapped_scalars = 1;
 struct HostScalars {
   double* h = nullptr;
   double* d = nullptr;
+  bool mapped = false;
   HostScalars() {
-    SCR_CUDA(cudaHostAlloc(&h, 4 * sizeof(double), cudaHostAllocMapped));
-    SCR_CUDA(cudaHostGetDevicePointer(&d, h, 0));
+    mapped = g_mapped_scalars != 0;
+    if (mapped) {
+      SCR_CUDA(cudaHostAlloc(&h, 4 * sizeof(double), cudaHostAllocMapped));
+      SCR_CUDA(cudaHostGetDevicePointer(&d, h, 0));
+    } else {
+      SCR_CUDA(cudaHostAlloc(&h, 4 * sizeof(double), cudaHostAllocDefault));
+      SCR_CUDA(cudaMalloc(&d, 4 * sizeof(double)));
+    }
   }
   ~HostScalars() {
     if (h) cudaFreeHost(h);
+    if (d && !mapped) cudaFree(d);
+  }
+  void fetch(cudaStream_t s) {
+    if (!mapped) SCR_CUDA(cudaMemcpyAsync(h, d, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
   }
   HostScalars(const HostScalars&) = delete;
   HostScalars& operator=(const HostScalars&) = delete;
@@ -742,6 +760,7 @@ struct Gmres {
     fill<T>(x, (T)0, n, s);
     norm2<T>(b, n, &st->nrm2, red, s);
     arnoldi_start(st, 1, hs.d, s);
+    hs.fetch(s);
     SCR_CUDA(cudaStreamSynchronize(s));
     ++syncs;
     *iters = 0;
@@ -767,6 +786,7 @@ struct Gmres {
         cgs_update_norm<T>(V, n, j + 1, st->h2, w, n, &st->nrm2, red, s);
         arnoldi_finalize(st, j, hs.d, s);
         scale_by<T>(w, &st->inv_hnext, V + (size_t)(j + 1) * n, n, s);
+        hs.fetch(s);
         SCR_CUDA(cudaStreamSynchronize(s));
         ++syncs;
         r = hs.h[0];
@@ -1214,6 +1234,7 @@ int scr_default_opts(scr_opts* o) {
   o->newton = 0;
   o->pdl = 1;
   o->tangent_resetup = 1;
+  o->mapped_scalars = 1;
   o->l2_prefetch = 192;
   o->amg_coarse_bf16 = 1;
   o->cuda_graphs = 1;
@@ -1252,6 +1273,8 @@ int scr_create(scr_handle* out, const scr_opts* o, void* stream) {
       throw std::invalid_argument("tangent_resetup must be 0 or 1");
     if (op.nrhs != 1 && op.nrhs != kSpmmCols) throw std::invalid_argument("nrhs must be 1 or 8");
     if (op.amg_coarse_bf16 != 0 && op.amg_coarse_bf16 != 1) throw std::invalid_argument("amg_coarse_bf16 must be 0 or 1");
+    if (op.mapped_scalars != 0 && op.mapped_scalars != 1) throw std::invalid_argument("mapped_scalars must be 0 or 1");
+    g_mapped_scalars = op.mapped_scalars;
     std::unique_ptr<scr_ctx> h(new scr_ctx());
     h->o = op;
     set_forced_group(op.spmv_group);
@@ -1958,6 +1981,7 @@ static bool mesh_cg(scr_ctx* h, const double* g, double* u, int* iters, double* 
   fill<double>(u, 0.0, n, s);
   copy<double>(g, h->mr, n, s);
   cg_start(h->cg, g, n, h->mred, h->mhs.d, s);
+  h->mhs.fetch(s);
   SCR_CUDA(cudaStreamSynchronize(s));
   *iters = 0;
   *rel = 0.0;
@@ -1974,6 +1998,7 @@ static bool mesh_cg(scr_ctx* h, const double* g, double* u, int* iters, double* 
     spmv<double, double>(h->L, h->mp, h->mq, 3, set, s);
     cg_alpha(h->cg, h->mp, h->mq, n, h->mred, s);
     cg_step_x_r(h->cg, h->mp, h->mq, u, h->mr, n, h->mred, h->mhs.d, s);
+    h->mhs.fetch(s);
     SCR_CUDA(cudaStreamSynchronize(s));
     *iters = it;
     *rel = hr[0];

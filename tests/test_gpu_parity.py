@@ -1216,13 +1216,15 @@ def test_numeric_resetup_matches_the_oracle_on_the_kept_patterns(small):
 
 
 def test_numeric_resetup_rejects_another_pattern(small, mini):
+    """Other sizes, or the same sizes with other column indices, are argument
+    errors (checked on the device before any value is written)."""
     with pkg.BlockSolver() as sol:
         sol.setup(small.A, small.B, small.C, small.D)
         with pytest.raises(pkg.ScrError, match="differ"):
             sol.update_values(mini.A, mini.B, mini.C, mini.D)
         A = F.BSR(small.A.br, small.A.bc, small.A.nb_rows, small.A.nb_cols, small.A.row_ptr.copy(),
                   small.A.col.copy(), small.A.val.copy())
-        r = 5
+        r = int(np.nonzero(np.diff(A.row_ptr) >= 3)[0][0])
         a, b = A.row_ptr[r], A.row_ptr[r + 1]
         A.col[a:b] = np.roll(A.col[a:b], 1)  # same sizes, another pattern
         with pytest.raises(pkg.ScrError, match="pattern"):
