@@ -218,14 +218,16 @@ def split_members(sizes, world: int) -> list[list[int]]:
 
 
 def roofline(kprof: dict | None, fp64: bool, clocks: dict, ms_step: float, hbm: float, peak_kind: str,
-             kernel: str, kernel_code: int) -> dict | None:
+             kernel: str, kernel_code: int, captured: bool = True) -> dict | None:
     """Roofline of the level-0 A product from the library's event profiler:
     algorithmic bytes (stored values and indices once, source vector once,
     destination and epilogue vectors) and flops (2 per stored scalar) of the
     profiled launches over their summed event time.  FP64: one FMA per stored
     value binds the FP64 pipe before HBM, so the bound is "alu" against 2 FMA
     per SM per clock at the sampled SM clock, with the HBM fraction beside
-    it; FP32: HBM against the measured copy bandwidth."""
+    it; FP32: HBM against the measured copy bandwidth.  `traffic` scales the
+    ncu DRAM/algorithmic ratio of the captured kernel (null for a kernel no
+    capture covers)."""
     if not kprof or kprof["timed"] <= 0:
         return None
     per_launch_s = kprof["ms"] * 1e-3 / kprof["timed"]
@@ -249,7 +251,7 @@ def roofline(kprof: dict | None, fp64: bool, clocks: dict, ms_step: float, hbm: 
     roof.update({"kernel": kernel, "kernel_code": kernel_code, "launches_per_step": kprof["launches"],
                  "timed_launches": kprof["timed"], "bytes_per_launch": bytes_pl, "us_per_launch": per_launch_s * 1e6,
                  "share_of_step": kprof["ms"] / ms_step,
-                 "traffic": ratio * bytes_pl if (ratio and kernel_code in (0, 102)) else None})
+                 "traffic": ratio * bytes_pl if (captured and ratio and kernel_code in (0, 102)) else None})
     if roof["traffic"] is not None:
         roof["traffic_note"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernel on a smaller tube, "
                                 "scaled to this launch by its algorithmic bytes")
@@ -696,7 +698,8 @@ def bifurcation_leg(args, pkg, F, torch, np, dev, stream, events, barrier, pg, a
            "inner_iters": st["a_iters"] + st["s_iters"] + st["i_iters"], "setup_ms": st["setup_ms"],
            "solve_ms": st["solve_ms"], "max_rel_res": float(np.max(rel)), "gpu_launches": int(launches),
            "roofline": roofline(kprof, False, clocks, ms, hbm, peak_kind,
-                                "level-0 A product, FP32 values, 8 interleaved right-hand sides", st["kernel_A"]),
+                                "level-0 A product, FP32 values, 8 interleaved right-hand sides", st["kernel_A"],
+                                captured=False),
            "clocks": clocks, "inputs_build_s": t_build}
     del Ad, Bd, Cd, Dd, rhs, xs, s
     return out
