@@ -1,12 +1,12 @@
 """The allocation-free block product (scr_bsr_spmv_noalloc) against the
 allocating one (scr_bsr_spmv), through the C ABI.
 
-Callers that cannot allocate device memory (graph-captured code, hosts whose
-device memory belongs to another allocator) use the allocation-free entry
-point; it must give the same product.  This file is collected after the
-others (but the full-size bifurcation) so that a run stopping at the first
-failure has run them before it; it also passes when run alone in a fresh
-process."""
+Callers that cannot let a library allocate device memory (hosts whose device
+memory belongs to another allocator or is fixed at start-up, code that must
+not call cudaFree, which waits for the whole device) use the allocation-free
+entry point; it must give the same product.  This file is collected after
+all the others so that a run stopping at the first failure has run them
+before it; it also passes when run alone in a fresh process."""
 import numpy as np
 import pytest
 
