@@ -499,7 +499,8 @@ def main(argv=None):
                "setup_ms": st["setup_ms"], "solve_ms": st["solve_ms"],
                "dofs_iters_per_s": s.n * st["outer_iters"] * 1000.0 / st["solve_ms"],
                "gpu_launches": int(launches), "clocks": clocks,
-               "kernel_A": st["kernel_A"], "kernel_Shat": st["kernel_Shat"]}
+               "kernel_A": st["kernel_A"], "kernel_Shat": st["kernel_Shat"],
+               "host_waits_per_solve": st["syncs"], "pc_from_device_loop_graph": st["pc_graph_runs"]}
         if with_mesh:
             rec.update({"mesh_iters": st["mm_iters"], "mesh_rel_res": st["mm_rel_res"],
                         "mm_setup_ms": st["mm_setup_ms"], "mm_solve_ms": st["mm_solve_ms"]})
@@ -633,7 +634,9 @@ def main(argv=None):
         "mesh_iters": head["mesh_iters"], "mesh_rel_res": head["mesh_rel_res"], "setup_ms": head["setup_ms"],
         "solve_ms": head["solve_ms"], "dofs_iters_per_s": head["dofs_iters_per_s"],
         "mm_setup_ms": head["mm_setup_ms"], "mm_solve_ms": head["mm_solve_ms"],
-        "gpu_launches": head["gpu_launches"], "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": head["gpu_launches"], "host_waits_per_solve": head["host_waits_per_solve"],
+        "pc_from_device_loop_graph": head["pc_from_device_loop_graph"],
+        "roofline": head["roofline"], "cpu_baseline": cpu, "e2e": e2e,
         "numeric_resetup": head.get("numeric_resetup"),
         "mixed": mixed, "oracle_check": oracle_check, "stenosis": sten, "bifurcation": bif,
         "batched": batched, "multi_rhs": multi, "assembly": assembly,

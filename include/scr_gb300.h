@@ -152,6 +152,17 @@ typedef struct {
                          staging vectors) for every later V-cycle; 0: every V-cycle launched
                          kernel by kernel.  V-cycles run kernel by kernel while scr_profile_begin
                          is active.  Results are the same either way. */
+  int graph_krylov;   /* device loops: each preconditioner application (Algorithm 1, SIMPLE or SIMPLEC)
+                         is recorded once per set-up as one CUDA graph and replayed; in it every
+                         intermediate and inner GMRES runs as a device-side loop (conditional WHILE
+                         and IF graph nodes: restart cycles, Arnoldi steps, restart), its convergence
+                         test evaluated on the GPU, so the host waits once per outer FGMRES iteration
+                         instead of once per inner iteration.  1: always; 0: host-driven inner loops;
+                         2 (default): device loops for block systems of at most 1,000,000 unknowns
+                         (times nrhs), where they were measured faster (small systems: 7-16 %),
+                         host-driven above (2.5M unknowns: 0.5-1.3 % slower with device loops).
+                         Direct launches while scr_profile_begin is active.  Results are the same
+                         either way. */
   int nrhs;           /* right-hand sides of the block solve: 1 (default, scr_solve) or 8
                          (scr_solve_multi: the block products act on 8 interleaved vectors at once) */
   double mm_rtol;     /* mesh CG relative residual, 1e-8 */
@@ -195,6 +206,8 @@ typedef struct {
   int syncs;                  /* host waits on device scalars */
   int kernel_A, kernel_Shat;  /* product kernel codes chosen for A and Shat in the solver
                                  precision (see scr_opts.spmv_group; 0 = heuristic) */
+  int pc_graph_runs;          /* preconditioner applications of the last solve replayed from
+                                 the recorded graph (scr_opts.graph_krylov) */
 } scr_stats;
 
 /* Fill o with the defaults listed above.  Never fails for non-NULL o. */

@@ -36,7 +36,7 @@ class Opts(C.Structure):
         ("newton", C.c_int), ("pdl", C.c_int), ("tangent_resetup", C.c_int),
         ("mapped_scalars", C.c_int),
         ("l2_prefetch", C.c_int), ("amg_coarse_bf16", C.c_int), ("cuda_graphs", C.c_int),
-        ("nrhs", C.c_int),
+        ("graph_krylov", C.c_int), ("nrhs", C.c_int),
         ("mm_rtol", C.c_double), ("mm_max_it", C.c_int), ("verbose", C.c_int),
     ]
 
@@ -70,7 +70,7 @@ class Stats(C.Structure):
         ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("mm_setup_ms", C.c_double),
         ("mm_solve_ms", C.c_double), ("kernel_launches", C.c_longlong), ("spmv_bytes", C.c_longlong),
         ("levels_A", C.c_int), ("levels_S", C.c_int), ("levels_M", C.c_int), ("syncs", C.c_int),
-        ("kernel_A", C.c_int), ("kernel_Shat", C.c_int),
+        ("kernel_A", C.c_int), ("kernel_Shat", C.c_int), ("pc_graph_runs", C.c_int),
     ]
 
     def as_dict(self) -> dict:

@@ -47,6 +47,23 @@ __global__ void k_scale_by(const T* __restrict__ x, const double* __restrict__ s
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
   for (; i < n; i += st) y[i] = a * x[i];
 }
+// y = x (times *sc when sc is given), with x and/or y a column of a basis
+// whose index is read on the device: column (*xj) of X, column (*yj + yoff)
+// of Y (stride ld); a null index pointer names the vector itself
+template <typename T>
+__global__ void k_col_copy(const T* __restrict__ X, const int* __restrict__ xj, T* __restrict__ Y,
+                           const int* __restrict__ yj, int yoff, long long ld, const double* __restrict__ sc,
+                           long long n) {
+  const T* x = xj ? X + (long long)*xj * ld : X;
+  T* y = yj ? Y + (long long)(*yj + yoff) * ld : Y;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+  if (sc) {
+    const T a = (T)*sc;
+    for (; i < n; i += st) y[i] = a * x[i];
+  } else {
+    for (; i < n; i += st) y[i] = x[i];
+  }
+}
 
 static int grid_for(long long n) {
   return (int)std::max<long long>(1, std::min<long long>(ceil_div(n, 256), 8LL * sm_count()));
@@ -239,6 +256,19 @@ void scale_by(const T* x, const double* sc, T* y, long long n, cudaStream_t s) {
 template void scale_by<double>(const double*, const double*, double*, long long, cudaStream_t);
 
 template <typename T>
+void col_copy(const T* X, const int* xj, T* Y, const int* yj, int yoff, long long ld, const double* sc, long long n,
+              cudaStream_t s) {
+  if (n <= 0) return;
+  k_col_copy<T><<<grid_for(n), 256, 0, s>>>(X, xj, Y, yj, yoff, ld, sc, n);
+  SCR_LAUNCH();
+  counters().launches++;
+}
+template void col_copy<double>(const double*, const int*, double*, const int*, int, long long, const double*,
+                               long long, cudaStream_t);
+template void col_copy<float>(const float*, const int*, float*, const int*, int, long long, const double*,
+                              long long, cudaStream_t);
+
+template <typename T>
 __global__ void k_axpby_t(T a, const T* __restrict__ x, T b, T* __restrict__ y, long long n) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
   for (; i < n; i += st) y[i] = a * x[i] + b * y[i];
@@ -328,10 +358,14 @@ __device__ __forceinline__ void store_partials_t(T (&acc)[KMAX], int k, double* 
   block_store_partials<KMAX>(d, k, partial);
 }
 
+// Counts: k, or (*kp + koff) when kp is given (a count kept on the device
+// by a loop recorded in a CUDA graph; KMAX bounds it either way).
 template <int KMAX, typename T>
 __global__ void __launch_bounds__(kRedThreads) k_multidot(const T* __restrict__ V, long long ld, int k,
                                                          const T* __restrict__ w, long long n,
-                                                         double* __restrict__ partial) {
+                                                         double* __restrict__ partial, const int* __restrict__ kp,
+                                                         int koff) {
+  if (kp) k = *kp + koff;
   T acc[KMAX];
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) acc[j] = (T)0;
@@ -349,7 +383,9 @@ __global__ void __launch_bounds__(kRedThreads) k_multidot(const T* __restrict__ 
 template <int KMAX, typename T>
 __global__ void __launch_bounds__(kRedThreads) k_cgs_update_dot(const T* __restrict__ V, long long ld, int k,
                                                                const double* __restrict__ h, T* __restrict__ w,
-                                                               long long n, double* __restrict__ partial) {
+                                                               long long n, double* __restrict__ partial,
+                                                               const int* __restrict__ kp, int koff) {
+  if (kp) k = *kp + koff;
   T hj[KMAX], acc[KMAX];
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) {
@@ -374,7 +410,9 @@ __global__ void __launch_bounds__(kRedThreads) k_cgs_update_dot(const T* __restr
 template <int KMAX, typename T>
 __global__ void __launch_bounds__(kRedThreads) k_cgs_update_norm(const T* __restrict__ V, long long ld, int k,
                                                                 const double* __restrict__ h, T* __restrict__ w,
-                                                                long long n, double* __restrict__ partial) {
+                                                                long long n, double* __restrict__ partial,
+                                                                const int* __restrict__ kp, int koff) {
+  if (kp) k = *kp + koff;
   T hj[KMAX];
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) hj[j] = j < k ? (T)h[j] : (T)0;
@@ -391,8 +429,104 @@ __global__ void __launch_bounds__(kRedThreads) k_cgs_update_norm(const T* __rest
   store_partials_t<1, T>(acc, 1, partial);
 }
 
+// Device-count variants (loops recorded in a CUDA graph): the count k is
+// read on the device, so the dot products are taken kDotTile columns at a time
+// with a fixed register tile, one pass over the rows per chunk (a single
+// pass for k <= kDotTile, the usual case of the inner solves).  Per column
+// they do the same multiply-adds in the same order as the fixed-count
+// kernels above and store the same block partial sums, so the results are
+// bit-identical; the fixed-count kernels sized for the largest count would
+// hold kMaxBasis accumulators per thread instead.
+constexpr int kDotTile = 8;
+
+// block partial sums of columns c0 .. c0 + kDotTile - 1 (those < k), as
+// block_store_partials stores them
+template <typename T>
+__device__ __forceinline__ void store_chunk_partials(const T (&acc)[kDotTile], int c0, int k, double* partial) {
+  __shared__ double sm[kRedThreads / 32][kDotTile];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < kDotTile; ++j) {
+    if (c0 + j < k) {
+      double v = warp_sum((double)acc[j]);
+      if (lane == 0) sm[wid][j] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < kDotTile && c0 + (int)threadIdx.x < k) {
+    double v = 0.0;
+#pragma unroll
+    for (int w = 0; w < kRedThreads / 32; ++w) v += sm[w][threadIdx.x];
+    partial[(long long)blockIdx.x * kMaxBasis + c0 + threadIdx.x] = v;
+  }
+  __syncthreads();  // sm is reused by the next chunk
+}
+
+template <typename T>
+__device__ __forceinline__ void chunk_dots(const T* __restrict__ V, long long ld, int c0, int k,
+                                           const T* __restrict__ w, long long n, double* __restrict__ partial) {
+  T acc[kDotTile];
+#pragma unroll
+  for (int j = 0; j < kDotTile; ++j) acc[j] = (T)0;
+  const long long st = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += st) {
+    const T wi = w[i];
+#pragma unroll
+    for (int j = 0; j < kDotTile; ++j)
+      if (c0 + j < k) acc[j] = fma(V[(c0 + j) * ld + i], wi, acc[j]);
+  }
+  store_chunk_partials<T>(acc, c0, k, partial);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_multidot_dev(const T* __restrict__ V, long long ld,
+                                                             const int* __restrict__ kp, int koff,
+                                                             const T* __restrict__ w, long long n,
+                                                             double* __restrict__ partial) {
+  const int k = *kp + koff;
+  for (int c0 = 0; c0 < k; c0 += kDotTile) chunk_dots<T>(V, ld, c0, k, w, n, partial);
+}
+
+// w -= V h (columns in increasing order), then the dots of the updated w
+// (NORM: its squared norm only)
+template <bool NORM, typename T>
+__global__ void __launch_bounds__(kRedThreads) k_cgs_update_dev(const T* __restrict__ V, long long ld,
+                                                               const int* __restrict__ kp, int koff,
+                                                               const double* __restrict__ h, T* __restrict__ w,
+                                                               long long n, double* __restrict__ partial) {
+  __shared__ T hs[kMaxBasis + 1];
+  const int k = *kp + koff;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = (T)h[j];
+  __syncthreads();
+  T acc[kDotTile];
+#pragma unroll
+  for (int j = 0; j < kDotTile; ++j) acc[j] = (T)0;
+  const long long st = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += st) {
+    T wi = w[i];
+#pragma unroll 4
+    for (int j = 0; j < k; ++j) wi = fma(-V[j * ld + i], hs[j], wi);
+    w[i] = wi;
+    if constexpr (NORM) {
+      acc[0] = fma(wi, wi, acc[0]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < kDotTile; ++j)
+        if (j < k) acc[j] = fma(V[j * ld + i], wi, acc[j]);
+    }
+  }
+  if constexpr (NORM) {
+    store_chunk_partials<T>(acc, 0, 1, partial);
+  } else {
+    store_chunk_partials<T>(acc, 0, k, partial);
+    for (int c0 = kDotTile; c0 < k; c0 += kDotTile) chunk_dots<T>(V, ld, c0, k, w, n, partial);
+  }
+}
+
 // out[j] = sum_b partial[b][j], fixed order
-__global__ void k_reduce_partials(const double* __restrict__ partial, int nblk, int k, double* __restrict__ out) {
+__global__ void k_reduce_partials(const double* __restrict__ partial, int nblk, int k, double* __restrict__ out,
+                                  const int* __restrict__ kp, int koff) {
+  if (kp) k = *kp + koff;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = wid; j < k; j += nw) {
     double v = 0.0;
@@ -404,18 +538,18 @@ __global__ void k_reduce_partials(const double* __restrict__ partial, int nblk, 
 
 template <int KMAX, typename T>
 static void launch_multidot(const T* V, long long ld, int k, const T* w, long long n, const Reducer& r,
-                            cudaStream_t s) {
-  k_multidot<KMAX, T><<<r.nblk, kRedThreads, 0, s>>>(V, ld, k, w, n, r.partial);
+                            cudaStream_t s, const int* kp, int koff) {
+  k_multidot<KMAX, T><<<r.nblk, kRedThreads, 0, s>>>(V, ld, k, w, n, r.partial, kp, koff);
 }
 template <int KMAX, typename T>
 static void launch_cgs_dot(const T* V, long long ld, int k, const double* h, T* w, long long n, const Reducer& r,
-                           cudaStream_t s) {
-  k_cgs_update_dot<KMAX, T><<<r.nblk, kRedThreads, 0, s>>>(V, ld, k, h, w, n, r.partial);
+                           cudaStream_t s, const int* kp, int koff) {
+  k_cgs_update_dot<KMAX, T><<<r.nblk, kRedThreads, 0, s>>>(V, ld, k, h, w, n, r.partial, kp, koff);
 }
 template <int KMAX, typename T>
 static void launch_cgs_norm(const T* V, long long ld, int k, const double* h, T* w, long long n, const Reducer& r,
-                            cudaStream_t s) {
-  k_cgs_update_norm<KMAX, T><<<r.nblk, kRedThreads, 0, s>>>(V, ld, k, h, w, n, r.partial);
+                            cudaStream_t s, const int* kp, int koff) {
+  k_cgs_update_norm<KMAX, T><<<r.nblk, kRedThreads, 0, s>>>(V, ld, k, h, w, n, r.partial, kp, koff);
 }
 
 #define SCR_KDISPATCH(FN, T, k, ...)                \
@@ -428,39 +562,42 @@ static void launch_cgs_norm(const T* V, long long ld, int k, const double* h, T*
     else FN<kMaxBasis, T>(__VA_ARGS__);             \
   } while (0)
 
-static void reduce(const Reducer& r, int k, double* out, cudaStream_t s) {
-  k_reduce_partials<<<1, 256, 0, s>>>(r.partial, r.nblk, k, out);
+static void reduce(const Reducer& r, int k, double* out, cudaStream_t s, const int* kp = nullptr, int koff = 0) {
+  k_reduce_partials<<<1, 256, 0, s>>>(r.partial, r.nblk, k, out, kp, koff);
   SCR_LAUNCH();
   counters().launches += 2;
 }
 
 template <typename T>
 void norm2(const T* x, long long n, double* out, const Reducer& r, cudaStream_t s) {
-  launch_multidot<1, T>(x, 0, 1, x, n, r, s);
+  launch_multidot<1, T>(x, 0, 1, x, n, r, s, nullptr, 0);
   SCR_LAUNCH();
   reduce(r, 1, out, s);
 }
 
 template <typename T>
 void multidot(const T* V, long long ld, int k, const T* w, long long n, double* out, const Reducer& r,
-              cudaStream_t s) {
-  SCR_KDISPATCH(launch_multidot, T, k, V, ld, k, w, n, r, s);
+              cudaStream_t s, const int* kp, int koff) {
+  if (kp) k_multidot_dev<T><<<r.nblk, kRedThreads, 0, s>>>(V, ld, kp, koff, w, n, r.partial);
+  else SCR_KDISPATCH(launch_multidot, T, k, V, ld, k, w, n, r, s, kp, koff);
   SCR_LAUNCH();
-  reduce(r, k, out, s);
+  reduce(r, k, out, s, kp, koff);
 }
 
 template <typename T>
 void cgs_update_dot(const T* V, long long ld, int k, const double* h, T* w, long long n, double* out,
-                    const Reducer& r, cudaStream_t s) {
-  SCR_KDISPATCH(launch_cgs_dot, T, k, V, ld, k, h, w, n, r, s);
+                    const Reducer& r, cudaStream_t s, const int* kp, int koff) {
+  if (kp) k_cgs_update_dev<false, T><<<r.nblk, kRedThreads, 0, s>>>(V, ld, kp, koff, h, w, n, r.partial);
+  else SCR_KDISPATCH(launch_cgs_dot, T, k, V, ld, k, h, w, n, r, s, kp, koff);
   SCR_LAUNCH();
-  reduce(r, k, out, s);
+  reduce(r, k, out, s, kp, koff);
 }
 
 template <typename T>
 void cgs_update_norm(const T* V, long long ld, int k, const double* h, T* w, long long n, double* out,
-                     const Reducer& r, cudaStream_t s) {
-  SCR_KDISPATCH(launch_cgs_norm, T, k, V, ld, k, h, w, n, r, s);
+                     const Reducer& r, cudaStream_t s, const int* kp, int koff) {
+  if (kp) k_cgs_update_dev<true, T><<<r.nblk, kRedThreads, 0, s>>>(V, ld, kp, koff, h, w, n, r.partial);
+  else SCR_KDISPATCH(launch_cgs_norm, T, k, V, ld, k, h, w, n, r, s, kp, koff);
   SCR_LAUNCH();
   reduce(r, 1, out, s);
 }
@@ -468,11 +605,11 @@ void cgs_update_norm(const T* V, long long ld, int k, const double* h, T* w, lon
 #define SCR_INST_BLAS(T)                                                                                      \
   template void norm2<T>(const T*, long long, double*, const Reducer&, cudaStream_t);                         \
   template void multidot<T>(const T*, long long, int, const T*, long long, double*, const Reducer&,           \
-                            cudaStream_t);                                                                    \
+                            cudaStream_t, const int*, int);                                                   \
   template void cgs_update_dot<T>(const T*, long long, int, const double*, T*, long long, double*,            \
-                                  const Reducer&, cudaStream_t);                                              \
+                                  const Reducer&, cudaStream_t, const int*, int);                             \
   template void cgs_update_norm<T>(const T*, long long, int, const double*, T*, long long, double*,           \
-                                   const Reducer&, cudaStream_t);
+                                   const Reducer&, cudaStream_t, const int*, int);
 SCR_INST_BLAS(double)
 SCR_INST_BLAS(float)
 
@@ -482,7 +619,8 @@ SCR_INST_BLAS(float)
 // lane 0 applies the rotations and the new one there (the same operations
 // in the same order as a single thread on the state), the lanes write the
 // column back.
-__global__ void k_arnoldi_finalize(ArnoldiState* st, int j, double* host_rel) {
+__global__ void k_arnoldi_finalize(ArnoldiState* st, int j, double* host_rel, const int* __restrict__ jp) {
+  if (jp) j = *jp;
   constexpr int ldh = kMaxBasis + 1;
   __shared__ double h[kMaxBasis + 2], rc[kMaxBasis], rs[kMaxBasis];
   const int t = threadIdx.x;
@@ -520,15 +658,17 @@ __global__ void k_arnoldi_finalize(ArnoldiState* st, int j, double* host_rel) {
     // happy breakdown: the new direction vanished relative to the column
     st->breakdown = (hn <= 1e-300 || d == 0.0) ? 1 : 0;
     st->inv_hnext = hn > 1e-300 ? 1.0 / hn : 0.0;
-    host_rel[0] = st->rel;
-    host_rel[1] = (double)st->breakdown;
+    if (host_rel) {
+      host_rel[0] = st->rel;
+      host_rel[1] = (double)st->breakdown;
+    }
   }
   __syncwarp();
   for (int i = t; i <= j + 1; i += 32) Hj[i] = h[i];
 }
 
-void arnoldi_finalize(ArnoldiState* st, int j, double* host_rel, cudaStream_t s) {
-  k_arnoldi_finalize<<<1, 32, 0, s>>>(st, j, host_rel);
+void arnoldi_finalize(ArnoldiState* st, int j, double* host_rel, cudaStream_t s, const int* jp) {
+  k_arnoldi_finalize<<<1, 32, 0, s>>>(st, j, host_rel, jp);
   SCR_LAUNCH();
   counters().launches++;
 }
@@ -542,8 +682,10 @@ __global__ void k_arnoldi_start(ArnoldiState* st, int first, double* host_rel) {
   st->inv_hnext = beta > 0.0 ? 1.0 / beta : 0.0;
   st->rel = st->bnorm > 0.0 ? beta / st->bnorm : 0.0;
   st->breakdown = 0;
-  host_rel[0] = st->rel;
-  host_rel[1] = st->bnorm;
+  if (host_rel) {
+    host_rel[0] = st->rel;
+    host_rel[1] = st->bnorm;
+  }
 }
 
 void arnoldi_start(ArnoldiState* st, int first, double* host_rel, cudaStream_t s) {
@@ -552,7 +694,8 @@ void arnoldi_start(ArnoldiState* st, int first, double* host_rel, cudaStream_t s
   counters().launches++;
 }
 
-__global__ void k_backsolve(ArnoldiState* st, int k) {
+__global__ void k_backsolve(ArnoldiState* st, int k, const int* __restrict__ kp) {
+  if (kp) k = *kp;
   constexpr int ldh = kMaxBasis + 1;
   for (int i = k - 1; i >= 0; --i) {
     double v = st->g[i];
@@ -564,7 +707,8 @@ __global__ void k_backsolve(ArnoldiState* st, int k) {
 
 template <int KMAX, typename T>
 __global__ void k_update_x(const ArnoldiState* __restrict__ st, int k, const T* __restrict__ Z, long long ld,
-                           T* __restrict__ x, long long n) {
+                           T* __restrict__ x, long long n, const int* __restrict__ kp) {
+  if (kp) k = *kp;
   T y[KMAX];
 #pragma unroll
   for (int j = 0; j < KMAX; ++j) y[j] = j < k ? (T)st->y[j] : (T)0;
@@ -579,21 +723,24 @@ __global__ void k_update_x(const ArnoldiState* __restrict__ st, int k, const T* 
 }
 template <int KMAX, typename T>
 static void launch_update_x(const ArnoldiState* st, int k, const T* Z, long long ld, T* x, long long n,
-                            cudaStream_t s) {
-  k_update_x<KMAX, T><<<grid_for(n), 256, 0, s>>>(st, k, Z, ld, x, n);
+                            cudaStream_t s, const int* kp) {
+  k_update_x<KMAX, T><<<grid_for(n), 256, 0, s>>>(st, k, Z, ld, x, n, kp);
 }
 
 template <typename T>
-void gmres_update(ArnoldiState* st, int k, const T* Z, long long ld, T* x, long long n, cudaStream_t s) {
+void gmres_update(ArnoldiState* st, int k, const T* Z, long long ld, T* x, long long n, cudaStream_t s,
+                  const int* kp) {
   if (k <= 0) return;
-  k_backsolve<<<1, 1, 0, s>>>(st, k);
+  k_backsolve<<<1, 1, 0, s>>>(st, k, kp);
   SCR_LAUNCH();
-  SCR_KDISPATCH(launch_update_x, T, k, st, k, Z, ld, x, n, s);
+  SCR_KDISPATCH(launch_update_x, T, k, st, k, Z, ld, x, n, s, kp);
   SCR_LAUNCH();
   counters().launches += 2;
 }
-template void gmres_update<double>(ArnoldiState*, int, const double*, long long, double*, long long, cudaStream_t);
-template void gmres_update<float>(ArnoldiState*, int, const float*, long long, float*, long long, cudaStream_t);
+template void gmres_update<double>(ArnoldiState*, int, const double*, long long, double*, long long, cudaStream_t,
+                                   const int*);
+template void gmres_update<float>(ArnoldiState*, int, const float*, long long, float*, long long, cudaStream_t,
+                                  const int*);
 
 // ------------------------------------------------------------ CG
 __global__ void k_cg_scalar(CgState* st, int mode, double* host_rel) {

@@ -104,6 +104,7 @@ class DeviceArena {
   }
   size_t bytes() const { return bytes_; }
   void set_stream(cudaStream_t s) { stream_ = s; }
+  cudaStream_t stream() const { return stream_; }
 
  private:
   cudaStream_t stream_;

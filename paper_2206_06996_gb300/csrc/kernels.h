@@ -9,6 +9,8 @@ namespace scr {
 struct LaunchCounter {
   long long launches = 0;
   long long spmv_bytes = 0;
+  long long vcycles[3] = {0, 0, 0};  // V-cycles recorded into a graph, by hierarchy (A, Shat, mesh)
+  long long fixed[2] = {0, 0};       // fixed-count A-solve steps recorded into a graph (intermediate, inner)
 };
 LaunchCounter& counters();
 
@@ -226,31 +228,42 @@ void cheb_zero(const T* b, const T* d, T* r, T* dv, T* x, double inv_theta, long
 // FP32 vectors are summed per thread in FP32, across threads in FP64.
 template <typename T>
 void norm2(const T* x, long long n, double* out, const Reducer& r, cudaStream_t s);
+// The Gram-Schmidt and update kernels take their count k from the host, or,
+// with kp given (loops recorded in a CUDA graph), from the device as
+// *kp + koff, with k then an upper bound of it.
 // out[j] = V_j . w, j < k (V vectors of length n with stride ld)
 template <typename T>
 void multidot(const T* V, long long ld, int k, const T* w, long long n, double* out, const Reducer& r,
-              cudaStream_t s);
+              cudaStream_t s, const int* kp = nullptr, int koff = 0);
 // w -= sum_j V_j h[j]; then out[j] = V_j . w (second Gram-Schmidt pass)
 template <typename T>
 void cgs_update_dot(const T* V, long long ld, int k, const double* h, T* w, long long n, double* out,
-                    const Reducer& r, cudaStream_t s);
+                    const Reducer& r, cudaStream_t s, const int* kp = nullptr, int koff = 0);
 // w -= sum_j V_j h[j]; then out = ||w||^2
 template <typename T>
 void cgs_update_norm(const T* V, long long ld, int k, const double* h, T* w, long long n, double* out,
-                     const Reducer& r, cudaStream_t s);
-// Arnoldi bookkeeping for column j: H(:,j) = h1 + h2, H(j+1,j) = sqrt(nrm2),
-// Givens rotations, residual estimate st->rel = |g_{j+1}| / bnorm, copied
-// to *host_rel (mapped host memory).
-void arnoldi_finalize(ArnoldiState* st, int j, double* host_rel, cudaStream_t s);
+                     const Reducer& r, cudaStream_t s, const int* kp = nullptr, int koff = 0);
+// Arnoldi bookkeeping for column j (or *jp when jp is given): H(:,j) = h1 + h2,
+// H(j+1,j) = sqrt(nrm2), Givens rotations, residual estimate
+// st->rel = |g_{j+1}| / bnorm, copied to *host_rel (mapped host memory) when
+// host_rel is not null.
+void arnoldi_finalize(ArnoldiState* st, int j, double* host_rel, cudaStream_t s, const int* jp = nullptr);
 // GMRES start: beta = sqrt(st->nrm2); g = beta e_1; bnorm set when first;
-// writes beta/bnorm to *host_rel
+// writes beta/bnorm to *host_rel when it is not null
 void arnoldi_start(ArnoldiState* st, int first, double* host_rel, cudaStream_t s);
 // y = x * (*scale) with scale a device scalar
 template <typename T>
 void scale_by(const T* x, const double* scale, T* y, long long n, cudaStream_t s);
-// y = H^{-1} g (k x k upper triangle), then x += sum_j y_j Z_j
+// y = x (times *sc when sc is not null); x is column *xj of X when xj is
+// given, y column *yj + yoff of Y when yj is given (columns ld apart)
 template <typename T>
-void gmres_update(ArnoldiState* st, int k, const T* Z, long long ld, T* x, long long n, cudaStream_t s);
+void col_copy(const T* X, const int* xj, T* Y, const int* yj, int yoff, long long ld, const double* sc, long long n,
+              cudaStream_t s);
+// y = H^{-1} g (k x k upper triangle, k = *kp when kp is given), then
+// x += sum_j y_j Z_j
+template <typename T>
+void gmres_update(ArnoldiState* st, int k, const T* Z, long long ld, T* x, long long n, cudaStream_t s,
+                  const int* kp = nullptr);
 
 // CG helpers: scalars on the device
 struct CgState {

@@ -84,6 +84,11 @@ struct HostScalars {
   HostScalars& operator=(const HostScalars&) = delete;
 };
 
+// nesting depth of Krylov-loop captures in progress on this thread: inside
+// one, V-cycles run as plain launches (recorded) and GMRES solves record
+// their loops inline
+static thread_local int g_capture_depth = 0;
+
 // ------------------------------------------------------------ AMG hierarchy
 struct Level {
   DBsr<double> A, P, R;
@@ -159,6 +164,7 @@ struct GraphExecDeleter {
 using GraphExecPtr = std::unique_ptr<CUgraphExec_st, GraphExecDeleter>;
 
 struct Hierarchy {
+  int slot = 0;  // 0: A, 1: Shat, 2: mesh (the recorded V-cycle counters)
   int bs = 1, nrhs = 1, nu = 1;
   int smoother = SCR_SMOOTH_CHEB, degree = 3;
   double cheb_theta_inv = 0.0;
@@ -715,6 +721,11 @@ struct Hierarchy {
 
   template <typename T>
   void apply(const T* b, T* x, cudaStream_t s) {
+    if (g_capture_depth > 0) {  // recorded into a graph: counted at each replay
+      cycle<T>(0, b, x, s);
+      counters().vcycles[slot]++;
+      return;
+    }
     ++vcycles;
     // the per-launch event profiler needs the launches themselves
     if (use_graph && !graph_failed && !profiler().active) {
@@ -733,6 +744,174 @@ struct Hierarchy {
   }
 };
 
+// ------------------------------------------------------------ device loops
+// A GMRES solve can be recorded into a CUDA graph with its control flow on
+// the device (option graph_krylov): a WHILE node over the restart cycles
+// holds a WHILE node over the Arnoldi steps (copy of v_j, preconditioner,
+// operator, the Gram-Schmidt passes, the Givens update, v_{j+1}), then the
+// solution update and an IF node with the restart.  One-thread kernels set
+// each node's condition from the residual estimate on the device, with the
+// same tests, in the same order, as the host-driven loop (Gmres::solve), so
+// both run the same kernels on the same data.  Every Arnoldi step counts
+// against the iteration cap and every cycle against a cycle cap, so each
+// loop ends after at most maxit body runs whatever the estimates are.
+struct KrylovLoop {
+  int j;          // Arnoldi step inside the current cycle
+  int iters;      // Arnoldi steps of the current solve
+  int cycles;     // restart cycles of the current solve
+  int nonfinite;  // 1 when an estimate was NaN or infinite
+  double rel;     // last residual estimate
+  // since the last reset (read back once per outer solve for the counters)
+  long long tot_iters, tot_solves, tot_cycles, tot_restarts;
+};
+
+// streams that record conditional bodies, one per nesting depth, created
+// before the outermost capture begins
+constexpr int kMaxCaptureDepth = 8;
+static thread_local cudaStream_t g_capture_streams[kMaxCaptureDepth + 1] = {};
+
+__global__ void k_loop_begin(const ArnoldiState* __restrict__ st, KrylovLoop* L, cudaGraphConditionalHandle h_outer) {
+  const double b = st->bnorm;
+  L->j = 0;
+  L->iters = 0;
+  L->cycles = 0;
+  L->nonfinite = isfinite(b) ? 0 : 1;
+  L->rel = isfinite(b) ? 0.0 : b;
+  L->tot_solves++;
+  // b = 0 gives x = 0 and a NaN or infinite b stops at once, as on the host
+  cudaGraphSetConditional(h_outer, (isfinite(b) && b > 0.0) ? 1u : 0u);
+}
+__global__ void k_loop_arm(KrylovLoop* L, cudaGraphConditionalHandle h_inner) {
+  L->j = 0;
+  L->tot_cycles++;
+  cudaGraphSetConditional(h_inner, 1u);
+}
+__global__ void k_loop_next(const ArnoldiState* __restrict__ st, KrylovLoop* L, cudaGraphConditionalHandle h_inner,
+                            double tol, int m, int maxit) {
+  const int j = L->j + 1, it = L->iters + 1;
+  L->j = j;
+  L->iters = it;
+  L->tot_iters++;
+  const double r = st->rel;
+  L->rel = r;
+  const bool fin = isfinite(r);
+  if (!fin) {  // the host loop returns here without the update: a zero count skips it
+    L->nonfinite = 1;
+    L->j = 0;
+  }
+  const bool go = fin && !(r <= tol) && st->breakdown == 0 && j < m && it < maxit;
+  cudaGraphSetConditional(h_inner, go ? 1u : 0u);
+}
+__global__ void k_loop_after(const ArnoldiState* __restrict__ st, KrylovLoop* L, cudaGraphConditionalHandle h_outer,
+                             cudaGraphConditionalHandle h_restart, double tol, int maxit) {
+  const int c = L->cycles + 1;
+  L->cycles = c;
+  const double r = st->rel;
+  const bool fin = isfinite(r);
+  const bool done = !fin || r <= tol || st->breakdown != 0 || L->iters >= maxit || c >= maxit;
+  if (!done) L->tot_restarts++;
+  cudaGraphSetConditional(h_outer, done ? 0u : 1u);
+  cudaGraphSetConditional(h_restart, done ? 0u : 1u);
+}
+
+// the graph being recorded on a capturing stream
+static cudaGraph_t capturing_graph(cudaStream_t cs) {
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  SCR_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, nullptr, nullptr, nullptr));
+  if (cst != cudaStreamCaptureStatusActive || !g) throw CudaError{cudaErrorStreamCaptureInvalidated, "capture"};
+  return g;
+}
+
+static cudaGraphConditionalHandle make_handle(cudaGraph_t g) {
+  cudaGraphConditionalHandle hnd = 0;
+  SCR_CUDA(cudaGraphConditionalHandleCreate(&hnd, g, 0, cudaGraphCondAssignDefault));
+  return hnd;
+}
+
+// appends a conditional node (WHILE or IF, condition hnd) after the work
+// recorded so far on the capturing stream cs, records its body with body(bs)
+// on the stream of the next nesting depth, and continues cs after the node
+template <class F>
+static void record_conditional(cudaStream_t cs, cudaGraphConditionalHandle hnd, cudaGraphConditionalNodeType type,
+                               F&& body) {
+  cudaStreamCaptureStatus cst = cudaStreamCaptureStatusNone;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  SCR_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &g, &deps, nullptr, &nd));
+  if (cst != cudaStreamCaptureStatusActive || !g) throw CudaError{cudaErrorStreamCaptureInvalidated, "capture"};
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = hnd;
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  SCR_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+  SCR_CUDA(cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  if (g_capture_depth >= kMaxCaptureDepth) throw CudaError{cudaErrorStreamCaptureUnsupported, "capture depth"};
+  cudaStream_t bs = g_capture_streams[g_capture_depth];
+  SCR_CUDA(cudaStreamBeginCaptureToGraph(bs, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeRelaxed));
+  ++g_capture_depth;
+  try {
+    body(bs);
+  } catch (...) {
+    --g_capture_depth;
+    cudaGraph_t tmp = nullptr;
+    cudaStreamEndCapture(bs, &tmp);
+    throw;
+  }
+  --g_capture_depth;
+  cudaGraph_t out = nullptr;
+  SCR_CUDA(cudaStreamEndCapture(bs, &out));
+}
+
+// records rec(cs) on a private stream and instantiates it; null when the
+// capture or the instantiation fails (the caller then runs eagerly)
+template <class F>
+static cudaGraphExec_t capture_exec(F&& rec) {
+  for (int d = 0; d <= kMaxCaptureDepth; ++d)
+    if (!g_capture_streams[d] && cudaStreamCreateWithFlags(&g_capture_streams[d], cudaStreamNonBlocking) != cudaSuccess) {
+      g_capture_streams[d] = nullptr;
+      cudaGetLastError();
+      return nullptr;
+    }
+  cudaStream_t cs = g_capture_streams[kMaxCaptureDepth];
+  const LaunchCounter c0 = counters();
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  bool ok = true;
+  ++g_capture_depth;
+  try {
+    rec(cs);
+  } catch (const CudaError&) {
+    ok = false;
+  } catch (const std::exception&) {
+    ok = false;
+  }
+  --g_capture_depth;
+  counters() = c0;  // nothing has run yet
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(cs, &g);
+  cudaGraphExec_t ex = nullptr;
+  if (ok && e == cudaSuccess && g && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) ex = nullptr;
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  return ex;
+}
+
+static LaunchCounter diff(const LaunchCounter& a, const LaunchCounter& b) {
+  LaunchCounter d;
+  d.launches = a.launches - b.launches;
+  d.spmv_bytes = a.spmv_bytes - b.spmv_bytes;
+  for (int i = 0; i < 3; ++i) d.vcycles[i] = a.vcycles[i] - b.vcycles[i];
+  for (int i = 0; i < 2; ++i) d.fixed[i] = a.fixed[i] - b.fixed[i];
+  return d;
+}
+
 // ------------------------------------------------------------ GMRES
 template <typename T>
 struct Gmres {
@@ -742,6 +921,14 @@ struct Gmres {
   ArnoldiState* st = nullptr;
   HostScalars hs;
   int syncs = 0;
+  // device loop (emit): the loop's counters, the preconditioner's input and
+  // output in the recorded Arnoldi step, and the library launches / modelled
+  // bytes of one prologue, Arnoldi step, cycle end and restart (nested
+  // loops excluded: they count their own)
+  KrylovLoop* L = nullptr;
+  T *pin = nullptr, *pout = nullptr;
+  LaunchCounter sec[4];
+  bool recorded = false;
 
   void init(DeviceArena& a, long long n_, int m_) {
     n = n_;
@@ -750,6 +937,94 @@ struct Gmres {
     Z = a.alloc<T>((size_t)m * n + 1);
     w = a.alloc<T>(n + 1);
     st = a.alloc<ArnoldiState>(1);
+    L = a.alloc<KrylovLoop>(1);
+    pin = a.alloc<T>(n + 1);
+    pout = a.alloc<T>(n + 1);
+    SCR_CUDA(cudaMemsetAsync(L, 0, sizeof(KrylovLoop), a.stream()));
+    recorded = false;
+  }
+
+  using OpS = std::function<void(const T*, T*, cudaStream_t)>;
+
+  // records the solve of op x = b (x0 = 0, restarted every m steps, to tol
+  // or maxit steps) into the graph being captured on cs
+  void emit(cudaStream_t cs, const OpS& op, const OpS& pc, const T* b, T* x, double tol, int maxit,
+            const Reducer& red) {
+    const LaunchCounter c0 = counters();
+    fill<T>(x, (T)0, n, cs);
+    norm2<T>(b, n, &st->nrm2, red, cs);
+    arnoldi_start(st, 1, nullptr, cs);
+    scale_by<T>(b, &st->inv_hnext, V, n, cs);
+    const cudaGraphConditionalHandle h_outer = make_handle(capturing_graph(cs));
+    k_loop_begin<<<1, 1, 0, cs>>>(st, L, h_outer);
+    SCR_LAUNCH();
+    counters().launches++;
+    sec[0] = diff(counters(), c0);
+    record_conditional(cs, h_outer, cudaGraphCondTypeWhile, [&](cudaStream_t os) {
+      const LaunchCounter c1 = counters();
+      const cudaGraph_t go = capturing_graph(os);
+      const cudaGraphConditionalHandle h_inner = make_handle(go), h_restart = make_handle(go);
+      k_loop_arm<<<1, 1, 0, os>>>(L, h_inner);
+      SCR_LAUNCH();
+      counters().launches++;
+      const LaunchCounter arm = diff(counters(), c1);
+      record_conditional(os, h_inner, cudaGraphCondTypeWhile, [&](cudaStream_t is) {
+        const LaunchCounter c2 = counters();
+        col_copy<T>(V, &L->j, pin, nullptr, 0, n, nullptr, n, is);
+        pc(pin, pout, is);
+        col_copy<T>(pout, nullptr, Z, &L->j, 0, n, nullptr, n, is);
+        op(pout, w, is);
+        multidot<T>(V, n, m, w, n, st->h1, red, is, &L->j, 1);
+        cgs_update_dot<T>(V, n, m, st->h1, w, n, st->h2, red, is, &L->j, 1);
+        cgs_update_norm<T>(V, n, m, st->h2, w, n, &st->nrm2, red, is, &L->j, 1);
+        arnoldi_finalize(st, 0, nullptr, is, &L->j);
+        col_copy<T>(w, nullptr, V, &L->j, 1, n, &st->inv_hnext, n, is);
+        k_loop_next<<<1, 1, 0, is>>>(st, L, h_inner, tol, m, maxit);
+        SCR_LAUNCH();
+        counters().launches++;
+        sec[1] = diff(counters(), c2);
+      });
+      const LaunchCounter c3 = counters();
+      gmres_update<T>(st, m, Z, n, x, n, os, &L->j);
+      k_loop_after<<<1, 1, 0, os>>>(st, L, h_outer, h_restart, tol, maxit);
+      SCR_LAUNCH();
+      counters().launches++;
+      sec[2] = diff(counters(), c3);
+      sec[2].launches += arm.launches;  // k_loop_arm: no V-cycle, no product
+      record_conditional(os, h_restart, cudaGraphCondTypeIf, [&](cudaStream_t rs) {
+        const LaunchCounter c4 = counters();
+        op(x, w, rs);
+        axpby_t<T>(1.0, b, -1.0, w, n, rs);
+        norm2<T>(w, n, &st->nrm2, red, rs);
+        arnoldi_start(st, 0, nullptr, rs);
+        scale_by<T>(w, &st->inv_hnext, V, n, rs);
+        sec[3] = diff(counters(), c4);
+      });
+    });
+    counters() = c0;  // counted from the loop's own counters when read back
+    recorded = true;
+  }
+
+  // counters of the device loops since the last reset_loop: adds their
+  // library launches and modelled bytes to the process counters, their
+  // V-cycles and fixed-count A-solve steps to acc, and returns the Arnoldi
+  // steps run
+  long long collect(cudaStream_t s, LaunchCounter& acc) {
+    if (!L || !recorded) return 0;
+    KrylovLoop hL{};
+    SCR_CUDA(cudaMemcpyAsync(&hL, L, sizeof hL, cudaMemcpyDeviceToHost, s));
+    SCR_CUDA(cudaStreamSynchronize(s));
+    const long long c[4] = {hL.tot_solves, hL.tot_iters, hL.tot_cycles, hL.tot_restarts};
+    for (int i = 0; i < 4; ++i) {
+      counters().launches += c[i] * sec[i].launches;
+      counters().spmv_bytes += c[i] * sec[i].spmv_bytes;
+      for (int k = 0; k < 3; ++k) acc.vcycles[k] += c[i] * sec[i].vcycles[k];
+      for (int k = 0; k < 2; ++k) acc.fixed[k] += c[i] * sec[i].fixed[k];
+    }
+    return hL.tot_iters;
+  }
+  void reset_loop(cudaStream_t s) {
+    if (L && recorded) SCR_CUDA(cudaMemsetAsync(L, 0, sizeof(KrylovLoop), s));
   }
 
   using Op = std::function<void(const T*, T*)>;
@@ -902,6 +1177,20 @@ struct scr_ctx {
   std::vector<int> b_nv, b_np, b_vo, b_po;
   std::vector<double> b_rel;
   double* b_norms = nullptr;  // device, 2 per member
+  // the preconditioner application as one CUDA graph (option graph_krylov):
+  // recorded from pc_r to pc_y at its first use after a set-up (epoch), with
+  // every inner GMRES as a device loop; the library launches, modelled bytes
+  // and A solves of its straight-line part, added at each replay
+  long long graph_epoch = 0, pc_epoch = -1;
+  bool pc_failed = false;
+  GraphExecPtr pc_exec;
+  double *pc_r = nullptr, *pc_y = nullptr;
+  LaunchCounter pc_sec;
+  int pc_a_solves = 0;
+  scr_ctx() {
+    hS.slot = 1;
+    hM.slot = 2;
+  }
 };
 
 namespace {
@@ -1026,6 +1315,36 @@ PcView<float> view32(scr_ctx* h) {
                        h->yhatf, h->rp2f, h->rv2f, h->xbarf, h->xtf, h->rrf, h->rtf, h->dAinvf, h->out_af};
 }
 
+// runs the context's launches on another stream for its lifetime (the
+// stream a Krylov-loop capture records on)
+struct StreamSwap {
+  scr_ctx* h;
+  cudaStream_t old;
+  StreamSwap(scr_ctx* h_, cudaStream_t s) : h(h_), old(h_->s) { h->s = s; }
+  ~StreamSwap() { h->s = old; }
+  StreamSwap(const StreamSwap&) = delete;
+  StreamSwap& operator=(const StreamSwap&) = delete;
+};
+
+// one GMRES solve of the path: recorded as a device loop when a Krylov-loop
+// capture is in progress (returns 0: its steps are counted on the device),
+// else the host-driven loop (returns its steps)
+template <typename T>
+int gmres_run(scr_ctx* h, Gmres<T>* g, const typename Gmres<T>::OpS& op, const typename Gmres<T>::OpS& pc,
+              const T* b, T* x, double tol, int maxit) {
+  if (g_capture_depth > 0) {
+    g->emit(h->s, op, pc, b, x, tol, maxit, h->red);
+    return 0;
+  }
+  cudaStream_t s = h->s;
+  typename Gmres<T>::Op o = [&](const T* a, T* y) { op(a, y, s); };
+  typename Gmres<T>::Op p = [&](const T* a, T* y) { pc(a, y, s); };
+  int it = 0;
+  double rel = 0;
+  g->solve(o, &p, b, x, tol, maxit, h->red, s, &it, &rel);
+  return it;
+}
+
 // y += sign * sum_j c_j a_j (a_j^T x) on the velocity rows (the outlets'
 // rank-1 terms of the momentum block; one dot and one update per outlet)
 template <typename T>
@@ -1082,15 +1401,18 @@ template <typename T>
 int solve_A(scr_ctx* h, PcView<T>& v, Gmres<T>* g, int k, double rtol, int maxit, const T* b, T* x) {
   if (k > 0) {
     richardson_A<T>(h, v, k, b, x);
+    if (g_capture_depth > 0) {  // recorded: counted at each replay
+      counters().fixed[g == v.gI ? 1 : 0] += k;
+      return 0;
+    }
     return k;
   }
-  cudaStream_t s = h->s;
-  typename Gmres<T>::Op opA = [&](const T* xx, T* y) { apply_A<T>(h, v, xx, y); };
-  typename Gmres<T>::Op pcA = [&](const T* bb, T* xx) { v.hA->template apply<T>(bb, xx, s); };
-  int it = 0;
-  double rel = 0;
-  g->solve(opA, &pcA, b, x, rtol, maxit, h->red, s, &it, &rel);
-  return it;
+  typename Gmres<T>::OpS opA = [&](const T* xx, T* y, cudaStream_t cs) {
+    StreamSwap sw(h, cs);
+    apply_A<T>(h, v, xx, y);
+  };
+  typename Gmres<T>::OpS pcA = [&](const T* bb, T* xx, cudaStream_t cs) { v.hA->template apply<T>(bb, xx, cs); };
+  return gmres_run<T>(h, g, opA, pcA, b, x, rtol, maxit);
 }
 
 // Algorithm 2: y_p = D x_p - C A^{-1} (B x_p), A^{-1} by inner GMRES + P_I
@@ -1112,10 +1434,11 @@ void apply_pc(scr_ctx* h, PcView<T>& v, const T* r, T* y) {
   const T* rp = r + nv3;
   T* yv = y;
   T* yp = y + nv3;
-  typename Gmres<T>::Op opS = [&](const T* x, T* o) { apply_S<T>(h, v, x, o); };
-  typename Gmres<T>::Op pcS = [&](const T* b, T* x) { v.hS->template apply<T>(b, x, s); };
-  int it = 0;
-  double rel = 0;
+  typename Gmres<T>::OpS opS = [&](const T* x, T* o, cudaStream_t cs) {
+    StreamSwap sw(h, cs);
+    apply_S<T>(h, v, x, o);
+  };
+  typename Gmres<T>::OpS pcS = [&](const T* b, T* x, cudaStream_t cs) { v.hS->template apply<T>(b, x, cs); };
   const int kA = h->o.inter_vcycles;
   // 1. A yhat_v = r_v
   h->stats.a_iters += solve_A<T>(h, v, v.gA, kA, h->o.rtol_A, h->o.max_A, rv, v.yhat);
@@ -1128,8 +1451,7 @@ void apply_pc(scr_ctx* h, PcView<T>& v, const T* r, T* y) {
   e.z = rp;
   spmv<T, T>(*v.C, v.yhat, v.rp2, h->k, e, s);
   // 3. S y_p = r_p
-  v.gS->solve(opS, &pcS, v.rp2, yp, h->o.rtol_S, h->o.max_S, h->red, s, &it, &rel);
-  h->stats.s_iters += it;
+  h->stats.s_iters += gmres_run<T>(h, v.gS, opS, pcS, v.rp2, yp, h->o.rtol_S, h->o.max_S);
   // 4. r_v <- r_v - B y_p
   e.z = rv;
   spmv<T, T>(*v.B, yp, v.rv2, h->k, e, s);
@@ -1150,10 +1472,10 @@ void apply_simple(scr_ctx* h, PcView<T>& v, const T* r, T* y) {
   const T* rp = r + nv3;
   T* yv = y;
   T* yp = y + nv3;
-  typename Gmres<T>::Op opS = [&](const T* x, T* o) { spmv<T, T>(*v.Shat, x, o, h->k, EpiArgs(), s); };
-  typename Gmres<T>::Op pcS = [&](const T* b, T* x) { v.hS->template apply<T>(b, x, s); };
-  int it = 0;
-  double rel = 0;
+  typename Gmres<T>::OpS opS = [&](const T* x, T* o, cudaStream_t cs) {
+    spmv<T, T>(*v.Shat, x, o, h->k, EpiArgs(), cs);
+  };
+  typename Gmres<T>::OpS pcS = [&](const T* b, T* x, cudaStream_t cs) { v.hS->template apply<T>(b, x, cs); };
   h->stats.a_iters += solve_A<T>(h, v, v.gA, h->o.inter_vcycles, h->o.rtol_A, h->o.max_A, rv, v.yhat);
   h->stats.a_solves++;
   EpiArgs e;
@@ -1162,8 +1484,7 @@ void apply_simple(scr_ctx* h, PcView<T>& v, const T* r, T* y) {
   e.beta = 1.0;
   e.z = rp;
   spmv<T, T>(*v.C, v.yhat, v.rp2, h->k, e, s);
-  v.gS->solve(opS, &pcS, v.rp2, yp, h->o.rtol_S, h->o.max_S, h->red, s, &it, &rel);
-  h->stats.s_iters += it;
+  h->stats.s_iters += gmres_run<T>(h, v.gS, opS, pcS, v.rp2, yp, h->o.rtol_S, h->o.max_S);
   EpiArgs u;
   u.kind = Epi::ScaledSub;
   u.z = v.yhat;
@@ -1171,7 +1492,7 @@ void apply_simple(scr_ctx* h, PcView<T>& v, const T* r, T* y) {
   spmv<T, T>(*v.B, yp, yv, h->k, u, s);
 }
 
-void apply_pc_any(scr_ctx* h, const double* r, double* y) {
+void apply_pc_direct(scr_ctx* h, const double* r, double* y) {
   const bool simple = h->o.precond == SCR_PC_SIMPLE || h->o.precond == SCR_PC_SIMPLEC;
   if (h->o.precision == SCR_MIXED) {
     const long long n = (3LL * h->nv + h->np) * h->k;
@@ -1185,6 +1506,77 @@ void apply_pc_any(scr_ctx* h, const double* r, double* y) {
     if (simple) apply_simple<double>(h, v, r, y);
     else apply_pc<double>(h, v, r, y);
   }
+}
+
+// Largest block system (unknowns times right-hand sides) that graph_krylov
+// = 2 runs with device loops.  Measured on one GB300 (set-up + solve, FP64 /
+// mixed): 24,764 unknowns 57 -> 53 ms / 47 -> 42 ms and 16 members of the
+// batch one after another 15.7 -> 15.1 s / 8.7 -> 7.8 s with device loops,
+// 2,503,844 unknowns 1037 -> 1042 ms / 581 -> 589 ms: where each inner step
+// takes milliseconds of GPU work the host waits cost less than the
+// conditional nodes' relaunch of their bodies.
+constexpr long long kDeviceLoopMaxUnknowns = 1000000;
+
+// y = P^{-1} r (SCR, SIMPLE or SIMPLEC in the handle's precision).  With
+// device loops (graph_krylov) the application is recorded once per set-up as
+// a CUDA graph from pc_r to pc_y, every inner GMRES a device loop, and
+// replayed between two copies; the library profiler, or a failed capture,
+// runs it directly.
+void apply_pc_any(scr_ctx* h, const double* r, double* y) {
+  const long long n_all = (3LL * h->nv + h->np) * h->k;
+  const bool loops = h->o.graph_krylov == 1 || (h->o.graph_krylov == 2 && n_all <= kDeviceLoopMaxUnknowns);
+  if (loops && !profiler().active && h->pc_r) {
+    if (h->pc_epoch != h->graph_epoch) {
+      h->pc_epoch = h->graph_epoch;
+      h->pc_exec.reset();
+      h->pc_failed = false;
+    }
+    if (!h->pc_exec && !h->pc_failed) {
+      const int a0 = h->stats.a_solves;
+      LaunchCounter sec;
+      cudaGraphExec_t ex = capture_exec([&](cudaStream_t cs) {
+        StreamSwap sw(h, cs);
+        const LaunchCounter c0 = counters();
+        apply_pc_direct(h, h->pc_r, h->pc_y);
+        sec = diff(counters(), c0);
+      });
+      h->pc_a_solves = h->stats.a_solves - a0;
+      h->stats.a_solves = a0;
+      h->pc_sec = sec;
+      if (ex) h->pc_exec.reset(ex);
+      else h->pc_failed = true;
+    }
+    if (h->pc_exec) {
+      const long long n = (3LL * h->nv + h->np) * h->k;
+      copy<double>(r, h->pc_r, n, h->s);
+      SCR_CUDA(cudaGraphLaunch(h->pc_exec.get(), h->s));
+      copy<double>(h->pc_y, y, n, h->s);
+      counters().launches += h->pc_sec.launches;
+      counters().spmv_bytes += h->pc_sec.spmv_bytes;
+      h->hA.vcycles += (int)h->pc_sec.vcycles[0];
+      h->hS.vcycles += (int)h->pc_sec.vcycles[1];
+      h->stats.a_iters += (int)h->pc_sec.fixed[0];
+      h->stats.i_iters += (int)h->pc_sec.fixed[1];
+      h->stats.a_solves += h->pc_a_solves;
+      h->stats.pc_graph_runs++;
+      return;
+    }
+  }
+  apply_pc_direct(h, r, y);
+}
+
+// adds the steps of the inner GMRES device loops run since the last
+// reset_solve_stats to the solve counters (one read-back per loop)
+void collect_loops(scr_ctx* h) {
+  LaunchCounter acc;
+  const long long a = h->gA.collect(h->s, acc) + h->gAf.collect(h->s, acc);
+  const long long sI = h->gS.collect(h->s, acc) + h->gSf.collect(h->s, acc);
+  const long long in = h->gI.collect(h->s, acc) + h->gIf.collect(h->s, acc);
+  h->stats.a_iters += (int)(a + acc.fixed[0]);
+  h->stats.s_iters += (int)sI;
+  h->stats.i_iters += (int)(in + acc.fixed[1]);
+  h->hA.vcycles += (int)acc.vcycles[0];
+  h->hS.vcycles += (int)acc.vcycles[1];
 }
 
 double true_rel_block(scr_ctx* h, const double* b, const double* x) {
@@ -1238,6 +1630,7 @@ int scr_default_opts(scr_opts* o) {
   o->l2_prefetch = 192;
   o->amg_coarse_bf16 = 1;
   o->cuda_graphs = 1;
+  o->graph_krylov = 2;
   o->nrhs = 1;
   o->mm_rtol = 1e-8;
   o->mm_max_it = 500;
@@ -1265,6 +1658,7 @@ int scr_create(scr_handle* out, const scr_opts* o, void* stream) {
     if (op.amg_degree < 1 || op.amg_degree > 16) throw std::invalid_argument("Chebyshev degree must lie in [1, 16]");
     if (op.l2_prefetch < 0) throw std::invalid_argument("l2_prefetch must be >= 0");
     if (op.vec != 0 && op.vec != 1) throw std::invalid_argument("vec must be 0 or 1");
+    if (op.graph_krylov < 0 || op.graph_krylov > 2) throw std::invalid_argument("graph_krylov must be 0, 1 or 2");
     if (op.inner_vcycles < 0 || op.inner_vcycles > 64 || op.inter_vcycles < 0 || op.inter_vcycles > 64)
       throw std::invalid_argument("inner_vcycles and inter_vcycles must lie in [0, 64]");
     if (op.newton != 0 && op.newton != 1) throw std::invalid_argument("newton must be 0 or 1");
@@ -1399,6 +1793,7 @@ int scr_update_values(scr_handle h, const scr_bsr* A, const scr_bsr* B, const sc
     }
     h->hA.refresh(h->A, h->o, s, f32 ? &h->Af : nullptr);
     h->hS.refresh(h->Shat, h->o, s);
+    h->graph_epoch++;
     SCR_CUDA(cudaStreamSynchronize(s));
     h->stats.setup_ms = ms_since(t0);
   });
@@ -1422,6 +1817,7 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
     if (!h->tangent_setup) h->ta.ready = false;  // new matrices: a new pattern for the tangent
     h->hA = Hierarchy();
     h->hS = Hierarchy();
+    h->hS.slot = 1;
     h->work.reset();
     h->mats.reset(new DeviceArena(s));
     DeviceArena& a = *h->mats;
@@ -1521,6 +1917,9 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
     const int k = h->k;
     const long long n = (3LL * nv + np) * k, nv3 = 3LL * nv * k;
     h->gOuter.init(w, n, h->o.restart);
+    h->pc_r = w.alloc<double>(n + 1);
+    h->pc_y = w.alloc<double>(n + 1);
+    h->graph_epoch++;
     if (k > 1) h->mstage = w.alloc<double>(n + 1);
     h->bvec = w.alloc<double>(n + 1);
     h->xvec = w.alloc<double>(n + 1);
@@ -1566,7 +1965,14 @@ int scr_setup(scr_handle h, const scr_bsr* A, const scr_bsr* B, const scr_bsr* C
 
 static void reset_solve_stats(scr_ctx* h) {
   h->stats.outer_iters = h->stats.a_solves = h->stats.a_iters = h->stats.s_iters = h->stats.i_iters = 0;
+  h->stats.pc_graph_runs = 0;
   h->hA.vcycles = h->hS.vcycles = 0;
+  h->gA.reset_loop(h->s);
+  h->gS.reset_loop(h->s);
+  h->gI.reset_loop(h->s);
+  h->gAf.reset_loop(h->s);
+  h->gSf.reset_loop(h->s);
+  h->gIf.reset_loop(h->s);
   h->gOuter.syncs = h->gA.syncs = h->gS.syncs = h->gI.syncs = 0;
   h->gAf.syncs = h->gSf.syncs = h->gIf.syncs = 0;
 }
@@ -1579,6 +1985,7 @@ static int solve_impl(scr_ctx* h, const double* b, double* x, double rtol) {
   int it = 0;
   double rel = 0;
   const bool ok = h->gOuter.solve(op, &pc, b, x, rtol, h->o.max_it, h->red, h->s, &it, &rel, &tr);
+  collect_loops(h);
   h->stats.outer_iters = it;
   h->stats.rel_res = true_rel_block(h, b, x);
   h->stats.vcycles_A = h->hA.vcycles;
@@ -1926,6 +2333,7 @@ int mm_setup(scr_handle h, const scr_bsr* L, int dev) {
     SCR_CUDA(cudaStreamSynchronize(s));
     h->have_mesh = false;
     h->hM = Hierarchy();
+    h->hM.slot = 2;
     h->mwork.reset();
     h->mmats.reset(new DeviceArena(s));
     h->nm = L->nb_rows;
@@ -2100,6 +2508,7 @@ int scr_apply_pc(scr_handle h, const double* r, double* y) {
   return guarded([&] {
     reset_solve_stats(h);
     apply_pc_any(h, r, y);
+    collect_loops(h);
     SCR_CUDA(cudaStreamSynchronize(h->s));
   });
 }
