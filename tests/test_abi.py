@@ -44,6 +44,10 @@ def test_default_options_without_gpu():
     o = abi.Opts()
     assert lib.scr_default_opts(ctypes.byref(o)) == 0
     assert o.rtol == 1e-8 and o.restart == 30 and o.rtol_A == 1e-3 and o.max_it == 200
+    # the defaults the header documents for the GPU-side choices
+    assert (o.vec, o.pdl, o.l2_prefetch, o.cuda_graphs, o.graph_krylov) == (1, 1, 192, 1, 2)
+    assert (o.mapped_scalars, o.tangent_resetup, o.newton, o.nrhs) == (1, 1, 0, 1)
+    assert (o.inner_vcycles, o.inter_vcycles, o.amg_coarse_bf16) == (0, 0, 1)
     assert lib.scr_default_opts(None) == abi.SCR_INVALID_ARG
 
 
@@ -83,3 +87,25 @@ def test_tune_file_round_trip_without_gpu(tmp_path):
             pkg.tune_load(str(f))
     with pytest.raises(pkg.ScrError):
         pkg.tune_load(str(tmp_path / "missing.txt"))
+
+
+def _struct_fields(src: str, start: str, end: str) -> list:
+    body = src[src.index(start):]
+    body = body[: body.index(end)]
+    decl = []
+    for line in re.sub(r"/\*.*?\*/", "", body, flags=re.S).splitlines():
+        line = line.strip().rstrip(";")
+        if not line or line.startswith("typedef"):
+            continue
+        m = re.match(r"(long long|double|int|float)\s+(.*)", line)
+        if m:
+            decl.extend(v.strip() for v in m.group(2).split(","))
+    return decl
+
+
+def test_stats_struct_layout_matches_header():
+    from paper_2206_06996_gb300 import abi
+    src = open(HEADER).read()
+    decl = _struct_fields(src, "typedef struct {\n  int outer_iters;", "} scr_stats;")
+    assert [f for f, _ in abi.Stats._fields_] == decl
+    assert "pc_graph_runs" in decl
