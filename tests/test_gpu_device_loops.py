@@ -225,3 +225,30 @@ def test_default_runs_device_loops_on_small_systems(small):
 def test_graph_krylov_option_is_checked():
     with pytest.raises(Exception):
         pkg.BlockSolver(graph_krylov=3)
+
+
+def test_device_loops_zero_and_nonfinite_inner_right_hand_sides(small):
+    """Algorithm 1 applied to a zero vector, and to one with a NaN in its
+    velocity part: the intermediate A solves then start from b = 0 (x = 0, no
+    step) or from a non-finite b (x = 0, stopped at once), the S solve runs
+    as usual, and the recorded loops give what the host loops give."""
+    nv3 = 3 * small.n_v
+    r_nan = np.random.default_rng(9).standard_normal(small.n)
+    r_nan[7] = np.nan
+    out = {}
+    for g in (0, 1):
+        with pkg.BlockSolver(graph_krylov=g) as sol:
+            sol.setup(small.A, small.B, small.C, small.D)
+            y0 = sol.apply_pc(_dev(np.zeros(small.n))).cpu().numpy()
+            st0 = sol.stats()
+            y1 = sol.apply_pc(_dev(r_nan)).cpu().numpy()
+            st1 = sol.stats()
+            out[g] = (y0, y1, st0, st1)
+    for g in (0, 1):
+        assert np.all(out[g][0] == 0.0)
+        assert np.all(out[g][1][:nv3] == 0.0)
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    for k in ("a_iters", "s_iters", "i_iters"):
+        assert out[0][2][k] == out[1][2][k] == 0, k
+        assert out[0][3][k] == out[1][3][k], k
+    assert out[1][3]["a_iters"] == 0
